@@ -1,0 +1,180 @@
+/*
+ * gpchol.h -- C ABI of the GB300 (sm_103a) Cholesky / Cholesky-adjoint /
+ * Gaussian-process likelihood library (libgpchol.so).
+ *
+ * The operations follow "GPU-based Parallel Computation Support for Stan"
+ * (Cesnovar et al., 2019): the blocked Cholesky decomposition and its blocked
+ * reverse mode (Section 3.3), triangular solves (Section 3.2), and the
+ * Gaussian-process log marginal likelihood that the GP regression example of
+ * Section 4.2 evaluates on top of them.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Matrices are FP64, ROW-MAJOR: element (i, j) of an n x n matrix with
+ *    leading dimension ld lives at ptr[i * ld + j], ld >= n.  Symmetric inputs
+ *    are read from their LOWER triangle (i >= j) only.  Lower-triangular
+ *    outputs (L, Kbar) have their strict upper triangle set to zero.
+ *  - Every pointer argument is a DEVICE pointer unless stated otherwise, owned
+ *    by the caller; the library never frees or retains it.  The library
+ *    allocates no device memory: calls that need scratch take a workspace
+ *    (ws, ws_bytes) sized by gpc_workspace_size().  Workspace contents are
+ *    undefined on return; two calls in flight at the same time need two
+ *    workspaces.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = the
+ *    legacy default stream) and returns a host status code once its kernels
+ *    are enqueued.  Conditions found on the device (a failing pivot, NaN
+ *    input) are written to the caller's device `info` array, which the caller
+ *    reads after synchronising.
+ *  - Sizes n = 0 are valid no-ops.  Negative sizes, ld < n, NULL pointers for
+ *    n > 0, a too-small workspace or an unknown precision return
+ *    GPC_ERR_INVALID_ARG without enqueuing anything.
+ */
+#ifndef GPCHOL_H
+#define GPCHOL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so this header needs no CUDA one. */
+typedef struct CUstream_st *gpc_stream_t;
+
+/* Host status codes (return values), also used as info[1] on the device. */
+#define GPC_OK 0
+#define GPC_ERR_INVALID_ARG 1   /* bad size, leading dimension, pointer, flag or workspace */
+#define GPC_ERR_NOT_PD 2        /* a pivot was <= 0: the matrix is not positive definite */
+#define GPC_ERR_NAN 3           /* a pivot was NaN or infinite */
+#define GPC_ERR_CUDA 4          /* a kernel launch or CUDA runtime call failed */
+#define GPC_ERR_TIMEOUT 5       /* a bounded device-side wait gave up */
+#define GPC_ERR_NO_CONVERGENCE 6 /* iterative refinement did not reach its tolerance */
+
+/* Arithmetic of the O(n^3) products. */
+#define GPC_FP64 0   /* every step in FP64 (DMMA tensor-core and FP64 ALU) */
+#define GPC_MIXED 1  /* trailing/adjoint products as error-free split BF16 slices on tcgen05 */
+
+/*
+ * Device `info` arrays have two ints: info[0] = the 0-based index of the first
+ * failing pivot, or -1; info[1] = GPC_OK, GPC_ERR_NOT_PD, GPC_ERR_NAN or
+ * GPC_ERR_TIMEOUT.  Calls that take `info` reset it to {-1, GPC_OK} on the
+ * stream before their first kernel.
+ */
+
+/* Human-readable text of a status code (static storage, never NULL). */
+const char *gpc_status_string(int status);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int gpc_version(void);
+
+/*
+ * Workspace bytes that gpc_chol, gpc_chol_adjoint, gpc_gp_lml and
+ * gpc_gp_lml_grad need for matrices of order n at `precision` with the
+ * current tuning (gpc_set_tuning).  One workspace of this size serves any of
+ * those calls with order <= n.  *bytes is a host pointer.
+ */
+int gpc_workspace_size(int n, int precision, size_t *bytes);
+
+/*
+ * Tuning knobs (host-side, process-wide; not thread-safe against concurrent
+ * calls).  key: GPC_TUNE_BLOCK = block size b of the blocked factorisation and
+ * adjoint (16..128, multiple of 16; default 128), GPC_TUNE_SLICES = number of
+ * BF16 slices of the mixed path (3..8), GPC_TUNE_SPLITK_MIN = minimum K per
+ * split of the split-K products.  Changing GPC_TUNE_BLOCK changes the
+ * workspace size.  Returns GPC_ERR_INVALID_ARG for an unknown key or value.
+ */
+#define GPC_TUNE_BLOCK 0
+#define GPC_TUNE_SLICES 1
+#define GPC_TUNE_SPLITK_MIN 2
+int gpc_set_tuning(int key, int value);
+int gpc_get_tuning(int key, int *value);
+
+/*
+ * Squared-exponential covariance of the rows of X (n x d, row-major, ldx >= d):
+ *   K_ij = alpha^2 exp(-|x_i - x_j|^2 / (2 rho^2)) + [i == j] (sigma^2 + jitter).
+ * The paper's GP regression example (Section 4.2) builds this matrix; its
+ * discussion lists covariance functions as GPU work to add (Section 5).
+ * Writes the lower triangle of K (ldk >= n); full != 0 mirrors it into the
+ * upper triangle, full == 0 leaves the upper triangle untouched.
+ * Requires rho > 0; d >= 1.
+ */
+int gpc_se_cov(int n, int d, const double *X, int ldx, double alpha, double rho, double sigma,
+               double jitter, double *K, int ldk, int full, gpc_stream_t stream);
+
+/*
+ * Cholesky factor L (lower, K = L L^T) of the SPD matrix whose lower triangle
+ * is in K -- the blocked right-looking form of Section 3.3 (primitive
+ * function): diagonal block factor and inverse, panel L21 = A21 L11^{-T} as a
+ * product with the inverse, trailing update A22 -= L21 L21^T.
+ * K == L (in place, same ld) is allowed; otherwise K is not modified.
+ * On a failing pivot p, info = {p, GPC_ERR_NOT_PD or GPC_ERR_NAN}, rows >= p
+ * of L are unspecified, and the call still returns GPC_OK (the failure is
+ * only visible on the device).  info: 2 device ints.
+ * precision GPC_MIXED computes the trailing updates with split-BF16 slices;
+ * the diagonal blocks and panels stay FP64.
+ */
+int gpc_chol(int n, const double *K, int ldk, double *L, int ldl, int precision, void *ws,
+             size_t ws_bytes, int *info, gpc_stream_t stream);
+
+/*
+ * Reverse mode of gpc_chol (Section 3.3, reverse mode function; the blocked
+ * sweep after Murray 2016): given L and an adjoint Lbar (both lower), writes
+ * Kbar = d f / d K restricted to the entries chol reads, i.e. for i >= j the
+ * derivative with respect to the lower-triangle entry K_ij (lower output, zero
+ * upper).  symmetric_out != 0 instead writes the full symmetric G with
+ * G_ii = Kbar_ii and G_ij = G_ji = Kbar_ij / 2 (the gradient of f over a
+ * symmetric K).  Kbar == Lbar (in place, same ld) is allowed; L must not
+ * alias either.  L is not modified.
+ */
+int gpc_chol_adjoint(int n, const double *L, int ldl, const double *Lbar, int ldlb, double *Kbar,
+                     int ldkb, int precision, int symmetric_out, void *ws, size_t ws_bytes,
+                     gpc_stream_t stream);
+
+/*
+ * Triangular solve with the lower factor L (Section 3.2):
+ *   trans == 0: x <- L^{-1} x      trans != 0: x <- L^{-T} x
+ * x is a device vector of n doubles, overwritten.  ws/ws_bytes: at least
+ * gpc_workspace_size(n, GPC_FP64) bytes.
+ */
+int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, size_t ws_bytes,
+             gpc_stream_t stream);
+
+/*
+ * Gaussian-process log marginal likelihood of y ~ N(0, K):
+ *   L = chol(K), z = L^{-1} y, alpha = L^{-T} z, logdet = 2 sum log L_ii,
+ *   value = -1/2 y^T alpha - 1/2 logdet - (n/2) log(2 pi).
+ * Writes L (may alias K when precision == GPC_FP64), alpha (n doubles), and
+ * the device scalars logdet and value.  With GPC_MIXED the solve is refined
+ * in FP64 against K (r = y - K alpha, alpha += L^{-T} L^{-1} r) until
+ * |r| <= 1e-14 |y| or 10 rounds; K must then not alias L, and a refinement
+ * that stops above tolerance sets info = {-1, GPC_ERR_NO_CONVERGENCE}.
+ */
+int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int ldl,
+               int precision, double *logdet, double *alpha, double *value, void *ws,
+               size_t ws_bytes, int *info, gpc_stream_t stream);
+
+/*
+ * Kbar = gbar * d value / d K for the likelihood of gpc_gp_lml, through the
+ * Cholesky adjoint: Lbar = gbar (tril(alpha z^T) - diag(1 / L_ii)) with
+ * z = L^T alpha, then Kbar = chol_adjoint(L, Lbar) (lower convention).
+ */
+int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double gbar,
+                    double *Kbar, int ldkb, int precision, void *ws, size_t ws_bytes,
+                    gpc_stream_t stream);
+
+/*
+ * Hyperparameter gradient from Kbar (lower convention) for the covariance of
+ * gpc_se_cov: grad3 = (d/d alpha, d/d rho, d/d sigma) of f, with
+ *   d K_ij/d alpha = 2 K^f_ij / alpha, d K_ij/d rho = K^f_ij r2_ij / rho^3,
+ *   d K_ii/d sigma = 2 sigma   (K^f: the noise-free part; jitter is constant),
+ * summed over i >= j.  K^f is recomputed from X; grad3: 3 device doubles.
+ */
+int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, double rho,
+                      double sigma, const double *Kbar, int ldkb, double *grad3,
+                      gpc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPCHOL_H */

@@ -1,0 +1,284 @@
+/*
+ * gpchol_oracle.c -- plain, slow, single-threaded FP64 CPU oracle for the
+ * dense Cholesky / Cholesky-adjoint / Gaussian-process likelihood path of
+ * "GPU-based Parallel Computation Support for Stan" (Cesnovar et al., 2019).
+ *
+ * THIS IS TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  The GPU library shares no code,
+ * header, table or helper with this file, and nothing here is ever used on
+ * the product path.
+ *
+ * Conventions: every matrix is FP64, row-major, element (i,j) at a[i*ld + j],
+ * ld >= n.  Only the lower triangle (i >= j) of a symmetric input is read.
+ * Lower-triangular outputs have their strict upper triangle set to zero.
+ * Compile with -O2 -ffp-contract=off (no fused multiply-add contraction), so
+ * every sum is an ordinary left-to-right FP64 sum in the order written.
+ *
+ * Every function is the plain unblocked definition of what the paper's
+ * blocked GPU routines compute; none of them is blocked, fused or reordered.
+ */
+#include <math.h>
+
+#define ORACLE_TWO_PI 6.283185307179586476925286766559
+#include <stdlib.h>
+#include <string.h>
+
+#define AT(a, ld, i, j) ((a)[(size_t)(i) * (size_t)(ld) + (size_t)(j)])
+
+/*
+ * Cholesky factor L of an SPD matrix K (K = L L^T, L lower, L_ii > 0).
+ * Section 3.3 (Cholesky decomposition, primitive function) partitions
+ * K = [A11 .; A21 A22] into L11 = chol(A11), L21 = A21 L11^{-T},
+ * L22 = chol(A22 - L21 L21^T).  Taking A11 to be 1x1 at every level gives
+ * the row-by-row Cholesky-Banachiewicz recurrence written here:
+ *   s = K_ij - sum_{k<j} L_ik L_jk  (k ascending),
+ *   L_ii = sqrt(s) on the diagonal, L_ij = s / L_jj below it.
+ * A pivot s that is not > 0 (this includes NaN) stops the factorisation.
+ * Returns -1 on success, else the 0-based index of the first failing pivot
+ * (rows from that index on are left as they were when it stopped).
+ * K and L may be the same buffer.
+ */
+int oracle_chol(int n, const double *K, int ldk, double *L, int ldl) {
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = AT(K, ldk, i, j);
+      for (int k = 0; k < j; ++k) s -= AT(L, ldl, i, k) * AT(L, ldl, j, k);
+      if (i == j) {
+        if (!(s > 0.0)) return i;
+        AT(L, ldl, i, i) = sqrt(s);
+      } else {
+        AT(L, ldl, i, j) = s / AT(L, ldl, j, j);
+      }
+    }
+    for (int j = i + 1; j < n; ++j) AT(L, ldl, i, j) = 0.0;
+  }
+  return -1;
+}
+
+/*
+ * Reverse mode of oracle_chol: given L and an adjoint Lbar (lower), returns
+ * Kbar (lower) = d f / d K_ij for i >= j, where f depends on K only through
+ * the lower-triangle entries that chol reads (Section 3.3, reverse mode
+ * function; Murray 2016 gives the unblocked form this follows).
+ * Each statement of the forward recurrence is reversed, visiting (i,j) in the
+ * exact reverse of the forward order (i descending, then j descending):
+ *   diagonal  L_ii = sqrt(s):   sbar = Lbar_ii / (2 L_ii)
+ *   off-diag  L_ij = s / L_jj:  sbar = Lbar_ij / L_jj,
+ *                                Lbar_jj -= Lbar_ij L_ij / L_jj
+ *   then Kbar_ij = sbar, and for k < j (from s -= L_ik L_jk):
+ *                                Lbar_ik -= sbar L_jk,  Lbar_jk -= sbar L_ik.
+ * Lbar is copied first and not modified.  Kbar may alias Lbar.
+ * Returns 0, or -1 if the scratch copy cannot be allocated.
+ */
+int oracle_chol_adjoint(int n, const double *L, int ldl, const double *Lbar,
+                        int ldlb, double *Kbar, int ldkb) {
+  double *W = (double *)malloc((size_t)n * (size_t)n * sizeof(double) + 8);
+  if (!W) return -1;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) AT(W, n, i, j) = (j <= i) ? AT(Lbar, ldlb, i, j) : 0.0;
+  for (int i = n - 1; i >= 0; --i) {
+    for (int j = i; j >= 0; --j) {
+      double sbar;
+      if (i == j) {
+        sbar = AT(W, n, i, i) / (2.0 * AT(L, ldl, i, i));
+      } else {
+        double ljj = AT(L, ldl, j, j);
+        sbar = AT(W, n, i, j) / ljj;
+        AT(W, n, j, j) -= AT(W, n, i, j) * AT(L, ldl, i, j) / ljj;
+      }
+      AT(W, n, i, j) = sbar; /* this slot now holds Kbar_ij */
+      for (int k = 0; k < j; ++k) {
+        AT(W, n, i, k) -= sbar * AT(L, ldl, j, k);
+        AT(W, n, j, k) -= sbar * AT(L, ldl, i, k);
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) AT(Kbar, ldkb, i, j) = (j <= i) ? AT(W, n, i, j) : 0.0;
+  free(W);
+  return 0;
+}
+
+/* x <- L^{-1} x (trans = 0) or x <- L^{-T} x (trans = 1); plain forward /
+ * back substitution with L lower (Section 3.2, solving triangular systems:
+ * the result the inverse-based GPU solver reaches). */
+void oracle_trsv(int n, const double *L, int ldl, double *x, int trans) {
+  if (!trans) {
+    for (int i = 0; i < n; ++i) {
+      double s = x[i];
+      for (int k = 0; k < i; ++k) s -= AT(L, ldl, i, k) * x[k];
+      x[i] = s / AT(L, ldl, i, i);
+    }
+  } else {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = x[i];
+      for (int k = i + 1; k < n; ++k) s -= AT(L, ldl, k, i) * x[k];
+      x[i] = s / AT(L, ldl, i, i);
+    }
+  }
+}
+
+/*
+ * Symbolic Cholesky adjoint (Murray 2016, the identity the blocked gradient of
+ * Section 3.3 applies block by block), as an independent cross-check of
+ * oracle_chol_adjoint:
+ *   P = Phi(L^T Lbar)   (Phi: lower triangle, diagonal halved)
+ *   S = L^{-T} P L^{-1}
+ *   Kbar_ij = S_ij + S_ji (i > j),  Kbar_ii = S_ii,  upper = 0.
+ * L^{-1} is applied by substitution, column by column.
+ * Returns 0, or -1 if scratch cannot be allocated.
+ */
+int oracle_chol_adjoint_symbolic(int n, const double *L, int ldl, const double *Lbar,
+                                 int ldlb, double *Kbar, int ldkb) {
+  double *P = (double *)malloc((size_t)n * (size_t)n * sizeof(double) + 8);
+  double *col = (double *)malloc((size_t)n * sizeof(double) + 8);
+  if (!P || !col) { free(P); free(col); return -1; }
+  /* P = Phi(L^T Lbar): (L^T Lbar)_ij = sum_k L_ki Lbar_kj over k >= max(i,j). */
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      if (j <= i) {
+        for (int k = i; k < n; ++k) s += AT(L, ldl, k, i) * AT(Lbar, ldlb, k, j);
+        if (i == j) s *= 0.5;
+      }
+      AT(P, n, i, j) = s;
+    }
+  }
+  /* T = P L^{-1}: row r of T solves t L = p_r, i.e. L^T t^T = p_r^T. */
+  for (int r = 0; r < n; ++r) {
+    for (int c = 0; c < n; ++c) col[c] = AT(P, n, r, c);
+    oracle_trsv(n, L, ldl, col, 1);
+    for (int c = 0; c < n; ++c) AT(P, n, r, c) = col[c];
+  }
+  /* S = L^{-T} T: column c of S solves L^T s = t_c. */
+  for (int c = 0; c < n; ++c) {
+    for (int r = 0; r < n; ++r) col[r] = AT(P, n, r, c);
+    oracle_trsv(n, L, ldl, col, 1);
+    for (int r = 0; r < n; ++r) AT(P, n, r, c) = col[r];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double v = 0.0;
+      if (j < i) v = AT(P, n, i, j) + AT(P, n, j, i);
+      else if (j == i) v = AT(P, n, i, i);
+      AT(Kbar, ldkb, i, j) = v;
+    }
+  free(P);
+  free(col);
+  return 0;
+}
+
+/*
+ * Squared-exponential covariance (the GP covariance of the Gaussian-process
+ * regression example of Section 4.2; the kernel's form is not printed there):
+ *   K_ij = alpha^2 exp(-sum_t (x_it - x_jt)^2 / (2 rho^2))  (i != j)
+ *   K_ii = alpha^2 + sigma^2 + jitter
+ * with direct coordinate differences.  Writes the lower triangle; when
+ * full != 0 the upper triangle is mirrored, else it is set to zero.
+ */
+void oracle_se_cov(int n, int d, const double *X, int ldx, double alpha, double rho,
+                   double sigma, double jitter, double *K, int ldk, int full) {
+  double a2 = alpha * alpha;
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < i; ++j) {
+      double r2 = 0.0;
+      for (int t = 0; t < d; ++t) {
+        double df = AT(X, ldx, i, t) - AT(X, ldx, j, t);
+        r2 += df * df;
+      }
+      AT(K, ldk, i, j) = a2 * exp(-r2 / (2.0 * rho * rho));
+    }
+    AT(K, ldk, i, i) = a2 + sigma * sigma + jitter;
+    for (int j = i + 1; j < n; ++j) AT(K, ldk, i, j) = 0.0;
+  }
+  if (full)
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) AT(K, ldk, i, j) = AT(K, ldk, j, i);
+}
+
+/*
+ * Gaussian-process log marginal likelihood of y ~ N(0, K) through the
+ * Cholesky factor (the quantity the GP regression model of Section 4.2
+ * evaluates every gradient step):
+ *   L = chol(K);  z = L^{-1} y;  alpha = L^{-T} z;
+ *   logdet = 2 sum_i log L_ii;
+ *   value = -1/2 z.z - 1/2 logdet - (n/2) log(2 pi).
+ * Writes L (may alias K), z and alpha (n each; may be NULL), logdet and value.
+ * Returns -1 on success or the failing pivot of oracle_chol.
+ */
+int oracle_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int ldl,
+                  double *z, double *alpha, double *logdet, double *value) {
+  int info = oracle_chol(n, K, ldk, L, ldl);
+  if (info >= 0) return info;
+  double *zz = (double *)malloc((size_t)n * sizeof(double) + 8);
+  double *aa = (double *)malloc((size_t)n * sizeof(double) + 8);
+  if (!zz || !aa) { free(zz); free(aa); return -2; }
+  for (int i = 0; i < n; ++i) zz[i] = y[i];
+  oracle_trsv(n, L, ldl, zz, 0);
+  for (int i = 0; i < n; ++i) aa[i] = zz[i];
+  oracle_trsv(n, L, ldl, aa, 1);
+  double ld = 0.0, q = 0.0;
+  for (int i = 0; i < n; ++i) ld += log(AT(L, ldl, i, i));
+  ld *= 2.0;
+  for (int i = 0; i < n; ++i) q += zz[i] * zz[i];
+  if (logdet) *logdet = ld;
+  if (value) *value = -0.5 * q - 0.5 * ld - 0.5 * (double)n * log(ORACLE_TWO_PI);
+  if (z) memcpy(z, zz, (size_t)n * sizeof(double));
+  if (alpha) memcpy(alpha, aa, (size_t)n * sizeof(double));
+  free(zz);
+  free(aa);
+  return -1;
+}
+
+/*
+ * Upstream adjoint of the log marginal likelihood with respect to L, scaled by
+ * gbar (reverse mode of oracle_gp_lml's value for fixed y):
+ *   Lbar = gbar * (tril(alpha z^T) - diag(1 / L_ii)).
+ * d(-1/2 z.z) = alpha^T dL z gives the first term, d(-sum log L_ii) the second.
+ */
+void oracle_lml_lbar(int n, const double *L, int ldl, const double *alpha, const double *z,
+                     double gbar, double *Lbar, int ldlb) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double v = 0.0;
+      if (j <= i) {
+        v = alpha[i] * z[j];
+        if (i == j) v -= 1.0 / AT(L, ldl, i, i);
+        v *= gbar;
+      }
+      AT(Lbar, ldlb, i, j) = v;
+    }
+}
+
+/*
+ * Hyperparameter gradient of a scalar f(K(alpha, rho, sigma)) from Kbar in the
+ * lower-triangle convention of oracle_chol_adjoint (Kbar_ij = df/dK_ij over
+ * the entries i >= j that chol reads), with K from oracle_se_cov:
+ *   g_alpha = sum_{i>=j} Kbar_ij * 2 K^f_ij / alpha
+ *   g_rho   = sum_{i>=j} Kbar_ij * K^f_ij * r2_ij / rho^3
+ *   g_sigma = sum_i Kbar_ii * 2 sigma
+ * where K^f_ij = alpha^2 exp(-r2_ij / (2 rho^2)) is the noise-free part and the
+ * jitter is a constant.  grad3 = {g_alpha, g_rho, g_sigma}.
+ */
+void oracle_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, double rho,
+                          double sigma, const double *Kbar, int ldkb, double *grad3) {
+  double ga = 0.0, gr = 0.0, gs = 0.0;
+  double a2 = alpha * alpha;
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double r2 = 0.0;
+      for (int t = 0; t < d; ++t) {
+        double df = AT(X, ldx, i, t) - AT(X, ldx, j, t);
+        r2 += df * df;
+      }
+      double kf = a2 * exp(-r2 / (2.0 * rho * rho));
+      double kb = AT(Kbar, ldkb, i, j);
+      ga += kb * 2.0 * kf / alpha;
+      gr += kb * kf * r2 / (rho * rho * rho);
+      if (i == j) gs += kb * 2.0 * sigma;
+    }
+  }
+  grad3[0] = ga;
+  grad3[1] = gr;
+  grad3[2] = gs;
+}

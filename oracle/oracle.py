@@ -1,0 +1,186 @@
+"""NumPy/ctypes front end of the plain FP64 CPU oracle (``gpchol_oracle.c``).
+
+This is test infrastructure: only the tests, the smoke check and the
+benchmark's CPU-baseline leg import it.  It shares nothing with the GPU
+library.  Every function takes and returns float64 NumPy arrays (row-major);
+the arithmetic lives in the C file, compiled with ``-O2 -ffp-contract=off``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gpchol_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libgpchol_oracle.so")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build``; returns the library path."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        # GPCHOL_ORACLE_LIB lets the mutation test load a deliberately broken copy.
+        lib = ctypes.CDLL(os.environ.get("GPCHOL_ORACLE_LIB") or build())
+        i, d = ctypes.c_int, ctypes.c_double
+        lib.oracle_chol.argtypes = [i, _D, i, _D, i]
+        lib.oracle_chol.restype = i
+        lib.oracle_chol_adjoint.argtypes = [i, _D, i, _D, i, _D, i]
+        lib.oracle_chol_adjoint.restype = i
+        lib.oracle_chol_adjoint_symbolic.argtypes = [i, _D, i, _D, i, _D, i]
+        lib.oracle_chol_adjoint_symbolic.restype = i
+        lib.oracle_trsv.argtypes = [i, _D, i, _D, i]
+        lib.oracle_trsv.restype = None
+        lib.oracle_se_cov.argtypes = [i, i, _D, i, d, d, d, d, _D, i, i]
+        lib.oracle_se_cov.restype = None
+        lib.oracle_gp_lml.argtypes = [i, _D, i, _D, _D, i, _D, _D, _D, _D]
+        lib.oracle_gp_lml.restype = i
+        lib.oracle_lml_lbar.argtypes = [i, _D, i, _D, _D, d, _D, i]
+        lib.oracle_lml_lbar.restype = None
+        lib.oracle_se_hyper_grad.argtypes = [i, i, _D, i, d, d, d, _D, i, _D]
+        lib.oracle_se_hyper_grad.restype = None
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _mat(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("expected a square matrix")
+    return a
+
+
+class NotPositiveDefinite(ValueError):
+    def __init__(self, info: int):
+        super().__init__(f"matrix is not positive definite (pivot {info})")
+        self.info = info
+
+
+def chol(K) -> np.ndarray:
+    """Lower Cholesky factor (Cholesky-Banachiewicz); raises on a failing pivot."""
+    K = _mat(K)
+    n = K.shape[0]
+    L = np.zeros_like(K)
+    info = _load().oracle_chol(n, _p(K), n, _p(L), n)
+    if info >= 0:
+        raise NotPositiveDefinite(info)
+    return L
+
+
+def chol_info(K) -> tuple[np.ndarray, int]:
+    """As ``chol`` but returns (partial L, info) with info = -1 on success."""
+    K = _mat(K)
+    n = K.shape[0]
+    L = np.zeros_like(K)
+    info = _load().oracle_chol(n, _p(K), n, _p(L), n)
+    return L, int(info)
+
+
+def chol_adjoint(L, Lbar) -> np.ndarray:
+    """Unblocked reverse mode of ``chol``: Kbar (lower) from L and Lbar."""
+    L, Lbar = _mat(L), _mat(Lbar)
+    n = L.shape[0]
+    Kbar = np.zeros_like(L)
+    if _load().oracle_chol_adjoint(n, _p(L), n, _p(Lbar), n, _p(Kbar), n) != 0:
+        raise MemoryError("oracle scratch allocation failed")
+    return Kbar
+
+
+def chol_adjoint_symbolic(L, Lbar) -> np.ndarray:
+    """Symbolic adjoint L^{-T} Phi(L^T Lbar) L^{-1}, folded to the lower convention."""
+    L, Lbar = _mat(L), _mat(Lbar)
+    n = L.shape[0]
+    Kbar = np.zeros_like(L)
+    if _load().oracle_chol_adjoint_symbolic(n, _p(L), n, _p(Lbar), n, _p(Kbar), n) != 0:
+        raise MemoryError("oracle scratch allocation failed")
+    return Kbar
+
+
+def trsv(L, x, trans: bool = False) -> np.ndarray:
+    """L^{-1} x (trans False) or L^{-T} x (trans True) by substitution."""
+    L = _mat(L)
+    out = np.array(x, dtype=np.float64, copy=True)
+    _load().oracle_trsv(L.shape[0], _p(L), L.shape[0], _p(out), 1 if trans else 0)
+    return out
+
+
+def se_cov(X, alpha: float, rho: float, sigma: float, jitter: float = 0.0,
+           full: bool = False) -> np.ndarray:
+    """Squared-exponential covariance of the rows of X (n x d)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n, d = X.shape
+    K = np.zeros((n, n))
+    _load().oracle_se_cov(n, d, _p(X), d, alpha, rho, sigma, jitter, _p(K), n, 1 if full else 0)
+    return K
+
+
+def gp_lml(K, y):
+    """Returns dict(L, z, alpha, logdet, value) for y ~ N(0, K)."""
+    K = _mat(K)
+    n = K.shape[0]
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    L = np.zeros_like(K)
+    z = np.zeros(n)
+    a = np.zeros(n)
+    ld = ctypes.c_double()
+    val = ctypes.c_double()
+    info = _load().oracle_gp_lml(n, _p(K), n, _p(y), _p(L), n, _p(z), _p(a),
+                                 ctypes.byref(ld), ctypes.byref(val))
+    if info == -2:
+        raise MemoryError("oracle scratch allocation failed")
+    if info >= 0:
+        raise NotPositiveDefinite(info)
+    return {"L": L, "z": z, "alpha": a, "logdet": ld.value, "value": val.value}
+
+
+def lml_lbar(L, alpha, z, gbar: float = 1.0) -> np.ndarray:
+    """Upstream Lbar = gbar (tril(alpha z^T) - diag(1/L_ii))."""
+    L = _mat(L)
+    n = L.shape[0]
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    Lbar = np.zeros_like(L)
+    _load().oracle_lml_lbar(n, _p(L), n, _p(alpha), _p(z), gbar, _p(Lbar), n)
+    return Lbar
+
+
+def se_hyper_grad(X, alpha: float, rho: float, sigma: float, Kbar) -> np.ndarray:
+    """(d/d alpha, d/d rho, d/d sigma) of f given Kbar = df/dK (lower convention)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Kbar = _mat(Kbar)
+    n, d = X.shape
+    g = np.zeros(3)
+    _load().oracle_se_hyper_grad(n, d, _p(X), d, alpha, rho, sigma, _p(Kbar), n, _p(g))
+    return g
+
+
+def gp_lml_and_grad(X, y, alpha: float, rho: float, sigma: float, jitter: float = 0.0):
+    """Full oracle pass: K, chol, LML, Lbar, Kbar and hyperparameter gradient."""
+    K = se_cov(X, alpha, rho, sigma, jitter)
+    r = gp_lml(K, y)
+    Lbar = lml_lbar(r["L"], r["alpha"], r["z"], 1.0)
+    Kbar = chol_adjoint(r["L"], Lbar)
+    g = se_hyper_grad(X, alpha, rho, sigma, Kbar)
+    r.update({"K": K, "Lbar": Lbar, "Kbar": Kbar, "grad": g})
+    return r

@@ -1,0 +1,298 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: each test uses a closed form, a
+hand-computed value, a library routine for a special case (LAPACK through
+NumPy/SciPy), central finite differences, or an independent derivation.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.spatial.distance
+import scipy.stats
+
+from oracle import oracle as O
+from paper_1907_01063_gb300 import workloads as W
+
+U = np.finfo(np.float64).eps / 2
+
+
+def rel_fro(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def spd_se(n, d=3, seed=0, jitter=1e-6):
+    X = W.gp_inputs(n, d, seed)
+    return X, O.se_cov(X, 1.0, 1.0, 0.3, jitter)
+
+
+# ---------------------------------------------------------------- chol
+def test_chol_1x1():
+    assert O.chol([[4.0]])[0, 0] == 2.0
+    assert O.chol([[2.0]])[0, 0] == math.sqrt(2.0)
+
+
+def test_chol_2x2_by_hand():
+    # [[4,2],[2,5]] = [[2,0],[1,2]] [[2,1],[0,2]]
+    L = O.chol(np.array([[4.0, 2.0], [2.0, 5.0]]))
+    assert np.array_equal(L, np.array([[2.0, 0.0], [1.0, 2.0]]))
+
+
+def test_chol_3x3_by_hand():
+    # L = [[1,0,0],[2,3,0],[4,5,6]] -> K = L L^T
+    L0 = np.array([[1.0, 0, 0], [2, 3, 0], [4, 5, 6]])
+    K = np.array([[1.0, 2, 4], [2, 13, 23], [4, 23, 77]])
+    assert np.array_equal(O.chol(K), L0)
+
+
+def test_chol_identity_and_diagonal():
+    assert np.array_equal(O.chol(np.eye(7)), np.eye(7))
+    d = np.array([1.0, 4.0, 9.0, 0.25, 16.0])
+    assert np.array_equal(O.chol(np.diag(d)), np.diag(np.sqrt(d)))
+
+
+@pytest.mark.parametrize("n", [1, 5, 37, 64, 129])
+def test_chol_known_factor(n):
+    L0 = W.known_factor(n, seed=n)
+    K = L0 @ L0.T
+    L = O.chol(K)
+    # forward error bound ~ cond(L0) * n * u
+    assert rel_fro(L, L0) < 1e3 * n * U * np.linalg.cond(L0)
+    assert np.all(np.triu(L, 1) == 0)
+    # log det from the factor's diagonal
+    ld = 2.0 * np.log(np.diag(L)).sum()
+    assert abs(ld - 2.0 * np.log(np.diag(L0)).sum()) < 1e-12 * max(1.0, abs(ld))
+
+
+@pytest.mark.parametrize("n", [2, 50, 150])
+def test_chol_reconstruction(n):
+    _, K = spd_se(n)
+    L = O.chol(K)
+    assert rel_fro(L @ L.T, np.tril(K) + np.tril(K, -1).T) < 4 * n * U
+
+
+def test_chol_toeplitz_matches_lapack():
+    A = W.toeplitz_spd(60)
+    L = O.chol(A)
+    assert rel_fro(L, np.linalg.cholesky(A)) < 1e-14
+
+
+def test_chol_reads_lower_only():
+    _, K = spd_se(30)
+    K2 = np.tril(K) + np.triu(np.full_like(K, 123.0), 1)
+    assert np.array_equal(O.chol(K2), O.chol(np.tril(K) + np.tril(K, -1).T))
+
+
+def test_chol_failing_pivot():
+    _, info = O.chol_info(np.diag([1.0, -1.0, 1.0]))
+    assert info == 1
+    _, info = O.chol_info(np.array([[1.0, 2.0], [2.0, 1.0]]))  # s = 1 - 4 < 0
+    assert info == 1
+    K = np.eye(4)
+    K[2, 2] = np.nan
+    _, info = O.chol_info(K)
+    assert info == 2
+    _, info = O.chol_info(np.zeros((3, 3)))
+    assert info == 0
+    with pytest.raises(O.NotPositiveDefinite):
+        O.chol(np.diag([1.0, 0.0]))
+
+
+# ---------------------------------------------------------------- adjoint
+def chol_fd_grad(K, Wt, h_rel=1e-6):
+    """Central differences of f(K) = sum(W o chol(K)) over the lower entries."""
+    n = K.shape[0]
+    G = np.zeros_like(K)
+    for i in range(n):
+        for j in range(i + 1):
+            h = h_rel * max(1.0, abs(K[i, j]))
+            Kp = K.copy()
+            Km = K.copy()
+            Kp[i, j] += h
+            Km[i, j] -= h
+            G[i, j] = ((Wt * O.chol(Kp)).sum() - (Wt * O.chol(Km)).sum()) / (2 * h)
+    return G
+
+
+def test_adjoint_1x1():
+    L = O.chol([[9.0]])
+    assert O.chol_adjoint(L, [[6.0]])[0, 0] == 6.0 / (2 * 3.0)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 13, 16])
+def test_adjoint_finite_differences(n):
+    _, K = spd_se(n, seed=n, jitter=1e-2)
+    Wt = W.random_lower(n, seed=100 + n)
+    L = O.chol(K)
+    G = O.chol_adjoint(L, Wt)
+    Gfd = chol_fd_grad(K, Wt)
+    assert rel_fro(G, Gfd) < 1e-6
+    assert np.all(np.triu(G, 1) == 0)
+
+
+def test_adjoint_diagonal_matrix_closed_form():
+    d = np.array([4.0, 9.0, 0.25, 2.0])
+    L = np.diag(np.sqrt(d))
+    Lbar = W.random_lower(4, seed=3)
+    G = O.chol_adjoint(L, Lbar)
+    ref = np.zeros((4, 4))
+    for i in range(4):
+        for j in range(i):
+            ref[i, j] = Lbar[i, j] / L[j, j]
+        ref[i, i] = Lbar[i, i] / (2 * L[i, i])
+    assert rel_fro(G, ref) < 1e-15
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 100])
+def test_adjoint_unblocked_equals_symbolic(n):
+    _, K = spd_se(n, seed=7, jitter=1e-3)
+    L = O.chol(K)
+    Lbar = W.random_lower(n, seed=8)
+    a = O.chol_adjoint(L, Lbar)
+    s = O.chol_adjoint_symbolic(L, Lbar)
+    assert rel_fro(a, s) < 1e-10
+
+
+def blocked_adjoint_reading(L, Lbar, b):
+    """The block sweep of Section 3.3 (reverse mode) as read for this library.
+
+    Slices are half-open; k runs N, N-b, ... > 0 and j = max(0, k - b).  The
+    garbled last statement is read as "halve the diagonal of D_adj, then zero
+    its strict upper triangle".  This test-only NumPy version checks the
+    reading against the unblocked definition; it is not used anywhere else.
+    """
+    N = L.shape[0]
+    A = np.tril(Lbar).copy()
+    k = N
+    while k > 0:
+        j = max(0, k - b)
+        R, D, B, C = L[j:k, 0:j], L[j:k, j:k], L[k:N, 0:j], L[k:N, j:k]
+        Dinv = np.linalg.inv(D)
+        Cb = A[k:N, j:k] @ Dinv
+        A[k:N, j:k] = Cb
+        A[k:N, 0:j] -= Cb @ R
+        Db = A[j:k, j:k] - Cb.T @ C
+        P = D.T @ np.tril(Db)
+        M = np.tril(P) + np.tril(P, -1).T
+        Db = Dinv.T @ M @ Dinv
+        Db = 0.5 * (Db + Db.T)
+        A[j:k, 0:j] -= Cb.T @ B + Db @ R
+        Db = np.tril(Db)
+        Db[np.arange(k - j), np.arange(k - j)] *= 0.5
+        A[j:k, j:k] = Db
+        k -= b
+    return A
+
+
+@pytest.mark.parametrize("n,b", [(11, 3), (20, 8), (33, 16), (16, 16), (5, 8)])
+def test_blocked_sweep_reading_matches_oracle(n, b):
+    _, K = spd_se(n, seed=n + b, jitter=1e-3)
+    L = O.chol(K)
+    Lbar = W.random_lower(n, seed=5)
+    ref = O.chol_adjoint(L, Lbar)
+    assert rel_fro(blocked_adjoint_reading(L, Lbar, b), ref) < 1e-11
+
+
+# ---------------------------------------------------------------- covariance
+def test_se_cov_two_points_by_hand():
+    K = O.se_cov(np.array([[0.0], [1.0]]), 2.0, 1.0, 0.5, 0.0, full=True)
+    assert K[0, 0] == 4.25 and K[1, 1] == 4.25
+    assert abs(K[1, 0] - 4.0 * math.exp(-0.5)) < 1e-15
+    assert K[0, 1] == K[1, 0]
+
+
+def test_se_cov_matches_cdist():
+    X = W.gp_inputs(50, 3, seed=2)
+    K = O.se_cov(X, 1.3, 0.7, 0.2, 1e-8, full=True)
+    D2 = scipy.spatial.distance.cdist(X, X, "sqeuclidean")
+    ref = 1.3 ** 2 * np.exp(-D2 / (2 * 0.7 ** 2)) + np.eye(50) * (0.2 ** 2 + 1e-8)
+    assert rel_fro(K, ref) < 1e-14
+    Kl = O.se_cov(X, 1.3, 0.7, 0.2, 1e-8, full=False)
+    assert np.all(np.triu(Kl, 1) == 0) and np.array_equal(np.tril(Kl), np.tril(K))
+
+
+# ---------------------------------------------------------------- solves, LML
+def test_trsv_matches_lapack():
+    L0 = W.known_factor(40, seed=1)
+    x = W.gp_inputs(40, 1, seed=2)[:, 0]
+    for trans in (False, True):
+        ref = scipy.linalg.solve_triangular(L0, x, lower=True, trans=1 if trans else 0)
+        assert rel_fro(O.trsv(L0, x, trans), ref) < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 3, 40, 200])
+def test_lml_matches_scipy_logpdf(n):
+    X = W.gp_inputs(n, 2, seed=n)
+    y = W.gp_targets(X, 1.0, 0.5, 0.1, seed=n + 1)
+    K = O.se_cov(X, 1.0, 0.5, 0.1, 1e-8, full=True)
+    r = O.gp_lml(K, y)
+    ref = scipy.stats.multivariate_normal(mean=np.zeros(n), cov=K).logpdf(y)
+    assert abs(r["value"] - ref) < 1e-9 * max(1.0, abs(ref))
+    sign, ld = np.linalg.slogdet(K)
+    assert sign > 0 and abs(r["logdet"] - ld) < 1e-10 * max(1.0, abs(ld))
+    assert rel_fro(r["alpha"], np.linalg.solve(K, y)) < 1e-8
+
+
+def test_lml_lbar_finite_differences():
+    n = 6
+    _, K = spd_se(n, seed=4, jitter=1e-2)
+    y = W.gp_inputs(n, 1, seed=9)[:, 0]
+    r = O.gp_lml(K, y)
+    L = r["L"]
+
+    def value_of_L(Lm):
+        z = scipy.linalg.solve_triangular(Lm, y, lower=True)
+        return -0.5 * z @ z - np.log(np.diag(Lm)).sum()
+
+    G = np.zeros((n, n))
+    h = 1e-6
+    for i in range(n):
+        for j in range(i + 1):
+            Lp, Lm = L.copy(), L.copy()
+            Lp[i, j] += h
+            Lm[i, j] -= h
+            G[i, j] = (value_of_L(Lp) - value_of_L(Lm)) / (2 * h)
+    Lbar = O.lml_lbar(L, r["alpha"], r["z"], 1.0)
+    assert rel_fro(Lbar, G) < 1e-7
+    assert rel_fro(O.lml_lbar(L, r["alpha"], r["z"], -2.5), -2.5 * G) < 1e-7
+
+
+@pytest.mark.parametrize("n", [1, 10, 120])
+def test_lml_kbar_closed_form(n):
+    X = W.gp_inputs(n, 2, seed=3)
+    y = W.gp_targets(X, 1.0, 0.5, 0.1, seed=4)
+    K = O.se_cov(X, 1.0, 0.5, 0.1, 1e-8, full=True)
+    r = O.gp_lml(K, y)
+    Kbar = O.chol_adjoint(r["L"], O.lml_lbar(r["L"], r["alpha"], r["z"]))
+    a = np.linalg.solve(K, y)
+    Kinv = np.linalg.inv(K)
+    G = np.outer(a, a) - Kinv          # off-diagonal: d value / d K_ij (pair i,j)
+    ref = np.tril(G, -1) + np.diag(0.5 * np.diag(G))
+    assert rel_fro(Kbar, ref) < 1e-8
+
+
+def test_hyper_grad_finite_differences():
+    n = 40
+    X = W.gp_inputs(n, 3, seed=11)
+    hyp = np.array([1.2, 0.9, 0.3])
+    y = W.gp_targets(X, *hyp, seed=12)
+
+    def value(h):
+        return O.gp_lml(O.se_cov(X, h[0], h[1], h[2], 1e-8), y)["value"]
+
+    r = O.gp_lml_and_grad(X, y, *hyp, jitter=1e-8)
+    fd = np.zeros(3)
+    for t in range(3):
+        e = np.zeros(3)
+        e[t] = 1e-6
+        fd[t] = (value(hyp + e) - value(hyp - e)) / 2e-6
+    assert np.allclose(r["grad"], fd, rtol=1e-6, atol=1e-6)
+
+
+def test_hyper_grad_sigma_only_on_diagonal():
+    n = 5
+    X = W.gp_inputs(n, 2, seed=1)
+    Kbar = np.tril(np.ones((n, n)))
+    g = O.se_hyper_grad(X, 1.0, 1.0, 0.25, Kbar)
+    assert abs(g[2] - n * 2 * 0.25) < 1e-15
