@@ -133,8 +133,10 @@ int gpc_chol_adjoint(int n, const double *L, int ldl, const double *Lbar, int ld
 /*
  * Triangular solve with the lower factor L (Section 3.2):
  *   trans == 0: x <- L^{-1} x      trans != 0: x <- L^{-T} x
- * x is a device vector of n doubles, overwritten.  ws/ws_bytes: at least
- * gpc_workspace_size(n, GPC_FP64) bytes.
+ * x is a device vector of n doubles, overwritten.  ws/ws_bytes: scratch for
+ * the solve's ready flags; gpc_workspace_size(n, GPC_FP64) bytes always
+ * suffice.  Each 64-row block waits (bounded) on the blocks before it; a
+ * wait that gives up leaves x unspecified.
  */
 int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, size_t ws_bytes,
              gpc_stream_t stream);
@@ -168,10 +170,16 @@ int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double
  *   d K_ij/d alpha = 2 K^f_ij / alpha, d K_ij/d rho = K^f_ij r2_ij / rho^3,
  *   d K_ii/d sigma = 2 sigma   (K^f: the noise-free part; jitter is constant),
  * summed over i >= j.  K^f is recomputed from X; grad3: 3 device doubles.
+ * The sums are formed per tile and then added in a fixed order, so repeated
+ * calls give bitwise-identical results.  ws/ws_bytes: at least
+ * gpc_se_hyper_grad_workspace_size(n) bytes.  Requires alpha != 0, rho > 0.
  */
 int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, double rho,
-                      double sigma, const double *Kbar, int ldkb, double *grad3,
-                      gpc_stream_t stream);
+                      double sigma, const double *Kbar, int ldkb, double *grad3, void *ws,
+                      size_t ws_bytes, gpc_stream_t stream);
+
+/* Workspace bytes gpc_se_hyper_grad needs at order n (*bytes: host pointer). */
+int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes);
 
 #ifdef __cplusplus
 }

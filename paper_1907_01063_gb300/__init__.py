@@ -1,1 +1,365 @@
-"""GB300 Cholesky / Cholesky-adjoint / GP-likelihood library (binding placeholder)."""
+"""GB300 (sm_103a) Cholesky, Cholesky adjoint and Gaussian-process likelihood.
+
+Python binding of libgpchol.so (C ABI in include/gpchol.h).  The binding only
+marshals arguments: every step runs in the library's CUDA kernels on the
+current torch stream.  PyTorch supplies device memory and streams.
+
+Two layers:
+  * ``capi`` -- the C entry points with their C names (``capi.gpc_chol`` ...),
+    taking raw integers for pointers and streams;
+  * tensor functions with the same names minus the prefix (``chol``,
+    ``chol_adjoint``, ``gp_lml`` ...) and the autograd functions ``Chol`` and
+    ``GPLml``.
+There is no CPU fallback: without the compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import torch
+
+from . import build as _build
+
+GPC_OK = 0
+GPC_ERR_INVALID_ARG = 1
+GPC_ERR_NOT_PD = 2
+GPC_ERR_NAN = 3
+GPC_ERR_CUDA = 4
+GPC_ERR_TIMEOUT = 5
+GPC_ERR_NO_CONVERGENCE = 6
+GPC_FP64 = 0
+GPC_MIXED = 1
+GPC_TUNE_BLOCK = 0
+GPC_TUNE_SLICES = 1
+GPC_TUNE_SPLITK_MIN = 2
+
+PRECISIONS = {"fp64": GPC_FP64, "mixed": GPC_MIXED, GPC_FP64: GPC_FP64, GPC_MIXED: GPC_MIXED}
+
+_c_int, _c_double, _c_size, _c_vp = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+
+# name -> (argtypes, restype)
+_SIGNATURES = {
+    "gpc_status_string": ([_c_int], ctypes.c_char_p),
+    "gpc_version": ([], _c_int),
+    "gpc_workspace_size": ([_c_int, _c_int, ctypes.POINTER(_c_size)], _c_int),
+    "gpc_set_tuning": ([_c_int, _c_int], _c_int),
+    "gpc_get_tuning": ([_c_int, ctypes.POINTER(_c_int)], _c_int),
+    "gpc_se_cov": ([_c_int, _c_int, _c_vp, _c_int, _c_double, _c_double, _c_double, _c_double,
+                    _c_vp, _c_int, _c_int, _c_vp], _c_int),
+    "gpc_chol": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_int, _c_vp, _c_size, _c_vp, _c_vp], _c_int),
+    "gpc_chol_adjoint": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_int, _c_int,
+                          _c_vp, _c_size, _c_vp], _c_int),
+    "gpc_trsv": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_size, _c_vp], _c_int),
+    "gpc_gp_lml": ([_c_int, _c_vp, _c_int, _c_vp, _c_vp, _c_int, _c_int, _c_vp, _c_vp, _c_vp,
+                    _c_vp, _c_size, _c_vp, _c_vp], _c_int),
+    "gpc_gp_lml_grad": ([_c_int, _c_vp, _c_int, _c_vp, _c_double, _c_vp, _c_int, _c_int, _c_vp,
+                         _c_size, _c_vp], _c_int),
+    "gpc_se_hyper_grad": ([_c_int, _c_int, _c_vp, _c_int, _c_double, _c_double, _c_double, _c_vp,
+                           _c_int, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
+    "gpc_se_hyper_grad_workspace_size": ([_c_int, ctypes.POINTER(_c_size)], _c_int),
+}
+
+
+class GpcholError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)}")
+        self.status = status
+
+
+class NotPositiveDefinite(GpcholError):
+    def __init__(self, status: int, pivot: int):
+        super().__init__(status, f"factorisation failed at pivot {pivot}")
+        self.pivot = pivot
+
+
+class _CApi:
+    """The C entry points, loaded on first use."""
+
+    def __init__(self):
+        self._lib = None
+
+    def load(self):
+        if self._lib is None:
+            path = library_path()
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            self._lib = lib
+        return self._lib
+
+    def __getattr__(self, name):
+        if name.startswith("gpc_"):
+            return getattr(self.load(), name)
+        raise AttributeError(name)
+
+
+capi = _CApi()
+
+
+def library_path(build_if_missing: bool = True) -> str:
+    """Path of the compiled library, building it with nvcc when missing."""
+    if os.path.exists(_build.LIB):
+        return _build.LIB
+    if not build_if_missing:
+        raise FileNotFoundError(f"{_build.LIB} is missing; run paper_1907_01063_gb300.build.build()")
+    return _build.build()
+
+
+def status_string(status: int) -> str:
+    return capi.gpc_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != GPC_OK:
+        raise GpcholError(status, what)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _square(t: torch.Tensor, name: str) -> int:
+    if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 2 and t.shape[0] == t.shape[1]):
+        raise ValueError(f"{name} must be a square float64 CUDA tensor")
+    if t.shape[0] > 0 and t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (stride(1) == 1)")
+    return int(t.stride(0)) if t.shape[0] > 0 else 1
+
+
+def _vector(t: torch.Tensor, n: int, name: str):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 1 and t.shape[0] == n
+            and (n == 0 or t.stride(0) == 1)):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA vector of length {n}")
+
+
+def precision_code(precision) -> int:
+    try:
+        return PRECISIONS[precision]
+    except KeyError:
+        raise ValueError(f"unknown precision {precision!r}") from None
+
+
+def set_tuning(key: int, value: int):
+    _check(capi.gpc_set_tuning(key, int(value)), "gpc_set_tuning")
+
+
+def get_tuning(key: int) -> int:
+    v = ctypes.c_int()
+    _check(capi.gpc_get_tuning(key, ctypes.byref(v)), "gpc_get_tuning")
+    return v.value
+
+
+def workspace_size(n: int, precision="fp64") -> int:
+    b = ctypes.c_size_t()
+    _check(capi.gpc_workspace_size(int(n), precision_code(precision), ctypes.byref(b)),
+           "gpc_workspace_size")
+    return b.value
+
+
+def workspace(n: int, precision="fp64", device=None) -> torch.Tensor:
+    """A byte tensor large enough for any call at order <= n."""
+    return torch.empty(workspace_size(n, precision), dtype=torch.uint8,
+                       device=device if device is not None else "cuda")
+
+
+def new_info(device=None) -> torch.Tensor:
+    return torch.full((2,), -1, dtype=torch.int32, device=device if device is not None else "cuda")
+
+
+def check_info(info: torch.Tensor, what: str = "factorisation"):
+    """Synchronises on info (2 device ints) and raises on a device-side failure."""
+    pivot, status = (int(v) for v in info.tolist())
+    if status in (GPC_ERR_NOT_PD, GPC_ERR_NAN):
+        raise NotPositiveDefinite(status, pivot)
+    if status != GPC_OK:
+        raise GpcholError(status, what)
+
+
+def _ws_for(n: int, precision, ws: torch.Tensor | None, device) -> torch.Tensor:
+    need = workspace_size(n, precision)
+    if ws is None:
+        return torch.empty(need, dtype=torch.uint8, device=device)
+    if ws.numel() * ws.element_size() < need or not ws.is_cuda:
+        raise ValueError(f"workspace too small: need {need} bytes")
+    return ws
+
+
+# ---------------------------------------------------------------- tensor API
+def se_cov(X: torch.Tensor, alpha: float, rho: float, sigma: float, jitter: float = 0.0,
+           full: bool = False, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Squared-exponential covariance of the rows of X (lower triangle, or full)."""
+    if not (X.is_cuda and X.dtype == torch.float64 and X.dim() == 2 and X.stride(1) == 1):
+        raise ValueError("X must be a row-major float64 CUDA matrix")
+    n, d = X.shape
+    K = out if out is not None else torch.zeros(n, n, dtype=torch.float64, device=X.device)
+    ldk = _square(K, "K")
+    _check(capi.gpc_se_cov(n, d, _ptr(X), max(int(X.stride(0)), d), float(alpha), float(rho),
+                           float(sigma), float(jitter), _ptr(K), ldk, 1 if full else 0, _stream()),
+           "gpc_se_cov")
+    return K
+
+
+def chol(K: torch.Tensor, precision="fp64", out: torch.Tensor | None = None,
+         ws: torch.Tensor | None = None, info: torch.Tensor | None = None,
+         check: bool = True) -> torch.Tensor:
+    """Lower Cholesky factor of the SPD matrix whose lower triangle is in K."""
+    n = K.shape[0]
+    ldk = _square(K, "K")
+    L = out if out is not None else torch.empty_like(K)
+    ldl = _square(L, "L")
+    wsb = _ws_for(n, precision, ws, K.device)
+    inf = info if info is not None else new_info(K.device)
+    _check(capi.gpc_chol(n, _ptr(K), ldk, _ptr(L), ldl, precision_code(precision), _ptr(wsb),
+                         wsb.numel(), _ptr(inf), _stream()), "gpc_chol")
+    if check:
+        check_info(inf, "gpc_chol")
+    return L
+
+
+def chol_adjoint(L: torch.Tensor, Lbar: torch.Tensor, precision="fp64", symmetric_out: bool = False,
+                 out: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """Kbar from L and Lbar (reverse mode of chol); lower convention unless symmetric_out."""
+    n = L.shape[0]
+    ldl = _square(L, "L")
+    ldlb = _square(Lbar, "Lbar")
+    Kbar = out if out is not None else torch.empty_like(Lbar)
+    ldkb = _square(Kbar, "Kbar")
+    wsb = _ws_for(n, precision, ws, L.device)
+    _check(capi.gpc_chol_adjoint(n, _ptr(L), ldl, _ptr(Lbar), ldlb, _ptr(Kbar), ldkb,
+                                 precision_code(precision), 1 if symmetric_out else 0, _ptr(wsb),
+                                 wsb.numel(), _stream()), "gpc_chol_adjoint")
+    return Kbar
+
+
+def trsv(L: torch.Tensor, x: torch.Tensor, trans: bool = False,
+         ws: torch.Tensor | None = None) -> torch.Tensor:
+    """x <- L^{-1} x (or L^{-T} x), in place; returns x."""
+    n = L.shape[0]
+    ldl = _square(L, "L")
+    _vector(x, n, "x")
+    wsb = _ws_for(n, "fp64", ws, L.device)
+    _check(capi.gpc_trsv(n, _ptr(L), ldl, _ptr(x), 1 if trans else 0, _ptr(wsb), wsb.numel(),
+                         _stream()), "gpc_trsv")
+    return x
+
+
+def gp_lml(K: torch.Tensor, y: torch.Tensor, precision="fp64", L: torch.Tensor | None = None,
+           ws: torch.Tensor | None = None, info: torch.Tensor | None = None, check: bool = True):
+    """Log marginal likelihood of y ~ N(0, K): returns dict(L, alpha, logdet, value).
+
+    logdet and value are 0-d device tensors (no host synchronisation unless
+    ``check`` reads the info flags).
+    """
+    n = K.shape[0]
+    ldk = _square(K, "K")
+    _vector(y, n, "y")
+    Lt = L if L is not None else torch.empty_like(K)
+    ldl = _square(Lt, "L")
+    alpha = torch.empty(n, dtype=torch.float64, device=K.device)
+    scal = torch.empty(2, dtype=torch.float64, device=K.device)
+    wsb = _ws_for(n, precision, ws, K.device)
+    inf = info if info is not None else new_info(K.device)
+    _check(capi.gpc_gp_lml(n, _ptr(K), ldk, _ptr(y), _ptr(Lt), ldl, precision_code(precision),
+                           scal.data_ptr(), _ptr(alpha), scal.data_ptr() + 8, _ptr(wsb), wsb.numel(),
+                           _ptr(inf), _stream()), "gpc_gp_lml")
+    if check:
+        check_info(inf, "gpc_gp_lml")
+    return {"L": Lt, "alpha": alpha, "logdet": scal[0], "value": scal[1], "info": inf}
+
+
+def gp_lml_grad(L: torch.Tensor, alpha: torch.Tensor, gbar: float = 1.0, precision="fp64",
+                out: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """Kbar = gbar * d value / dK (lower convention) through the Cholesky adjoint."""
+    n = L.shape[0]
+    ldl = _square(L, "L")
+    _vector(alpha, n, "alpha")
+    Kbar = out if out is not None else torch.empty_like(L)
+    ldkb = _square(Kbar, "Kbar")
+    wsb = _ws_for(n, precision, ws, L.device)
+    _check(capi.gpc_gp_lml_grad(n, _ptr(L), ldl, _ptr(alpha), float(gbar), _ptr(Kbar), ldkb,
+                                precision_code(precision), _ptr(wsb), wsb.numel(), _stream()),
+           "gpc_gp_lml_grad")
+    return Kbar
+
+
+def se_hyper_grad_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t()
+    _check(capi.gpc_se_hyper_grad_workspace_size(int(n), ctypes.byref(b)),
+           "gpc_se_hyper_grad_workspace_size")
+    return b.value
+
+
+def se_hyper_grad(X: torch.Tensor, alpha: float, rho: float, sigma: float, Kbar: torch.Tensor,
+                  ws: torch.Tensor | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """(d/d alpha, d/d rho, d/d sigma) as a 3-vector on the device."""
+    n, d = X.shape
+    ldkb = _square(Kbar, "Kbar")
+    g = out if out is not None else torch.empty(3, dtype=torch.float64, device=X.device)
+    need = se_hyper_grad_workspace_size(n)
+    wsb = ws if ws is not None else torch.empty(need, dtype=torch.uint8, device=X.device)
+    _check(capi.gpc_se_hyper_grad(n, d, _ptr(X), max(int(X.stride(0)), d), float(alpha), float(rho),
+                                  float(sigma), _ptr(Kbar), ldkb, _ptr(g), _ptr(wsb),
+                                  wsb.numel() * wsb.element_size(), _stream()),
+           "gpc_se_hyper_grad")
+    return g
+
+
+# ---------------------------------------------------------------- autograd
+class Chol(torch.autograd.Function):
+    """L = chol(K) with the blocked adjoint as backward.
+
+    The gradient returned for K is the lower-convention Kbar: entry (i, j),
+    i >= j, is d f / d K_ij over the entries chol reads; the upper triangle of
+    K does not influence L and gets zero gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, K, precision="fp64"):
+        L = chol(K.detach(), precision)
+        ctx.precision = precision
+        ctx.save_for_backward(L)
+        return L
+
+    @staticmethod
+    def backward(ctx, Lbar):
+        (L,) = ctx.saved_tensors
+        Lbar = torch.tril(Lbar.contiguous())
+        return chol_adjoint(L, Lbar, ctx.precision), None
+
+
+class GPLml(torch.autograd.Function):
+    """Log marginal likelihood of y under an SE-kernel GP, differentiable in
+    (alpha, rho, sigma); K is rebuilt on the device and only L and alpha are
+    kept for the backward pass."""
+
+    @staticmethod
+    def forward(ctx, X, y, hyp, jitter=0.0, precision="fp64"):
+        a, r, s = (float(v) for v in hyp.detach().cpu().tolist())
+        K = se_cov(X, a, r, s, jitter)
+        res = gp_lml(K, y, precision, L=K if precision_code(precision) == GPC_FP64 else None)
+        ctx.save_for_backward(X, res["L"], res["alpha"])
+        ctx.hyp = (a, r, s)
+        ctx.hyp_device = hyp.device
+        ctx.precision = precision
+        return res["value"].clone()
+
+    @staticmethod
+    def backward(ctx, gvalue):
+        X, L, alpha = ctx.saved_tensors
+        a, r, s = ctx.hyp
+        Kbar = gp_lml_grad(L, alpha, 1.0, ctx.precision)
+        g = se_hyper_grad(X, a, r, s, Kbar)
+        return None, None, (g * gvalue).to(ctx.hyp_device), None, None
+
+
+def gp_lml_value(X, y, hyp, jitter=0.0, precision="fp64"):
+    """Differentiable log marginal likelihood; hyp = tensor([alpha, rho, sigma])."""
+    return GPLml.apply(X, y, hyp, jitter, precision)

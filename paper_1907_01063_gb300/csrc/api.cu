@@ -1,0 +1,246 @@
+// C ABI of libgpchol: argument checks, workspace layout and the launch
+// sequence of each entry point.  Every step of each call runs in this
+// library's kernels on the caller's stream.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace gpc {
+
+Tuning &tuning() {
+  static Tuning t;
+  return t;
+}
+
+int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+namespace {
+
+struct ApiWs {
+  void *core;
+  double *vec;  // 4 n doubles
+  int *flags;   // triangular-solve tickets and ready flags
+};
+
+size_t core_bytes(int n, int precision) {
+  size_t c = std::max(chol_workspace_bytes(n, precision), adjoint_workspace_bytes(n, precision));
+  c = std::max(c, ltv_workspace_bytes(n));
+  return align_up(c, 256);
+}
+
+size_t total_bytes(int n, int precision) {
+  return core_bytes(n, precision) + align_up(4 * (size_t)std::max(n, 1) * sizeof(double), 256) +
+         trsv_workspace_bytes(std::max(n, 1));
+}
+
+ApiWs carve(void *ws, int n, int precision) {
+  ApiWs w;
+  char *p = (char *)ws;
+  w.core = p;
+  p += core_bytes(n, precision);
+  w.vec = (double *)p;
+  p += align_up(4 * (size_t)std::max(n, 1) * sizeof(double), 256);
+  w.flags = (int *)p;
+  return w;
+}
+
+int status_of(cudaError_t e) { return e == cudaSuccess ? GPC_OK : GPC_ERR_CUDA; }
+
+bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes) {
+  const char *pa = (const char *)a, *pb = (const char *)b;
+  return pa < pb + bbytes && pb < pa + abytes;
+}
+
+size_t mat_bytes(int n, int ld) { return n > 0 ? ((size_t)(n - 1) * ld + n) * sizeof(double) : 0; }
+
+bool bad_square(int n, const void *p, int ld) { return n > 0 && (p == nullptr || ld < n); }
+
+}  // namespace
+}  // namespace gpc
+
+using namespace gpc;
+
+extern "C" {
+
+const char *gpc_status_string(int status) {
+  switch (status) {
+    case GPC_OK: return "GPC_OK: success";
+    case GPC_ERR_INVALID_ARG: return "GPC_ERR_INVALID_ARG: invalid argument";
+    case GPC_ERR_NOT_PD: return "GPC_ERR_NOT_PD: matrix is not positive definite";
+    case GPC_ERR_NAN: return "GPC_ERR_NAN: NaN or infinite pivot";
+    case GPC_ERR_CUDA: return "GPC_ERR_CUDA: CUDA launch or runtime error";
+    case GPC_ERR_TIMEOUT: return "GPC_ERR_TIMEOUT: bounded device wait gave up";
+    case GPC_ERR_NO_CONVERGENCE: return "GPC_ERR_NO_CONVERGENCE: refinement above tolerance";
+    default: return "unknown gpchol status";
+  }
+}
+
+int gpc_version(void) { return 100; }
+
+int gpc_set_tuning(int key, int value) {
+  switch (key) {
+    case GPC_TUNE_BLOCK:
+      if (value < 16 || value > kMaxBlock || value % 16) return GPC_ERR_INVALID_ARG;
+      tuning().block = value;
+      return GPC_OK;
+    case GPC_TUNE_SLICES:
+      if (value < 3 || value > 8) return GPC_ERR_INVALID_ARG;
+      tuning().slices = value;
+      return GPC_OK;
+    case GPC_TUNE_SPLITK_MIN:
+      if (value < 16 || value > (1 << 20)) return GPC_ERR_INVALID_ARG;
+      tuning().splitk_min = value;
+      return GPC_OK;
+    default:
+      return GPC_ERR_INVALID_ARG;
+  }
+}
+
+int gpc_get_tuning(int key, int *value) {
+  if (!value) return GPC_ERR_INVALID_ARG;
+  switch (key) {
+    case GPC_TUNE_BLOCK: *value = tuning().block; return GPC_OK;
+    case GPC_TUNE_SLICES: *value = tuning().slices; return GPC_OK;
+    case GPC_TUNE_SPLITK_MIN: *value = tuning().splitk_min; return GPC_OK;
+    default: return GPC_ERR_INVALID_ARG;
+  }
+}
+
+int gpc_workspace_size(int n, int precision, size_t *bytes) {
+  if (!bytes || n < 0 || (precision != GPC_FP64 && precision != GPC_MIXED)) return GPC_ERR_INVALID_ARG;
+  *bytes = total_bytes(n, precision);
+  return GPC_OK;
+}
+
+int gpc_se_cov(int n, int d, const double *X, int ldx, double alpha, double rho, double sigma,
+               double jitter, double *K, int ldk, int full, gpc_stream_t stream) {
+  if (n < 0 || d < 1 || d > kMaxDim) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (!X || ldx < d || bad_square(n, K, ldk) || !(rho > 0.0)) return GPC_ERR_INVALID_ARG;
+  return status_of(se_cov(n, d, X, ldx, alpha, rho, sigma, jitter, K, ldk, full, stream));
+}
+
+int gpc_chol(int n, const double *K, int ldk, double *L, int ldl, int precision, void *ws,
+             size_t ws_bytes, int *info, gpc_stream_t stream) {
+  if (n < 0 || precision != GPC_FP64 || !info) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return status_of(reset_info(info, stream));
+  if (bad_square(n, K, ldk) || bad_square(n, L, ldl) || !ws || ws_bytes < total_bytes(n, precision))
+    return GPC_ERR_INVALID_ARG;
+  if ((const void *)K == (const void *)L) {
+    if (ldk != ldl) return GPC_ERR_INVALID_ARG;
+  } else if (overlaps(K, mat_bytes(n, ldk), L, mat_bytes(n, ldl))) {
+    return GPC_ERR_INVALID_ARG;
+  }
+  ApiWs w = carve(ws, n, precision);
+  cudaError_t e = reset_info(info, stream);
+  if (e == cudaSuccess) e = copy_lower(n, K, ldk, L, ldl, stream);
+  if (e == cudaSuccess) e = chol_fp64(n, L, ldl, w.core, info, stream);
+  return status_of(e);
+}
+
+int gpc_chol_adjoint(int n, const double *L, int ldl, const double *Lbar, int ldlb, double *Kbar,
+                     int ldkb, int precision, int symmetric_out, void *ws, size_t ws_bytes,
+                     gpc_stream_t stream) {
+  if (n < 0 || precision != GPC_FP64) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (bad_square(n, L, ldl) || bad_square(n, Lbar, ldlb) || bad_square(n, Kbar, ldkb) || !ws ||
+      ws_bytes < total_bytes(n, precision))
+    return GPC_ERR_INVALID_ARG;
+  if ((const void *)Lbar == (const void *)Kbar) {
+    if (ldlb != ldkb) return GPC_ERR_INVALID_ARG;
+  } else if (overlaps(Lbar, mat_bytes(n, ldlb), Kbar, mat_bytes(n, ldkb))) {
+    return GPC_ERR_INVALID_ARG;
+  }
+  if (overlaps(L, mat_bytes(n, ldl), Kbar, mat_bytes(n, ldkb))) return GPC_ERR_INVALID_ARG;
+  ApiWs w = carve(ws, n, precision);
+  cudaError_t e = copy_lower(n, Lbar, ldlb, Kbar, ldkb, stream);
+  if (e == cudaSuccess) e = chol_adjoint_fp64(n, L, ldl, Kbar, ldkb, w.core, stream);
+  if (e == cudaSuccess && symmetric_out) e = lower_to_symmetric_half(n, Kbar, ldkb, stream);
+  return status_of(e);
+}
+
+int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, size_t ws_bytes,
+             gpc_stream_t stream) {
+  if (n < 0) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (bad_square(n, L, ldl) || !x || !ws || ws_bytes < trsv_workspace_bytes(n)) return GPC_ERR_INVALID_ARG;
+  return status_of(trsv(n, L, ldl, x, trans, ws, nullptr, stream));
+}
+
+int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int ldl,
+               int precision, double *logdet, double *alpha, double *value, void *ws,
+               size_t ws_bytes, int *info, gpc_stream_t stream) {
+  if (n < 0 || precision != GPC_FP64 || !info || !logdet || !value) return GPC_ERR_INVALID_ARG;
+  if (n == 0) {
+    cudaError_t e = reset_info(info, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(logdet, 0, sizeof(double), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(value, 0, sizeof(double), stream);
+    return status_of(e);
+  }
+  if (bad_square(n, K, ldk) || bad_square(n, L, ldl) || !y || !alpha || !ws ||
+      ws_bytes < total_bytes(n, precision))
+    return GPC_ERR_INVALID_ARG;
+  if ((const void *)K == (const void *)L) {
+    if (ldk != ldl) return GPC_ERR_INVALID_ARG;
+  } else if (overlaps(K, mat_bytes(n, ldk), L, mat_bytes(n, ldl))) {
+    return GPC_ERR_INVALID_ARG;
+  }
+  if (overlaps(alpha, n * sizeof(double), L, mat_bytes(n, ldl)) ||
+      overlaps(alpha, n * sizeof(double), y, n * sizeof(double)))
+    return GPC_ERR_INVALID_ARG;
+  ApiWs w = carve(ws, n, precision);
+  cudaError_t e = reset_info(info, stream);
+  if (e == cudaSuccess) e = copy_lower(n, K, ldk, L, ldl, stream);
+  if (e == cudaSuccess) e = chol_fp64(n, L, ldl, w.core, info, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(alpha, y, n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+  if (e == cudaSuccess) e = trsv(n, L, ldl, alpha, 0, w.flags, info, stream);
+  if (e == cudaSuccess) e = trsv(n, L, ldl, alpha, 1, w.flags, info, stream);
+  if (e == cudaSuccess) e = lml_finalize(n, L, ldl, y, alpha, logdet, value, stream);
+  return status_of(e);
+}
+
+int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double gbar,
+                    double *Kbar, int ldkb, int precision, void *ws, size_t ws_bytes,
+                    gpc_stream_t stream) {
+  if (n < 0 || precision != GPC_FP64) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (bad_square(n, L, ldl) || bad_square(n, Kbar, ldkb) || !alpha || !ws ||
+      ws_bytes < total_bytes(n, precision))
+    return GPC_ERR_INVALID_ARG;
+  if (overlaps(L, mat_bytes(n, ldl), Kbar, mat_bytes(n, ldkb))) return GPC_ERR_INVALID_ARG;
+  ApiWs w = carve(ws, n, precision);
+  double *z = w.vec;
+  cudaError_t e = ltv(n, L, ldl, alpha, z, w.core, stream);
+  if (e == cudaSuccess) e = lml_lbar(n, L, ldl, alpha, z, gbar, Kbar, ldkb, stream);
+  if (e == cudaSuccess) e = chol_adjoint_fp64(n, L, ldl, Kbar, ldkb, w.core, stream);
+  return status_of(e);
+}
+
+int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, double rho,
+                      double sigma, const double *Kbar, int ldkb, double *grad3, void *ws,
+                      size_t ws_bytes, gpc_stream_t stream) {
+  if (n < 0 || d < 1 || d > kMaxDim || !grad3) return GPC_ERR_INVALID_ARG;
+  if (n > 0 && (!X || ldx < d || bad_square(n, Kbar, ldkb) || !(rho > 0.0) || !(alpha != 0.0) ||
+                !ws || ws_bytes < se_hyper_grad_workspace_bytes(n)))
+    return GPC_ERR_INVALID_ARG;
+  return status_of(se_hyper_grad(n, d, X, ldx, alpha, rho, sigma, Kbar, ldkb, grad3, ws, stream));
+}
+
+int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes) {
+  if (n < 0 || !bytes) return GPC_ERR_INVALID_ARG;
+  *bytes = se_hyper_grad_workspace_bytes(std::max(n, 1));
+  return GPC_OK;
+}
+
+}  // extern "C"

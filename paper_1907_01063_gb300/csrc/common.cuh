@@ -1,0 +1,105 @@
+// Internal declarations shared by the CUDA translation units of libgpchol.
+// Nothing here is part of the public C ABI (include/gpchol.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/gpchol.h"
+
+namespace gpc {
+
+// ---------------------------------------------------------------- tuning
+struct Tuning {
+  int block = 128;        // b: block size of the blocked factorisation / adjoint
+  int slices = 6;         // BF16 slices per FP64 operand on the mixed path
+  int splitk_min = 512;   // minimum K per split of a split-K product
+};
+Tuning &tuning();
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// ---------------------------------------------------------------- FP64 GEMM
+// C = beta * C + alpha * op(A) * op(B), row-major, op(A) M x K, op(B) K x N.
+// transA: A is stored K x M (element (m,k) at A[k*lda + m]); else M x K.
+// transB: B is stored N x K (element (k,n) at B[n*ldb + k]); else K x N.
+// uplo: 0 full; 1 lower triangle only (M == N, entries with col > row are
+// neither computed nor touched); 2 lower, mirrored into the upper triangle.
+// beta == 0 never reads C.
+enum { UPLO_FULL = 0, UPLO_LOWER = 1, UPLO_LOWER_MIRROR = 2 };
+struct Gemm {
+  int M = 0, N = 0, K = 0;
+  bool transA = false, transB = false;
+  double alpha = 1.0, beta = 0.0;
+  const double *A = nullptr;
+  long long lda = 0;
+  const double *B = nullptr;
+  long long ldb = 0;
+  double *C = nullptr;
+  long long ldc = 0;
+  int uplo = UPLO_FULL;
+};
+// Bytes of split-K scratch any gemm_f64 call may use (a fixed cap).
+size_t gemm_f64_scratch_bytes();
+cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s);
+
+// ---------------------------------------------------------------- diagonal blocks
+constexpr int kMaxBlock = 128;
+// Factor the nb x nb lower block at A (in place, upper part of the block set
+// to zero) and write its inverse (lower, ld = nb) to Winv.  On a failing
+// pivot p records {pivot_offset + p, status} in info if info[1] is still 0.
+cudaError_t potrf_trtri_diag(int nb, double *A, long long lda, double *Winv, int *info,
+                             int pivot_offset, cudaStream_t s);
+// Inverse (lower, ld = nb) of the nb x nb lower block D.
+cudaError_t trtri_diag(int nb, const double *D, long long ldd, double *Dinv, cudaStream_t s);
+
+// ---------------------------------------------------------------- elementwise helpers
+// dst(i,j) = src(i,j) for j <= i; strict upper of dst set to 0 (src may == dst).
+cudaError_t copy_lower(int n, const double *src, long long lds, double *dst, long long ldd,
+                       cudaStream_t s);
+// dst (m x c) = src (m x c).
+cudaError_t copy_rect(int m, int c, const double *src, long long lds, double *dst,
+                      long long ldd, cudaStream_t s);
+// Block nb x nb at A: halve the diagonal, zero the strict upper triangle.
+cudaError_t phi_block(int nb, double *A, long long lda, cudaStream_t s);
+// Lower Kbar -> full symmetric G: G_ii = Kbar_ii, G_ij = G_ji = Kbar_ij / 2.
+cudaError_t lower_to_symmetric_half(int n, double *A, long long lda, cudaStream_t s);
+cudaError_t reset_info(int *info, cudaStream_t s);
+
+// ---------------------------------------------------------------- drivers
+size_t chol_workspace_bytes(int n, int precision);
+size_t adjoint_workspace_bytes(int n, int precision);
+size_t trsv_workspace_bytes(int n);
+cudaError_t chol_fp64(int n, double *L, long long ldl, void *ws, int *info, cudaStream_t s);
+cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, long long lda,
+                              void *ws, cudaStream_t s);
+cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, void *ws,
+                 int *info, cudaStream_t s);
+
+// ---------------------------------------------------------------- GP pieces
+constexpr int kMaxDim = 256;
+cudaError_t se_cov(int n, int d, const double *X, long long ldx, double alpha, double rho,
+                   double sigma, double jitter, double *K, long long ldk, int full,
+                   cudaStream_t s);
+size_t se_hyper_grad_workspace_bytes(int n);
+cudaError_t se_hyper_grad(int n, int d, const double *X, long long ldx, double alpha,
+                          double rho, double sigma, const double *Kbar, long long ldkb,
+                          double *grad3, void *ws, cudaStream_t s);
+// scal[0] = logdet = 2 sum log L_ii, scal[1] = y . alpha, value = -1/2 scal[1] - 1/2 logdet
+// - n/2 log(2 pi).  logdet/value may be null.
+cudaError_t lml_finalize(int n, const double *L, long long ldl, const double *y,
+                         const double *alpha, double *logdet, double *value, cudaStream_t s);
+size_t ltv_workspace_bytes(int n);
+// z = L^T v (L lower n x n).
+cudaError_t ltv(int n, const double *L, long long ldl, const double *v, double *z, void *ws,
+                cudaStream_t s);
+// Lbar = gbar (tril(alpha z^T) - diag(1/L_ii)), strict upper zero.
+cudaError_t lml_lbar(int n, const double *L, long long ldl, const double *alpha,
+                     const double *z, double gbar, double *Lbar, long long ldlb, cudaStream_t s);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace gpc

@@ -1,0 +1,279 @@
+// FP64 register-tiled GEMM on the FP64 tensor path (mma.sync m16n8k16 .f64).
+//
+// This is the workhorse of the FP64 blocked Cholesky (panel product with the
+// diagonal-block inverse, trailing update A22 -= L21 L21^T of Section 3.3) and
+// of the blocked adjoint sweep (the products of the reverse-mode procedure of
+// Section 3.3).  tcgen05 has no FP64 kind, so the FP64 tensor instruction on
+// sm_103a is the warp-level DMMA; on GB300 the m16n8k16 shape issues twice
+// the FP64 rate of the m8n8k4 / m16n8k4 shapes and of plain DFMA.
+//
+// Tile: 64 x 64 per CTA, K step 16, 4 warps in a 2 x 2 grid, 32 x 32 per warp
+// (2 x 4 m16n8 fragments).  Operands are staged through shared memory with a
+// register prefetch of the next K step; FP64 throughput on this part is low
+// enough that one stage of prefetch hides global latency completely.
+// Triangular outputs launch only the lower tiles; thin-output / long-K
+// products split K over grid.z into partial tiles summed in fixed order by a
+// second kernel (deterministic).
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace gpc {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, PAD = 4, THREADS = 128;
+constexpr size_t kScratchCap = size_t(40) << 20;  // split-K partial tiles, bytes
+
+struct Params {
+  int M, N, K;
+  double alpha, beta;
+  const double *A;
+  long long lda;
+  const double *B;
+  long long ldb;
+  double *C;
+  long long ldc;
+  int uplo, tiles_n, kchunk;
+  double *partial;  // non-null when grid.z > 1
+};
+
+__device__ __forceinline__ void tri_index(int x, int &ti, int &tj) {
+  int t = (int)((sqrtf(8.0f * (float)x + 1.0f) - 1.0f) * 0.5f);
+  while ((t + 1) * (t + 2) / 2 <= x) ++t;
+  while (t * (t + 1) / 2 > x) --t;
+  ti = t;
+  tj = x - t * (t + 1) / 2;
+}
+
+__device__ __forceinline__ void dmma16816(double (&c)[4], const double (&a)[8], const double (&b)[4]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
+      "{%4,%5,%6,%7,%8,%9,%10,%11}, {%12,%13,%14,%15}, {%0,%1,%2,%3};\n"
+      : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+      : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(a[4]), "d"(a[5]), "d"(a[6]), "d"(a[7]),
+        "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
+}
+
+// Global -> registers for one K step.  Each thread holds 8 A and 8 B values.
+template <bool TA, bool TB>
+__device__ __forceinline__ void load_tiles(const Params &p, int m0, int n0, int k0, int kend,
+                                           double (&ra)[8], double (&rb)[8]) {
+  const int t = threadIdx.x;
+  if (!TA) {  // A[m][k]: 2 threads per row, 8 consecutive k each
+    const int r = t >> 1, c0 = (t & 1) * 8, m = m0 + r;
+    const double *src = p.A + (long long)m * p.lda;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = k0 + c0 + i;
+      ra[i] = (m < p.M && k < kend) ? src[k] : 0.0;
+    }
+  } else {  // A[k][m]: 8 threads per k-row, 8 consecutive m each
+    const int kk = t >> 3, mm0 = (t & 7) * 8, k = k0 + kk;
+    const double *src = p.A + (long long)k * p.lda;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = m0 + mm0 + i;
+      ra[i] = (m < p.M && k < kend) ? src[m] : 0.0;
+    }
+  }
+  if (!TB) {  // B[k][n]
+    const int kk = t >> 3, nn0 = (t & 7) * 8, k = k0 + kk;
+    const double *src = p.B + (long long)k * p.ldb;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int n = n0 + nn0 + i;
+      rb[i] = (n < p.N && k < kend) ? src[n] : 0.0;
+    }
+  } else {  // B[n][k]
+    const int r = t >> 1, c0 = (t & 1) * 8, n = n0 + r;
+    const double *src = p.B + (long long)n * p.ldb;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = k0 + c0 + i;
+      rb[i] = (n < p.N && k < kend) ? src[k] : 0.0;
+    }
+  }
+}
+
+template <bool TA, bool TB>
+__device__ __forceinline__ void store_tiles(double (*As)[BK + PAD], double (*Bs)[BK + PAD],
+                                            const double (&ra)[8], const double (&rb)[8]) {
+  const int t = threadIdx.x;
+  if (!TA) {
+    const int r = t >> 1, c0 = (t & 1) * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) As[r][c0 + i] = ra[i];
+  } else {
+    const int kk = t >> 3, mm0 = (t & 7) * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) As[mm0 + i][kk] = ra[i];
+  }
+  if (!TB) {
+    const int kk = t >> 3, nn0 = (t & 7) * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Bs[nn0 + i][kk] = rb[i];
+  } else {
+    const int r = t >> 1, c0 = (t & 1) * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Bs[r][c0 + i] = rb[i];
+  }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
+  __shared__ double As[2][BM][BK + PAD];
+  __shared__ double Bs[2][BN][BK + PAD];
+
+  int tm, tn;
+  if (p.uplo != UPLO_FULL) {
+    tri_index(blockIdx.x, tm, tn);
+  } else {
+    tm = blockIdx.x / p.tiles_n;
+    tn = blockIdx.x - tm * p.tiles_n;
+  }
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int kbeg = blockIdx.z * p.kchunk;
+  const int kend = min(p.K, kbeg + p.kchunk);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int g = lane >> 2, tg = lane & 3;
+
+  double acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0;
+
+  double ra[8], rb[8];
+  int buf = 0;
+  if (kbeg < kend) {
+    load_tiles<TA, TB>(p, m0, n0, kbeg, kend, ra, rb);
+    store_tiles<TA, TB>(As[0], Bs[0], ra, rb);
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) load_tiles<TA, TB>(p, m0, n0, k0 + BK, kend, ra, rb);
+    double a[2][8], b[4][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+      const int r = wm * 32 + mi * 16 + g;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[mi][i] = As[buf][r + 8 * (i & 1)][tg + 4 * (i >> 1)];
+    }
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+      const int c = wn * 32 + ni * 8 + g;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) b[ni][i] = Bs[buf][c][tg + 4 * i];
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) dmma16816(acc[mi][ni], a[mi], b[ni]);
+    if (more) {
+      store_tiles<TA, TB>(As[buf ^ 1], Bs[buf ^ 1], ra, rb);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+
+  // Epilogue: fragment (mi, ni) element r sits at row g (+8 for r >= 2),
+  // column 2*tg + (r & 1) of the 16 x 8 tile.
+  const bool split = p.partial != nullptr;
+  double *part = split ? p.partial + (size_t)blockIdx.z * p.M * p.N : nullptr;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = m0 + wm * 32 + mi * 16 + g + ((r >> 1) << 3);
+        const int col = n0 + wn * 32 + ni * 8 + 2 * tg + (r & 1);
+        if (row >= p.M || col >= p.N) continue;
+        const double v = p.alpha * acc[mi][ni][r];
+        if (split) {
+          part[(size_t)row * p.N + col] = v;
+          continue;
+        }
+        if (p.uplo != UPLO_FULL && col > row) continue;
+        double *dst = p.C + (long long)row * p.ldc + col;
+        const double out = (p.beta == 0.0) ? v : fma(p.beta, *dst, v);
+        *dst = out;
+        if (p.uplo == UPLO_LOWER_MIRROR && col < row) p.C[(long long)col * p.ldc + row] = out;
+      }
+}
+
+__global__ void splitk_reduce_kernel(Params p, int splits) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)p.M * p.N;
+  if (idx >= total) return;
+  const int row = (int)(idx / p.N), col = (int)(idx - (long long)row * p.N);
+  if (p.uplo != UPLO_FULL && col > row) return;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += p.partial[(size_t)z * total + idx];
+  double *dst = p.C + (long long)row * p.ldc + col;
+  const double out = (p.beta == 0.0) ? s : fma(p.beta, *dst, s);
+  *dst = out;
+  if (p.uplo == UPLO_LOWER_MIRROR && col < row) p.C[(long long)col * p.ldc + row] = out;
+}
+
+}  // namespace
+
+size_t gemm_f64_scratch_bytes() { return kScratchCap; }
+
+cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.uplo != UPLO_FULL && g.M != g.N) return cudaErrorInvalidValue;
+  Params p;
+  p.M = g.M;
+  p.N = g.N;
+  p.K = std::max(g.K, 0);
+  p.alpha = g.alpha;
+  p.beta = g.beta;
+  p.A = g.A;
+  p.lda = g.lda;
+  p.B = g.B;
+  p.ldb = g.ldb;
+  p.C = g.C;
+  p.ldc = g.ldc;
+  p.uplo = g.uplo;
+  const int tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
+  p.tiles_n = tn;
+  const long long tiles = (g.uplo != UPLO_FULL) ? (long long)tm * (tm + 1) / 2 : (long long)tm * tn;
+
+  // Split K when the output alone cannot fill the machine.
+  int splits = 1;
+  const long long target = 2LL * sm_count();
+  const int kmin = std::max(tuning().splitk_min, BK);
+  if (scratch && tiles < target && p.K >= 2 * kmin) {
+    long long want = (target + tiles - 1) / tiles;
+    want = std::min<long long>(want, p.K / kmin);
+    want = std::min<long long>(want, 64);
+    const long long cap = (long long)(kScratchCap / (sizeof(double) * (size_t)g.M * g.N));
+    want = std::min(want, cap);
+    splits = (int)std::max<long long>(want, 1);
+  }
+  int kchunk = (p.K + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  if (kchunk == 0) kchunk = BK;
+  splits = std::max(1, (p.K + kchunk - 1) / kchunk);
+  p.kchunk = kchunk;
+  p.partial = splits > 1 ? scratch : nullptr;
+
+  dim3 grid((unsigned)tiles, 1, (unsigned)splits);
+  if (!g.transA && !g.transB) gemm_f64_kernel<false, false><<<grid, THREADS, 0, s>>>(p);
+  else if (!g.transA && g.transB) gemm_f64_kernel<false, true><<<grid, THREADS, 0, s>>>(p);
+  else if (g.transA && !g.transB) gemm_f64_kernel<true, false><<<grid, THREADS, 0, s>>>(p);
+  else gemm_f64_kernel<true, true><<<grid, THREADS, 0, s>>>(p);
+  if (splits > 1) {
+    const long long total = (long long)g.M * g.N;
+    splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, splits);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gpc

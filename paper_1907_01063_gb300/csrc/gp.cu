@@ -1,0 +1,409 @@
+// Gaussian-process pieces around the factorisation: squared-exponential
+// covariance build, triangular solves, log-likelihood reduction, the upstream
+// adjoint Lbar and the hyperparameter gradient (GP regression of Section 4.2;
+// triangular solves of Section 3.2).
+#include "common.cuh"
+
+namespace gpc {
+namespace {
+
+constexpr int CT = 32;  // covariance / gradient tile (CT x CT entries per CTA)
+
+__device__ __forceinline__ void tri_tile(long long x, int &ti, int &tj) {
+  long long t = (long long)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+  while ((t + 1) * (t + 2) / 2 <= x) ++t;
+  while (t * (t + 1) / 2 > x) --t;
+  ti = (int)t;
+  tj = (int)(x - t * (t + 1) / 2);
+}
+
+// ---------------------------------------------------------------- covariance
+__global__ void __launch_bounds__(256)
+se_cov_kernel(int n, int d, const double *X, long long ldx, double a2, double inv2r2,
+              double diagv, double *K, long long ldk, int full) {
+  extern __shared__ double xs[];  // [2][CT][d]
+  double *xi = xs, *xj = xs + CT * d;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int i0 = ti * CT, j0 = tj * CT;
+  for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
+    const int r = idx / d, t = idx - r * d;
+    xi[idx] = (i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0;
+    xj[idx] = (j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x & (CT - 1);
+  const int j = j0 + c;
+  for (int r = threadIdx.x >> 5; r < CT; r += blockDim.x >> 5) {
+    const int i = i0 + r;
+    if (i >= n || j >= n || j > i) continue;
+    double v;
+    if (i == j) {
+      v = a2 + diagv;
+    } else {
+      double r2 = 0.0;
+      for (int t = 0; t < d; ++t) {
+        const double df = xi[r * d + t] - xj[c * d + t];
+        r2 = fma(df, df, r2);
+      }
+      v = a2 * exp(-r2 * inv2r2);
+    }
+    K[(long long)i * ldk + j] = v;
+    if (full && i != j) K[(long long)j * ldk + i] = v;
+  }
+}
+
+__device__ __forceinline__ double block_sum_256(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+  return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256)
+se_hyper_grad_kernel(int n, int d, const double *X, long long ldx, double alpha, double rho,
+                     double sigma, const double *Kbar, long long ldkb, double *partial) {
+  extern __shared__ double xs[];
+  __shared__ double red[8];
+  double *xi = xs, *xj = xs + CT * d;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int i0 = ti * CT, j0 = tj * CT;
+  for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
+    const int r = idx / d, t = idx - r * d;
+    xi[idx] = (i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0;
+    xj[idx] = (j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0;
+  }
+  __syncthreads();
+  const double a2 = alpha * alpha, inv2r2 = 1.0 / (2.0 * rho * rho), inv_r3 = 1.0 / (rho * rho * rho);
+  const int c = threadIdx.x & (CT - 1);
+  const int j = j0 + c;
+  double ga = 0.0, gr = 0.0, gs = 0.0;
+  for (int r = threadIdx.x >> 5; r < CT; r += blockDim.x >> 5) {
+    const int i = i0 + r;
+    if (i >= n || j >= n || j > i) continue;
+    double r2 = 0.0;
+    for (int t = 0; t < d; ++t) {
+      const double df = xi[r * d + t] - xj[c * d + t];
+      r2 = fma(df, df, r2);
+    }
+    const double kf = a2 * exp(-r2 * inv2r2);
+    const double kb = Kbar[(long long)i * ldkb + j];
+    ga = fma(kb, 2.0 * kf / alpha, ga);
+    gr = fma(kb, kf * r2 * inv_r3, gr);
+    if (i == j) gs = fma(kb, 2.0 * sigma, gs);
+  }
+  const double sa = block_sum_256(ga, red);
+  const double sr = block_sum_256(gr, red);
+  const double ss = block_sum_256(gs, red);
+  if (threadIdx.x == 0) {
+    partial[3 * (size_t)blockIdx.x + 0] = sa;
+    partial[3 * (size_t)blockIdx.x + 1] = sr;
+    partial[3 * (size_t)blockIdx.x + 2] = ss;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+sum3_kernel(const double *partial, long long count, double *out) {
+  __shared__ double red[8];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (long long k = threadIdx.x; k < count; k += blockDim.x) {
+    a += partial[3 * k + 0];
+    b += partial[3 * k + 1];
+    c += partial[3 * k + 2];
+  }
+  const double sa = block_sum_256(a, red);
+  const double sb = block_sum_256(b, red);
+  const double sc = block_sum_256(c, red);
+  if (threadIdx.x == 0) {
+    out[0] = sa;
+    out[1] = sb;
+    out[2] = sc;
+  }
+}
+
+// ---------------------------------------------------------------- triangular solve
+// One CTA per 64-row block of the solve.  CTAs take their block from a ticket
+// counter in launch order, so a CTA only ever waits on blocks owned by CTAs
+// that started before it.  Each finished block publishes a ready flag (1 =
+// solved, 2 = gave up); every wait is bounded and a timeout is reported as
+// GPC_ERR_TIMEOUT and propagated to later blocks as flag 2.
+constexpr int TB = 64;
+constexpr long long kSpinLimit = 1LL << 22;
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+__global__ void __launch_bounds__(256)
+trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sync, int *info) {
+  __shared__ int s_order, s_abort;
+  __shared__ double diag[TB][TB + 1];
+  __shared__ double red[4][TB];
+  __shared__ double rhs[TB];
+  const int nblk = (n + TB - 1) / TB;
+  if (threadIdx.x == 0) {
+    s_order = atomicAdd(&sync[0], 1);
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int order = s_order;
+  const int blk = trans ? (nblk - 1 - order) : order;
+  const int b0 = blk * TB, nb = min(TB, n - b0);
+  const int q = threadIdx.x & 63, rg = threadIdx.x >> 6;
+  double acc[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) acc[r] = 0.0;
+
+  for (int step = 0; step < order; ++step) {
+    const int c = trans ? (nblk - 1 - step) : step;
+    if (threadIdx.x == 0) {
+      long long spins = 0;
+      int f;
+      while ((f = ld_volatile(&sync[1 + c])) == 0 && ++spins < kSpinLimit) __nanosleep(64);
+      if (f != 1) s_abort = 1;
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const int c0 = c * TB, cn = min(TB, n - c0);
+    if (!trans) {
+      if (q < cn) {
+        const double xq = __ldcg(&x[c0 + q]);
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+          const int row = rg * 16 + rr;
+          if (row < nb) acc[rr] = fma(L[(long long)(b0 + row) * ldl + c0 + q], xq, acc[rr]);
+        }
+      }
+    } else {
+      if (q < nb) {
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+          const int r = rg * 16 + rr;
+          if (r < cn) acc[0] = fma(L[(long long)(c0 + r) * ldl + b0 + q], __ldcg(&x[c0 + r]), acc[0]);
+        }
+      }
+    }
+  }
+  if (s_abort) {
+    if (threadIdx.x == 0) {
+      if (info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
+      __threadfence();
+      atomicExch(&sync[1 + blk], 2);
+    }
+    return;
+  }
+
+  // Reduce the partial products of this block.
+  if (!trans) {
+    // rows rg*16 + rr, summed over q (two warps per row group)
+    const int w = (threadIdx.x >> 5) & 1, l = threadIdx.x & 31;
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+      double v = acc[rr];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (l == 0) red[w][rg * 16 + rr] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < TB) {
+      const int r = threadIdx.x;
+      rhs[r] = (r < nb) ? x[b0 + r] - (red[0][r] + red[1][r]) : 0.0;
+    }
+  } else {
+    red[rg][q] = acc[0];
+    __syncthreads();
+    if (threadIdx.x < TB) {
+      const int r = threadIdx.x;
+      rhs[r] = (r < nb) ? x[b0 + r] - ((red[0][r] + red[1][r]) + (red[2][r] + red[3][r])) : 0.0;
+    }
+  }
+  for (int idx = threadIdx.x; idx < TB * TB; idx += blockDim.x) {
+    const int i = idx >> 6, j = idx & 63;
+    diag[i][j] = (i < nb && j < nb) ? L[(long long)(b0 + i) * ldl + b0 + j] : 0.0;
+  }
+  __syncthreads();
+
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double v0 = rhs[lane], v1 = rhs[lane + 32];
+    if (!trans) {
+      for (int k = 0; k < nb; ++k) {
+        const double vk = (k < 32) ? __shfl_sync(0xffffffffu, v0, k) : __shfl_sync(0xffffffffu, v1, k - 32);
+        const double zk = vk / diag[k][k];
+        if (lane > k) v0 = fma(-diag[lane][k], zk, v0);
+        if (lane + 32 > k) v1 = fma(-diag[lane + 32][k], zk, v1);
+        if (lane == k) v0 = zk;
+        if (lane + 32 == k) v1 = zk;
+      }
+    } else {
+      for (int k = nb - 1; k >= 0; --k) {
+        const double vk = (k < 32) ? __shfl_sync(0xffffffffu, v0, k) : __shfl_sync(0xffffffffu, v1, k - 32);
+        const double zk = vk / diag[k][k];
+        if (lane < k) v0 = fma(-diag[k][lane], zk, v0);
+        if (lane + 32 < k) v1 = fma(-diag[k][lane + 32], zk, v1);
+        if (lane == k) v0 = zk;
+        if (lane + 32 == k) v1 = zk;
+      }
+    }
+    if (lane < nb) x[b0 + lane] = v0;
+    if (lane + 32 < nb) x[b0 + lane + 32] = v1;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(&sync[1 + blk], 1);
+  }
+}
+
+// ---------------------------------------------------------------- likelihood pieces
+__global__ void __launch_bounds__(256)
+lml_finalize_kernel(int n, const double *L, long long ldl, const double *y, const double *alpha,
+                    double *logdet, double *value) {
+  __shared__ double red[8];
+  double ld = 0.0, q = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    ld += log(L[(long long)i * ldl + i]);
+    q = fma(y[i], alpha[i], q);
+  }
+  const double sld = block_sum_256(ld, red);
+  const double sq = block_sum_256(q, red);
+  if (threadIdx.x == 0) {
+    const double lg = 2.0 * sld;
+    if (logdet) *logdet = lg;
+    if (value) *value = -0.5 * sq - 0.5 * lg - 0.5 * (double)n * 1.8378770664093454835606594728112;
+  }
+}
+
+constexpr int LTV_ROWS = 256, LTV_COLS = 256;
+
+__global__ void __launch_bounds__(LTV_COLS)
+ltv_partial_kernel(int n, const double *L, long long ldl, const double *v, double *partial) {
+  const int rc = blockIdx.y, col = blockIdx.x * LTV_COLS + threadIdx.x;
+  const int r0 = rc * LTV_ROWS, r1 = min(n, r0 + LTV_ROWS);
+  if (col >= n) return;
+  double acc = 0.0;
+  for (int i = max(r0, col); i < r1; ++i) acc = fma(L[(long long)i * ldl + col], v[i], acc);
+  partial[(size_t)rc * n + col] = acc;
+}
+
+__global__ void ltv_reduce_kernel(int n, int chunks, const double *partial, double *z) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < chunks; ++c) s += partial[(size_t)c * n + col];
+  z[col] = s;
+}
+
+__global__ void lml_lbar_kernel(int n, const double *L, long long ldl, const double *alpha,
+                                const double *z, double gbar, double *Lbar, long long ldlb) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+  double v = 0.0;
+  if (j <= i) {
+    v = alpha[i] * z[j];
+    if (i == j) v -= 1.0 / L[(long long)i * ldl + i];
+    v *= gbar;
+  }
+  Lbar[(long long)i * ldlb + j] = v;
+}
+
+bool g_attr[64][2];
+
+cudaError_t set_dyn_smem(const void *fn, int which) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaSuccess;
+  if (g_attr[dev][which]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       2 * CT * kMaxDim * (int)sizeof(double));
+  if (e == cudaSuccess) g_attr[dev][which] = true;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t se_cov(int n, int d, const double *X, long long ldx, double alpha, double rho,
+                   double sigma, double jitter, double *K, long long ldk, int full,
+                   cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = set_dyn_smem((const void *)se_cov_kernel, 0);
+  if (e != cudaSuccess) return e;
+  const long long T = (n + CT - 1) / CT;
+  const size_t smem = 2 * CT * (size_t)d * sizeof(double);
+  se_cov_kernel<<<(unsigned)(T * (T + 1) / 2), 256, smem, s>>>(
+      n, d, X, ldx, alpha * alpha, 1.0 / (2.0 * rho * rho), sigma * sigma + jitter, K, ldk, full);
+  return cudaGetLastError();
+}
+
+size_t se_hyper_grad_workspace_bytes(int n) {
+  const long long T = (n + CT - 1) / CT;
+  return align_up((size_t)(T * (T + 1) / 2) * 3 * sizeof(double), 256);
+}
+
+cudaError_t se_hyper_grad(int n, int d, const double *X, long long ldx, double alpha, double rho,
+                          double sigma, const double *Kbar, long long ldkb, double *grad3,
+                          void *ws, cudaStream_t s) {
+  if (n <= 0) return cudaMemsetAsync(grad3, 0, 3 * sizeof(double), s);
+  cudaError_t e = set_dyn_smem((const void *)se_hyper_grad_kernel, 1);
+  if (e != cudaSuccess) return e;
+  const long long T = (n + CT - 1) / CT;
+  const long long tiles = T * (T + 1) / 2;
+  const size_t smem = 2 * CT * (size_t)d * sizeof(double);
+  double *partial = (double *)ws;
+  se_hyper_grad_kernel<<<(unsigned)tiles, 256, smem, s>>>(n, d, X, ldx, alpha, rho, sigma, Kbar,
+                                                          ldkb, partial);
+  sum3_kernel<<<1, 256, 0, s>>>(partial, tiles, grad3);
+  return cudaGetLastError();
+}
+
+size_t trsv_workspace_bytes(int n) {
+  const int nblk = (n + TB - 1) / TB;
+  return align_up((size_t)(nblk + 1) * sizeof(int), 256);
+}
+
+cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, void *ws,
+                 int *info, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nblk = (n + TB - 1) / TB;
+  int *sync = (int *)ws;
+  cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nblk + 1) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  trsv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, x, trans ? 1 : 0, sync, info);
+  return cudaGetLastError();
+}
+
+cudaError_t lml_finalize(int n, const double *L, long long ldl, const double *y,
+                         const double *alpha, double *logdet, double *value, cudaStream_t s) {
+  lml_finalize_kernel<<<1, 256, 0, s>>>(n, L, ldl, y, alpha, logdet, value);
+  return cudaGetLastError();
+}
+
+size_t ltv_workspace_bytes(int n) {
+  const int chunks = (n + LTV_ROWS - 1) / LTV_ROWS;
+  return align_up((size_t)chunks * n * sizeof(double), 256);
+}
+
+cudaError_t ltv(int n, const double *L, long long ldl, const double *v, double *z, void *ws,
+                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int chunks = (n + LTV_ROWS - 1) / LTV_ROWS;
+  double *partial = (double *)ws;
+  dim3 grid((n + LTV_COLS - 1) / LTV_COLS, chunks);
+  ltv_partial_kernel<<<grid, LTV_COLS, 0, s>>>(n, L, ldl, v, partial);
+  ltv_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, chunks, partial, z);
+  return cudaGetLastError();
+}
+
+cudaError_t lml_lbar(int n, const double *L, long long ldl, const double *alpha, const double *z,
+                     double gbar, double *Lbar, long long ldlb, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long total = (long long)n * n;
+  lml_lbar_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, L, ldl, alpha, z, gbar, Lbar,
+                                                                   ldlb);
+  return cudaGetLastError();
+}
+
+}  // namespace gpc

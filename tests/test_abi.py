@@ -1,0 +1,91 @@
+"""The C-ABI library loads and exports every symbol include/gpchol.h declares.
+
+Runs without a GPU: only host-side entry points are called (status strings,
+version, workspace sizing, tuning, and argument checks that return before any
+CUDA call).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1907_01063_gb300 as gp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gpchol.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gpc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gpc_chol", "gpc_chol_adjoint", "gpc_gp_lml", "gpc_gp_lml_grad", "gpc_trsv",
+                     "gpc_se_cov", "gpc_se_hyper_grad", "gpc_workspace_size"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(gp.library_path())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(gp._SIGNATURES)
+
+
+def test_host_only_calls():
+    assert gp.capi.gpc_version() >= 100
+    assert "not positive definite" in gp.status_string(gp.GPC_ERR_NOT_PD)
+    assert gp.status_string(12345) == "unknown gpchol status"
+    assert gp.workspace_size(0) > 0
+    assert gp.workspace_size(4096) < gp.workspace_size(8192)
+
+
+def test_tuning_roundtrip_and_validation():
+    old = gp.get_tuning(gp.GPC_TUNE_BLOCK)
+    try:
+        gp.set_tuning(gp.GPC_TUNE_BLOCK, 64)
+        assert gp.get_tuning(gp.GPC_TUNE_BLOCK) == 64
+        for bad in (0, 8, 100, 256):
+            with pytest.raises(gp.GpcholError):
+                gp.set_tuning(gp.GPC_TUNE_BLOCK, bad)
+        with pytest.raises(gp.GpcholError):
+            gp.set_tuning(99, 1)
+    finally:
+        gp.set_tuning(gp.GPC_TUNE_BLOCK, old)
+
+
+def test_argument_checks_return_before_any_launch():
+    c = gp.capi
+    bad = gp.GPC_ERR_INVALID_ARG
+    fake = 0x1000  # never dereferenced: every call below fails validation first
+    size = ctypes.c_size_t()
+    assert c.gpc_workspace_size(-1, 0, ctypes.byref(size)) == bad
+    assert c.gpc_workspace_size(10, 7, ctypes.byref(size)) == bad
+    # negative n, ld < n, null pointers, unknown precision, tiny workspace
+    assert c.gpc_chol(-1, fake, 1, fake, 1, 0, fake, 1 << 30, fake, None) == bad
+    assert c.gpc_chol(10, fake, 9, fake, 10, 0, fake, 1 << 30, fake, None) == bad
+    assert c.gpc_chol(10, None, 10, fake, 10, 0, fake, 1 << 30, fake, None) == bad
+    assert c.gpc_chol(10, fake, 10, fake, 10, 5, fake, 1 << 30, fake, None) == bad
+    assert c.gpc_chol(10, fake, 10, fake + 8, 10, 0, fake, 1 << 30, fake, None) == bad  # overlap
+    assert c.gpc_chol(10, fake, 10, fake, 11, 0, fake, 1 << 30, fake, None) == bad  # in place, ld differs
+    assert c.gpc_chol(10, fake, 10, fake, 10, 0, fake, 16, fake, None) == bad
+    assert c.gpc_chol(10, fake, 10, 0x100000, 10, 0, fake, 1 << 30, None, None) == bad  # no info
+    assert c.gpc_chol_adjoint(10, fake, 10, 0x100000, 10, 0x100000, 10, 0, 0, fake, 16, None) == bad
+    assert c.gpc_chol_adjoint(10, fake, 10, 0x100000, 10, fake, 10, 0, 0, fake, 1 << 30, None) == bad
+    assert c.gpc_trsv(10, None, 10, fake, 0, fake, 1 << 20, None) == bad
+    assert c.gpc_se_cov(10, 0, fake, 1, 1.0, 1.0, 0.1, 0.0, fake, 10, 0, None) == bad
+    assert c.gpc_se_cov(10, 2, fake, 2, 1.0, 0.0, 0.1, 0.0, fake, 10, 0, None) == bad
+    assert c.gpc_se_cov(10, 2, fake, 2, 1.0, -1.0, 0.1, 0.0, fake, 10, 0, None) == bad
+    assert c.gpc_gp_lml(10, fake, 10, fake, 0x100000, 10, 0, None, fake, fake, fake, 1 << 30,
+                        fake, None) == bad
+    assert c.gpc_se_hyper_grad(10, 2, fake, 2, 1.0, 1.0, 0.1, fake, 10, None, fake, 1 << 20, None) == bad
+    # zero-size calls that need no device work
+    assert c.gpc_chol_adjoint(0, None, 0, None, 0, None, 0, 0, 0, None, 0, None) == gp.GPC_OK
+    assert c.gpc_trsv(0, None, 0, None, 0, None, 0, None) == gp.GPC_OK
+    assert c.gpc_se_cov(0, 1, None, 1, 1.0, 1.0, 0.1, 0.0, None, 0, 0, None) == gp.GPC_OK
