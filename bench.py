@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the GP-likelihood hot path on GB300.
+
+One step = one full pass of the path on resident inputs: squared-exponential
+covariance K (n x n) from X (n x d), Cholesky factor L, the two triangular
+solves, log det and log marginal likelihood, the upstream adjoint Lbar, the
+blocked Cholesky adjoint Kbar, and the hyperparameter gradient.  The metric is
+chol+adjoint GFLOP/s: (n^3/3 + the adjoint's counted flops) per step divided
+by the step's device time (the covariance, solves and gradient kernels are
+inside the timed step but add no counted flops).
+
+Workload (default): n = 16384, d = 16, X ~ N(0, 1), alpha = 1, rho = 4 and
+sigma^2 = lambda_max(K^f) / 1e5 (condition number about 1e5), targets from an
+approximate GP draw.  K, L and Kbar are 2 GiB each, far larger than L2, so no
+L2 flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica on its own GPU
+(replicas only: one dense factorisation is not sharded).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "chol+adjoint GFLOP/s and % tensor peak at n=16384; mixed vs FP64 at LML rel err ≤1e-8"
+COND_FILE = os.path.join(ROOT, "tests", "golden", "cond_sigma.json")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--d", type=int, default=16)
+    p.add_argument("--precision", choices=["fp64"], default="fp64")
+    p.add_argument("--block", type=int, default=0, help="block size b (0: library default)")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-sample", type=int, default=3072,
+                   help="order of the leading block the oracle factors for cpu_baseline")
+    p.add_argument("--ref-sample", type=int, default=2048,
+                   help="order of the leading block one reference step factors")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- flop counts
+def chol_flops(n: int) -> float:
+    return n ** 3 / 3.0
+
+
+def adjoint_flops(n: int, b: int) -> float:
+    """Counted flops of the blocked adjoint sweep: panel solve m b^2, GEMM 2mnk,
+    lower-only Cbar^T C m b^2, diagonal-block work (4/3) b^3, Rbar update
+    2 b j (m + b)."""
+    total = 0.0
+    k = n
+    while k > 0:
+        j = max(0, k - b)
+        nb = k - j
+        m = n - k
+        total += m * nb * nb          # Cbar <- Cbar D^{-1}
+        total += 2.0 * m * j * nb     # Bbar -= Cbar R
+        total += m * nb * nb          # Dbar -= Cbar^T C (lower)
+        total += 4.0 / 3.0 * nb ** 3  # diagonal block
+        total += 2.0 * nb * j * (m + nb)  # Rbar -= Cbar^T B + Dbar R
+        k -= b
+    return total
+
+
+# ---------------------------------------------------------------- workload
+def workload(n: int, d: int):
+    from paper_1907_01063_gb300 import workloads as W
+    alpha, rho = 1.0, 4.0
+    sigma = None
+    if os.path.exists(COND_FILE):
+        rec = json.load(open(COND_FILE))
+        if rec.get("n") == n and rec.get("d") == d:
+            sigma = rec["sigma"]
+    if sigma is None:
+        # Other sizes: the same recipe's lambda_max scales about linearly in n.
+        rec = json.load(open(COND_FILE))
+        sigma = math.sqrt(rec["lambda_max"] * n / rec["n"] / rec["target_cond"])
+    X = W.gp_inputs(n, d, seed=0)
+    y = W.gp_targets(X, alpha, rho, sigma, seed=1)
+    return X, y, (alpha, rho, sigma), 0.0
+
+
+def describe(n, d, hyp, b, precision):
+    return {"workload": f"GP LML + gradient, SE kernel, n={n}, d={d}, cond~1e5 ({precision})",
+            "n": n, "d": d, "alpha": hyp[0], "rho": hyp[1], "sigma": round(hyp[2], 6),
+            "block": b, "precision": precision,
+            "l2": "inputs larger than L2 (K, L, Kbar are 8 n^2 bytes each)",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def oracle_sample(ns: int, d: int, hyp):
+    """Unblocked oracle chol + adjoint on the leading ns x ns block (its own
+    SE covariance of the first ns points); returns (seconds, counted flops)."""
+    from oracle import oracle as O
+    from paper_1907_01063_gb300 import workloads as W
+    X = W.gp_inputs(ns, d, seed=0)
+    K = O.se_cov(X, hyp[0], hyp[1], hyp[2], 0.0)
+    Lbar = W.random_lower(ns, seed=2)
+    t0 = time.perf_counter()
+    L = O.chol(K)
+    O.chol_adjoint(L, Lbar)
+    dt = time.perf_counter() - t0
+    return dt, chol_flops(ns) + 2.0 * ns ** 3 / 3.0
+
+
+def cpu_baseline(ns: int, d: int, hyp):
+    dt, fl = oracle_sample(ns, d, hyp)
+    return {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": (f"single-threaded unblocked FP64 oracle: Cholesky-Banachiewicz + unblocked "
+                       f"reverse-mode adjoint of the leading {ns}x{ns} block of the workload "
+                       f"(flops n^3/3 + 2n^3/3), {dt:.1f} s on {os.cpu_count()} host cores available")}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    n, d = args.n, args.d
+    _, _, hyp, _ = workload(n, d)
+    ns = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample(ns, d, hyp)
+    times, flops = [], 0.0
+    for _ in range(args.steps):
+        dt, fl = oracle_sample(ns, d, hyp)
+        times.append(dt)
+        flops += fl
+    total = sum(times)
+    value = flops / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": describe(n, d, hyp, 0, "fp64"),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": (f"each step: single-threaded unblocked FP64 oracle chol + "
+                                    f"adjoint of the leading {ns}x{ns} block of the workload")},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1907_01063_gb300 as gp
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    if args.block:
+        gp.set_tuning(gp.GPC_TUNE_BLOCK, args.block)
+    b = gp.get_tuning(gp.GPC_TUNE_BLOCK)
+    n, d, prec = args.n, args.d, args.precision
+    X, y, hyp, jitter = workload(n, d)
+    a, r, s = hyp
+    step_flops = chol_flops(n) + adjoint_flops(n, b)
+
+    Xd = torch.as_tensor(X, device=dev)
+    yd = torch.as_tensor(y, device=dev)
+    K = torch.empty(n, n, dtype=torch.float64, device=dev)
+    L = torch.empty_like(K)
+    Kbar = torch.empty_like(K)
+    ws = gp.workspace(n, prec, dev)
+    hws = torch.empty(gp.se_hyper_grad_workspace_size(n), dtype=torch.uint8, device=dev)
+    info = gp.new_info(dev)
+    g3 = torch.empty(3, dtype=torch.float64, device=dev)
+
+    def step(Xs, ys):
+        gp.se_cov(Xs, a, r, s, jitter, out=K)
+        res = gp.gp_lml(K, ys, prec, L=L, ws=ws, info=info, check=False)
+        gp.gp_lml_grad(L, res["alpha"], 1.0, prec, out=Kbar, ws=ws)
+        gp.se_hyper_grad(Xs, a, r, s, Kbar, ws=hws, out=g3)
+        return res
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        res = step(Xd, yd)
+    barrier()
+    gp.check_info(info, "warm-up step")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gp.trace_enable(True)
+    launches0 = gp.launch_count()
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        res = step(Xd, yd)
+    ev1.record(stream)
+    barrier()
+    launches = gp.launch_count() - launches0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    trace = gp.trace_summary()
+    gp.trace_enable(False)
+    clk = clocks.stop()
+    gp.check_info(info, "timed step")
+    value_rank = res["value"].item()
+    grad_rank = g3.tolist()
+
+    t_max = elapsed_ms
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = t.item()
+    value = world * args.steps * step_flops / (t_max / 1e3) / 1e9
+
+    # end to end: pinned host inputs in, scalars out, every step
+    Xh = torch.as_tensor(X).pin_memory()
+    yh = torch.as_tensor(y).pin_memory()
+    out_h = torch.empty(4, dtype=torch.float64).pin_memory()
+    Xe = torch.empty_like(Xd)
+    ye = torch.empty_like(yd)
+    e2e_steps = max(1, args.e2e_steps)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        Xe.copy_(Xh, non_blocking=True)
+        ye.copy_(yh, non_blocking=True)
+        res_e = step(Xe, ye)
+        out_h[0:1].copy_(res_e["value"].reshape(1), non_blocking=True)
+        out_h[1:4].copy_(g3, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+    e2e_value = world * e2e_steps * step_flops / (e2e_ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel class (largest device time in the trace)
+    dom_name, dom = max(((k, v) for k, v in trace.items() if v["launches"]), key=lambda kv: kv[1]["ms"])
+    fp64_peak = gp.fp64_peak_gflops() if hasattr(gp, "fp64_peak_gflops") else None
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    nominal_fp64 = peaks.get("bf16_tflops", 1900.0) * 1e3 * 1.25 / 2250.0
+    if dom_name.startswith("gemm") or dom_name == "diag":
+        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0
+        peak = fp64_peak if fp64_peak else nominal_fp64
+        roof = {"kernel": "gemm_f64_kernel (FP64 mma.sync m16n8k16)" if dom_name == "gemm_f64" else dom_name,
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1),
+                "peak_source": ("FP64 DMMA m16n8k16 throughput measured in this run"
+                                if fp64_peak else "of fallback: bf16 burst x 1.25/2250"),
+                "peak_nominal_ratio": nominal_fp64}
+    else:
+        achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(args.cpu_sample, d, hyp)
+    h2d = Xh.numel() * 8 + yh.numel() * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": describe(n, d, hyp, b, prec),
+        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 32, "ms_per_step": e2e_ms / e2e_steps},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "lml": value_rank, "grad": grad_rank,
+        "flops_per_step": step_flops,
+        "kernel_time_ms": {k: round(v["ms"], 3) for k, v in trace.items() if v["launches"]},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

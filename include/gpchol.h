@@ -181,6 +181,39 @@ int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, doub
 /* Workspace bytes gpc_se_hyper_grad needs at order n (*bytes: host pointer). */
 int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes);
 
+/*
+ * Launch trace (no counterpart in the paper; measurement support).  The
+ * library counts every kernel it launches; gpc_launch_count returns the
+ * running total (host pointer *count).  gpc_trace_enable(1) clears the
+ * per-class totals and starts recording a CUDA event pair around each launch
+ * on the launching stream; gpc_trace_enable(0) stops.  gpc_trace_summary
+ * synchronises the recorded events and returns, for one class, the number of
+ * launches, their summed device time in ms and their summed algorithmic
+ * flops and bytes (host pointers).  Not thread-safe; meant for benchmarks.
+ */
+#define GPC_TRACE_GEMM_F64 0   /* FP64 DMMA products (panel, trailing update, adjoint) */
+#define GPC_TRACE_DIAG 1       /* diagonal-block factor / inverse */
+#define GPC_TRACE_TRSV 2       /* triangular solves */
+#define GPC_TRACE_SECOV 3      /* covariance build */
+#define GPC_TRACE_HYPER 4      /* hyperparameter gradient */
+#define GPC_TRACE_ELEM 5       /* copies, reductions and other small kernels */
+#define GPC_TRACE_GEMM_MIXED 6 /* split-BF16 tensor-core products */
+#define GPC_TRACE_SPLIT 7      /* FP64 -> BF16 slice splitting */
+#define GPC_TRACE_CLASSES 8
+int gpc_launch_count(long long *count);
+
+/*
+ * FP64 tensor-core throughput of the current device (measurement support, no
+ * counterpart in the paper): runs an mma.sync m16n8k16 .f64 issue-rate kernel
+ * on every SM three times and returns the best rate in GFLOP/s in *gflops
+ * (host pointer).  ws: device scratch of at least 8 * 256 * 8 * (SM count)
+ * bytes (4 MiB covers a 256-SM device).  Synchronises
+ * the stream.  Used as the roofline denominator of the FP64 products.
+ */
+int gpc_fp64_peak(void *ws, size_t ws_bytes, double *gflops, gpc_stream_t stream);
+int gpc_trace_enable(int on);
+int gpc_trace_summary(int cls, long long *launches, double *ms, double *flops, double *bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,7 +59,15 @@ _SIGNATURES = {
     "gpc_se_hyper_grad": ([_c_int, _c_int, _c_vp, _c_int, _c_double, _c_double, _c_double, _c_vp,
                            _c_int, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
     "gpc_se_hyper_grad_workspace_size": ([_c_int, ctypes.POINTER(_c_size)], _c_int),
+    "gpc_launch_count": ([ctypes.POINTER(ctypes.c_longlong)], _c_int),
+    "gpc_fp64_peak": ([_c_vp, _c_size, ctypes.POINTER(_c_double), _c_vp], _c_int),
+    "gpc_trace_enable": ([_c_int], _c_int),
+    "gpc_trace_summary": ([_c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_c_double),
+                           ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)], _c_int),
 }
+
+TRACE_CLASSES = {"gemm_f64": 0, "diag": 1, "trsv": 2, "se_cov": 3, "hyper_grad": 4, "elementwise": 5,
+                 "gemm_mixed": 6, "split": 7}
 
 
 class GpcholError(RuntimeError):
@@ -190,6 +198,37 @@ def _ws_for(n: int, precision, ws: torch.Tensor | None, device) -> torch.Tensor:
     if ws.numel() * ws.element_size() < need or not ws.is_cuda:
         raise ValueError(f"workspace too small: need {need} bytes")
     return ws
+
+
+def launch_count() -> int:
+    """Running total of kernels this library has launched in this process."""
+    v = ctypes.c_longlong()
+    _check(capi.gpc_launch_count(ctypes.byref(v)), "gpc_launch_count")
+    return v.value
+
+
+def fp64_peak_gflops(device=None) -> float:
+    """Measured FP64 tensor (mma.sync m16n8k16) throughput of the device, GFLOP/s."""
+    ws = torch.empty(4 << 20, dtype=torch.uint8, device=device if device is not None else "cuda")
+    v = ctypes.c_double()
+    _check(capi.gpc_fp64_peak(ws.data_ptr(), ws.numel(), ctypes.byref(v), _stream()), "gpc_fp64_peak")
+    return v.value
+
+
+def trace_enable(on: bool = True):
+    """Start (clearing totals) or stop per-launch CUDA-event timing."""
+    _check(capi.gpc_trace_enable(1 if on else 0), "gpc_trace_enable")
+
+
+def trace_summary() -> dict:
+    """Per kernel class: launches, device ms, algorithmic flops and bytes."""
+    out = {}
+    for name, cls in TRACE_CLASSES.items():
+        n, ms, fl, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(capi.gpc_trace_summary(cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                      ctypes.byref(by)), "gpc_trace_summary")
+        out[name] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+    return out
 
 
 # ---------------------------------------------------------------- tensor API

@@ -101,6 +101,7 @@ cudaError_t chol_fp64(int n, double *L, long long ldl, void *ws, int *info, cuda
     g.A = w.panel; g.lda = nb;
     g.B = w.inv; g.ldb = nb; g.transB = true;
     g.C = A21; g.ldc = ldl;
+    g.algo_flops = (double)m * nb * (nb + 1);  // triangular B
     TRY(gemm_f64(g, w.scratch, s));
     Gemm u;  // A22 -= L21 L21^T (lower tiles)
     u.M = m; u.N = m; u.K = nb;
@@ -131,6 +132,7 @@ cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, 
       g.A = w.panel; g.lda = nb;
       g.B = w.dinv; g.ldb = nb;
       g.C = Cbar; g.ldc = lda;
+      g.algo_flops = (double)m * nb * (nb + 1);  // triangular B
       TRY(gemm_f64(g, w.scratch, s));
       if (j > 0) {
         Gemm h;  // Bbar -= Cbar R
@@ -156,12 +158,14 @@ cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, 
       p.B = Dbar; p.ldb = lda;
       p.C = w.m; p.ldc = nb;
       p.uplo = UPLO_LOWER_MIRROR;
+      p.algo_flops = (double)nb * nb * nb / 3.0;  // triangular A and B, lower output
       TRY(gemm_f64(p, w.scratch, s));
       Gemm t;  // T = M D^{-1}
       t.M = nb; t.N = nb; t.K = nb;
       t.A = w.m; t.lda = nb;
       t.B = w.dinv; t.ldb = nb;
       t.C = w.t; t.ldc = nb;
+      t.algo_flops = (double)nb * nb * (nb + 1);  // triangular B
       TRY(gemm_f64(t, w.scratch, s));
       Gemm d;  // Dbar = D^{-T} T, symmetric
       d.M = nb; d.N = nb; d.K = nb;
@@ -169,6 +173,7 @@ cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, 
       d.B = w.t; d.ldb = nb;
       d.C = Dbar; d.ldc = lda;
       d.uplo = UPLO_LOWER_MIRROR;
+      d.algo_flops = (double)nb * nb * nb / 3.0 * 2.0;  // triangular A, lower output
       TRY(gemm_f64(d, w.scratch, s));
     }
     if (j > 0) {

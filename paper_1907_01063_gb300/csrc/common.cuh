@@ -32,6 +32,7 @@ int sm_count();
 enum { UPLO_FULL = 0, UPLO_LOWER = 1, UPLO_LOWER_MIRROR = 2 };
 struct Gemm {
   int M = 0, N = 0, K = 0;
+  double algo_flops = 0.0;  // algorithmic flops for the trace (0: 2MNK, or M(M+1)K lower)
   bool transA = false, transB = false;
   double alpha = 1.0, beta = 0.0;
   const double *A = nullptr;
@@ -101,5 +102,20 @@ cudaError_t lml_lbar(int n, const double *L, long long ldl, const double *alpha,
                      const double *z, double gbar, double *Lbar, long long ldlb, cudaStream_t s);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- launch trace
+// Every kernel launch site brackets its launch with trace_begin/trace_end.
+// A process-wide counter always counts launches; when tracing is enabled
+// (gpc_trace_enable) CUDA events are also recorded on the launching stream
+// so per-class device time can be read back with gpc_trace_summary.
+// Classes match the GPC_TRACE_* values of the public header.
+void trace_begin(int cls, cudaStream_t s);
+void trace_end(int cls, double flops, double bytes, cudaStream_t s);
+#define GPC_LAUNCH(cls, flops, bytes, stream, ...) \
+  do {                                              \
+    ::gpc::trace_begin((cls), (stream));            \
+    __VA_ARGS__;                                    \
+    ::gpc::trace_end((cls), (flops), (bytes), (stream)); \
+  } while (0)
 
 }  // namespace gpc

@@ -146,7 +146,10 @@ static cudaError_t launch_diag(int nb, double *A, long long lda, double *Winv, i
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  potrf_trtri_kernel<<<1, DIAG_THREADS, smem, s>>>(nb, A, lda, Winv, info, pivot_offset, factor);
+  const double nb3 = (double)nb * nb * nb;
+  GPC_LAUNCH(GPC_TRACE_DIAG, (factor ? nb3 / 3.0 : 0.0) + nb3 / 3.0, 8.0 * 1.5 * nb * nb, s,
+             potrf_trtri_kernel<<<1, DIAG_THREADS, smem, s>>>(nb, A, lda, Winv, info, pivot_offset,
+                                                               factor));
   return cudaGetLastError();
 }
 
@@ -162,32 +165,36 @@ cudaError_t trtri_diag(int nb, const double *D, long long ldd, double *Dinv, cud
 cudaError_t copy_lower(int n, const double *src, long long lds, double *dst, long long ldd,
                        cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  copy_lower_kernel<<<blocks_for((long long)n * n, 256), 256, 0, s>>>(n, src, lds, dst, ldd);
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (double)n * n * 1.5, s,
+             copy_lower_kernel<<<blocks_for((long long)n * n, 256), 256, 0, s>>>(n, src, lds, dst, ldd));
   return cudaGetLastError();
 }
 
 cudaError_t copy_rect(int m, int c, const double *src, long long lds, double *dst, long long ldd,
                       cudaStream_t s) {
   if (m <= 0 || c <= 0) return cudaSuccess;
-  copy_rect_kernel<<<blocks_for((long long)m * c, 256), 256, 0, s>>>(m, c, src, lds, dst, ldd);
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 16.0 * (double)m * c, s,
+             copy_rect_kernel<<<blocks_for((long long)m * c, 256), 256, 0, s>>>(m, c, src, lds, dst, ldd));
   return cudaGetLastError();
 }
 
 cudaError_t phi_block(int nb, double *A, long long lda, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  phi_block_kernel<<<blocks_for((long long)nb * nb, 256), 256, 0, s>>>(nb, A, lda);
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 16.0 * (double)nb * nb, s,
+             phi_block_kernel<<<blocks_for((long long)nb * nb, 256), 256, 0, s>>>(nb, A, lda));
   return cudaGetLastError();
 }
 
 cudaError_t lower_to_symmetric_half(int n, double *A, long long lda, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  lower_to_symmetric_half_kernel<<<blocks_for((long long)n * n, 256), 256, 0, s>>>(n, A, lda);
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 16.0 * (double)n * n, s,
+             lower_to_symmetric_half_kernel<<<blocks_for((long long)n * n, 256), 256, 0, s>>>(n, A, lda));
   return cudaGetLastError();
 }
 
 cudaError_t reset_info(int *info, cudaStream_t s) {
   if (!info) return cudaSuccess;
-  reset_info_kernel<<<1, 1, 0, s>>>(info);
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0, s, reset_info_kernel<<<1, 1, 0, s>>>(info));
   return cudaGetLastError();
 }
 

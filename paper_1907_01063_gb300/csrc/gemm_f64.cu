@@ -265,13 +265,19 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   p.partial = splits > 1 ? scratch : nullptr;
 
   dim3 grid((unsigned)tiles, 1, (unsigned)splits);
-  if (!g.transA && !g.transB) gemm_f64_kernel<false, false><<<grid, THREADS, 0, s>>>(p);
-  else if (!g.transA && g.transB) gemm_f64_kernel<false, true><<<grid, THREADS, 0, s>>>(p);
-  else if (g.transA && !g.transB) gemm_f64_kernel<true, false><<<grid, THREADS, 0, s>>>(p);
-  else gemm_f64_kernel<true, true><<<grid, THREADS, 0, s>>>(p);
+  const double mn = (g.uplo != UPLO_FULL) ? 0.5 * (double)g.M * (g.M + 1) : (double)g.M * g.N;
+  const double flops = g.algo_flops > 0.0 ? g.algo_flops : 2.0 * mn * (double)p.K;
+  const double bytes = 8.0 * ((double)g.M * p.K + (double)p.K * g.N + (g.beta != 0.0 ? 2.0 : 1.0) * mn);
+  GPC_LAUNCH(GPC_TRACE_GEMM_F64, flops, bytes, s, {
+    if (!g.transA && !g.transB) gemm_f64_kernel<false, false><<<grid, THREADS, 0, s>>>(p);
+    else if (!g.transA && g.transB) gemm_f64_kernel<false, true><<<grid, THREADS, 0, s>>>(p);
+    else if (g.transA && !g.transB) gemm_f64_kernel<true, false><<<grid, THREADS, 0, s>>>(p);
+    else gemm_f64_kernel<true, true><<<grid, THREADS, 0, s>>>(p);
+  });
   if (splits > 1) {
     const long long total = (long long)g.M * g.N;
-    splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, splits);
+    GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (splits + 2) * mn, s,
+               splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, splits));
   }
   return cudaGetLastError();
 }

@@ -333,8 +333,11 @@ cudaError_t se_cov(int n, int d, const double *X, long long ldx, double alpha, d
   if (e != cudaSuccess) return e;
   const long long T = (n + CT - 1) / CT;
   const size_t smem = 2 * CT * (size_t)d * sizeof(double);
-  se_cov_kernel<<<(unsigned)(T * (T + 1) / 2), 256, smem, s>>>(
-      n, d, X, ldx, alpha * alpha, 1.0 / (2.0 * rho * rho), sigma * sigma + jitter, K, ldk, full);
+  const double tri = 0.5 * (double)n * (n + 1);
+  GPC_LAUNCH(GPC_TRACE_SECOV, tri * 3.0 * d, 8.0 * (full ? 2.0 * tri - n : tri) + 8.0 * n * d, s,
+             se_cov_kernel<<<(unsigned)(T * (T + 1) / 2), 256, smem, s>>>(
+                 n, d, X, ldx, alpha * alpha, 1.0 / (2.0 * rho * rho), sigma * sigma + jitter, K,
+                 ldk, full));
   return cudaGetLastError();
 }
 
@@ -353,9 +356,11 @@ cudaError_t se_hyper_grad(int n, int d, const double *X, long long ldx, double a
   const long long tiles = T * (T + 1) / 2;
   const size_t smem = 2 * CT * (size_t)d * sizeof(double);
   double *partial = (double *)ws;
-  se_hyper_grad_kernel<<<(unsigned)tiles, 256, smem, s>>>(n, d, X, ldx, alpha, rho, sigma, Kbar,
-                                                          ldkb, partial);
-  sum3_kernel<<<1, 256, 0, s>>>(partial, tiles, grad3);
+  const double tri = 0.5 * (double)n * (n + 1);
+  GPC_LAUNCH(GPC_TRACE_HYPER, tri * (3.0 * d + 6.0), 8.0 * tri + 8.0 * n * d, s,
+             se_hyper_grad_kernel<<<(unsigned)tiles, 256, smem, s>>>(n, d, X, ldx, alpha, rho,
+                                                                     sigma, Kbar, ldkb, partial));
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 24.0 * tiles, s, sum3_kernel<<<1, 256, 0, s>>>(partial, tiles, grad3));
   return cudaGetLastError();
 }
 
@@ -371,13 +376,15 @@ cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, vo
   int *sync = (int *)ws;
   cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nblk + 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  trsv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, x, trans ? 1 : 0, sync, info);
+  GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n, 4.0 * (double)n * (n + 1) + 16.0 * n, s,
+             trsv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, x, trans ? 1 : 0, sync, info));
   return cudaGetLastError();
 }
 
 cudaError_t lml_finalize(int n, const double *L, long long ldl, const double *y,
                          const double *alpha, double *logdet, double *value, cudaStream_t s) {
-  lml_finalize_kernel<<<1, 256, 0, s>>>(n, L, ldl, y, alpha, logdet, value);
+  GPC_LAUNCH(GPC_TRACE_ELEM, 3.0 * n, 24.0 * n, s,
+             lml_finalize_kernel<<<1, 256, 0, s>>>(n, L, ldl, y, alpha, logdet, value));
   return cudaGetLastError();
 }
 
@@ -392,8 +399,10 @@ cudaError_t ltv(int n, const double *L, long long ldl, const double *v, double *
   const int chunks = (n + LTV_ROWS - 1) / LTV_ROWS;
   double *partial = (double *)ws;
   dim3 grid((n + LTV_COLS - 1) / LTV_COLS, chunks);
-  ltv_partial_kernel<<<grid, LTV_COLS, 0, s>>>(n, L, ldl, v, partial);
-  ltv_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, chunks, partial, z);
+  GPC_LAUNCH(GPC_TRACE_ELEM, (double)n * n, 4.0 * (double)n * (n + 1), s,
+             ltv_partial_kernel<<<grid, LTV_COLS, 0, s>>>(n, L, ldl, v, partial));
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (double)chunks * n, s,
+             ltv_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, chunks, partial, z));
   return cudaGetLastError();
 }
 
@@ -401,8 +410,9 @@ cudaError_t lml_lbar(int n, const double *L, long long ldl, const double *alpha,
                      double gbar, double *Lbar, long long ldlb, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const long long total = (long long)n * n;
-  lml_lbar_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, L, ldl, alpha, z, gbar, Lbar,
-                                                                   ldlb);
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (double)total, s,
+             lml_lbar_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, L, ldl, alpha, z,
+                                                                             gbar, Lbar, ldlb));
   return cudaGetLastError();
 }
 
