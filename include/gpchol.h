@@ -142,6 +142,29 @@ int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, si
              gpc_stream_t stream);
 
 /*
+ * gpc_trsv without any caller-supplied scratch (the paper has no counterpart;
+ * this is an addition for callers that cannot give the library device memory).
+ * Callers that run under a device-memory budget owned by someone else (a
+ * framework or sampler whose pool holds all device memory) or inside loops
+ * that must not call cudaMalloc/cudaFree (cudaFree may synchronise the whole
+ * device) pass only L and x; the solve's scratch -- a ticket counter and one
+ * ready flag per 64-row block -- is a fixed 16.25 KiB array inside the library,
+ * held by every GPU that loads the library until the process exits.
+ *  - n must be <= GPC_TRSV_NOALLOC_MAX_N; larger n returns GPC_ERR_INVALID_ARG
+ *    before anything is enqueued.  Other arguments as in gpc_trsv.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *    first call before any stream capture.  No call allocates memory.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents; each call clears the flags it uses on `stream` before its
+ *    kernel.  Calls whose execution overlaps on the GPU (different streams
+ *    without ordering between them) race on the array and give wrong results:
+ *    serialise them.
+ */
+#define GPC_TRSV_NOALLOC_MAX_N 262144
+int gpc_trsv_noalloc(int n, const double *L, int ldl, double *x, int trans, gpc_stream_t stream);
+
+/*
  * Gaussian-process log marginal likelihood of y ~ N(0, K):
  *   L = chol(K), z = L^{-1} y, alpha = L^{-T} z, logdet = 2 sum log L_ii,
  *   value = -1/2 y^T alpha - 1/2 logdet - (n/2) log(2 pi).

@@ -52,6 +52,7 @@ _SIGNATURES = {
     "gpc_chol_adjoint": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_int, _c_int,
                           _c_vp, _c_size, _c_vp], _c_int),
     "gpc_trsv": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_size, _c_vp], _c_int),
+    "gpc_trsv_noalloc": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp], _c_int),
     "gpc_gp_lml": ([_c_int, _c_vp, _c_int, _c_vp, _c_vp, _c_int, _c_int, _c_vp, _c_vp, _c_vp,
                     _c_vp, _c_size, _c_vp, _c_vp], _c_int),
     "gpc_gp_lml_grad": ([_c_int, _c_vp, _c_int, _c_vp, _c_double, _c_vp, _c_int, _c_int, _c_vp,
