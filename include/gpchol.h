@@ -228,9 +228,10 @@ int gpc_launch_count(long long *count);
 /*
  * FP64 tensor-core throughput of the current device (measurement support, no
  * counterpart in the paper): runs an mma.sync m16n8k16 .f64 issue-rate kernel
- * on every SM three times and returns the best rate in GFLOP/s in *gflops
- * (host pointer).  ws: device scratch of at least 8 * 256 * 8 * (SM count)
- * bytes (4 MiB covers a 256-SM device).  Synchronises
+ * (eight independent accumulator chains per warp, 32 warps per SM) three times
+ * and returns the best rate in GFLOP/s in *gflops (host pointer).  ws: device
+ * scratch of at least 8 * 128 * 8 * (SM count) bytes (4 MiB covers any
+ * current device).  Synchronises
  * the stream.  Used as the roofline denominator of the FP64 products.
  */
 int gpc_fp64_peak(void *ws, size_t ws_bytes, double *gflops, gpc_stream_t stream);

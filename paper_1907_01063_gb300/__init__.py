@@ -60,6 +60,8 @@ _SIGNATURES = {
     "gpc_se_hyper_grad": ([_c_int, _c_int, _c_vp, _c_int, _c_double, _c_double, _c_double, _c_vp,
                            _c_int, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
     "gpc_se_hyper_grad_workspace_size": ([_c_int, ctypes.POINTER(_c_size)], _c_int),
+    "gpc_test_ozaki_workspace_size": ([_c_int, _c_int, _c_int, ctypes.POINTER(_c_size)], _c_int),
+    "gpc_test_ozaki_gemm": ([_c_int, _c_int, _c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_size, _c_vp, _c_vp], _c_int),
     "gpc_launch_count": ([ctypes.POINTER(ctypes.c_longlong)], _c_int),
     "gpc_fp64_peak": ([_c_vp, _c_size, ctypes.POINTER(_c_double), _c_vp], _c_int),
     "gpc_trace_enable": ([_c_int], _c_int),
@@ -350,6 +352,24 @@ def se_hyper_grad(X: torch.Tensor, alpha: float, rho: float, sigma: float, Kbar:
                                   wsb.numel() * wsb.element_size(), _stream()),
            "gpc_se_hyper_grad")
     return g
+
+
+def test_ozaki_gemm(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """A @ B.T through the mixed path's split-BF16 tensor-core product (test hook)."""
+    M, K = A.shape
+    N, K2 = B.shape
+    if K != K2 or not (A.is_contiguous() and B.is_contiguous()):
+        raise ValueError("A (M x K) and B (N x K) must be contiguous with equal K")
+    nb = ctypes.c_size_t()
+    _check(capi.gpc_test_ozaki_workspace_size(M, N, K, ctypes.byref(nb)), "gpc_test_ozaki_workspace_size")
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=A.device)
+    C = torch.empty(M, N, dtype=torch.float64, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(capi.gpc_test_ozaki_gemm(M, N, K, A.data_ptr(), B.data_ptr(), C.data_ptr(), ws.data_ptr(),
+                                    ws.numel(), err.data_ptr(), _stream()), "gpc_test_ozaki_gemm")
+    if int(err.item()) != 0:
+        raise GpcholError(int(err.item()), "gpc_test_ozaki_gemm")
+    return C
 
 
 # ---------------------------------------------------------------- autograd

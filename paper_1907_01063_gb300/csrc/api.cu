@@ -36,8 +36,11 @@ struct ApiWs {
 size_t core_bytes(int n, int precision) {
   size_t c = std::max(chol_workspace_bytes(n, precision), adjoint_workspace_bytes(n, precision));
   c = std::max(c, ltv_workspace_bytes(n));
+  if (precision == GPC_MIXED) c = std::max(c, mixed_workspace_bytes(n));
   return align_up(c, 256);
 }
+
+bool valid_precision(int p) { return p == GPC_FP64 || p == GPC_MIXED; }
 
 size_t total_bytes(int n, int precision) {
   return core_bytes(n, precision) + align_up(4 * (size_t)std::max(n, 1) * sizeof(double), 256) +
@@ -133,7 +136,7 @@ int gpc_se_cov(int n, int d, const double *X, int ldx, double alpha, double rho,
 
 int gpc_chol(int n, const double *K, int ldk, double *L, int ldl, int precision, void *ws,
              size_t ws_bytes, int *info, gpc_stream_t stream) {
-  if (n < 0 || precision != GPC_FP64 || !info) return GPC_ERR_INVALID_ARG;
+  if (n < 0 || !valid_precision(precision) || !info) return GPC_ERR_INVALID_ARG;
   if (n == 0) return status_of(reset_info(info, stream));
   if (bad_square(n, K, ldk) || bad_square(n, L, ldl) || !ws || ws_bytes < total_bytes(n, precision))
     return GPC_ERR_INVALID_ARG;
@@ -144,6 +147,11 @@ int gpc_chol(int n, const double *K, int ldk, double *L, int ldl, int precision,
   }
   ApiWs w = carve(ws, n, precision);
   cudaError_t e = reset_info(info, stream);
+  if (precision == GPC_MIXED) {
+    if (e == cudaSuccess) e = to_df_lower(n, K, ldk, L, ldl, stream);
+    if (e == cudaSuccess) e = chol_mixed(n, L, ldl, w.core, info, stream);
+    return status_of(e);
+  }
   if (e == cudaSuccess) e = copy_lower(n, K, ldk, L, ldl, stream);
   if (e == cudaSuccess) e = chol_fp64(n, L, ldl, w.core, info, stream);
   return status_of(e);
@@ -152,7 +160,7 @@ int gpc_chol(int n, const double *K, int ldk, double *L, int ldl, int precision,
 int gpc_chol_adjoint(int n, const double *L, int ldl, const double *Lbar, int ldlb, double *Kbar,
                      int ldkb, int precision, int symmetric_out, void *ws, size_t ws_bytes,
                      gpc_stream_t stream) {
-  if (n < 0 || precision != GPC_FP64) return GPC_ERR_INVALID_ARG;
+  if (n < 0 || !valid_precision(precision)) return GPC_ERR_INVALID_ARG;
   if (n == 0) return GPC_OK;
   if (bad_square(n, L, ldl) || bad_square(n, Lbar, ldlb) || bad_square(n, Kbar, ldkb) || !ws ||
       ws_bytes < total_bytes(n, precision))
@@ -164,8 +172,14 @@ int gpc_chol_adjoint(int n, const double *L, int ldl, const double *Lbar, int ld
   }
   if (overlaps(L, mat_bytes(n, ldl), Kbar, mat_bytes(n, ldkb))) return GPC_ERR_INVALID_ARG;
   ApiWs w = carve(ws, n, precision);
-  cudaError_t e = copy_lower(n, Lbar, ldlb, Kbar, ldkb, stream);
-  if (e == cudaSuccess) e = chol_adjoint_fp64(n, L, ldl, Kbar, ldkb, w.core, stream);
+  cudaError_t e;
+  if (precision == GPC_MIXED) {
+    e = to_df_lower(n, Lbar, ldlb, Kbar, ldkb, stream);
+    if (e == cudaSuccess) e = chol_adjoint_mixed(n, L, ldl, Kbar, ldkb, w.core, w.flags, stream);
+  } else {
+    e = copy_lower(n, Lbar, ldlb, Kbar, ldkb, stream);
+    if (e == cudaSuccess) e = chol_adjoint_fp64(n, L, ldl, Kbar, ldkb, w.core, stream);
+  }
   if (e == cudaSuccess && symmetric_out) e = lower_to_symmetric_half(n, Kbar, ldkb, stream);
   return status_of(e);
 }

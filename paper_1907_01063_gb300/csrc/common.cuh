@@ -14,7 +14,7 @@ namespace gpc {
 // ---------------------------------------------------------------- tuning
 struct Tuning {
   int block = 128;        // b: block size of the blocked factorisation / adjoint
-  int slices = 6;         // BF16 slices per FP64 operand on the mixed path
+  int slices = 5;         // BF16 slices per FP64 operand on the mixed path
   int splitk_min = 512;   // minimum K per split of a split-K product
 };
 Tuning &tuning();
@@ -102,6 +102,37 @@ cudaError_t lml_lbar(int n, const double *L, long long ldl, const double *alpha,
                      const double *z, double gbar, double *Lbar, long long ldlb, cudaStream_t s);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- mixed precision (ozaki.cu)
+// BF16 slice planes of an operand, K-major: plane p, row r, K index k at
+// base[p * rows_pad * kpad + r * kpad + k]; K is cut into 128-wide chunks.
+struct SliceBuf {
+  void *base = nullptr;
+  int rows_pad = 0;
+  int kpad = 0;
+};
+int slices_count();
+int slice_chunk();
+size_t slice_bytes(int rows, int kchunks);
+SliceBuf slice_view(void *base, int rows, int kchunks);
+// Operand element (r, k) = src[r * rs + k * ks]; chunk 0 is k in [0, first).
+cudaError_t split_operand(const double *src, long long rs, long long ks, int M, int K, int first,
+                          const SliceBuf &out, cudaStream_t s);
+size_t ozaki_partial_bytes(int M, int N, int splits);
+// C (double-float storage, ld in 8-byte elements) += alpha * A[a_row0 + i, a_k0 + k] B[b_row0 + j, b_k0 + k]
+// over `chunks` K chunks; lower: only col <= row (M == N).  splits > 1 sums
+// K ranges through `partial` (ozaki_partial_bytes) in fixed order.
+cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &B, int b_row0, int b_k0,
+                       int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
+                       int splits, float2 *partial, int *err, cudaStream_t s);
+// Lower triangle of src (FP64) -> dst in double-float storage (upper set to 0); src may == dst.
+cudaError_t to_df_lower(int n, const double *src, long long lds, double *dst, long long ldd, cudaStream_t s);
+// m x c block in double-float storage -> FP64, in place.
+cudaError_t from_df_rect(int m, int c, double *p, long long ld, cudaStream_t s);
+size_t mixed_workspace_bytes(int n);
+cudaError_t chol_mixed(int n, double *L, long long ldl, void *ws, int *info, cudaStream_t s);
+cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A, long long lda, void *ws,
+                               int *err, cudaStream_t s);
 
 // ---------------------------------------------------------------- launch trace
 // Every kernel launch site brackets its launch with trace_begin/trace_end.

@@ -1,0 +1,702 @@
+// Mixed-precision products on the fifth-generation tensor cores (tcgen05).
+//
+// The O(n^3) products of the blocked Cholesky and of its blocked adjoint
+// (Section 3.3) are evaluated with an error-free split of the FP64 operands
+// into BF16 slices (the Ozaki scheme: Ozaki, Ogita, Oishi & Rump, 2012).
+//
+// Splitting.  The K index of an operand is cut into chunks of at most 128.
+// For every (row, chunk) the exponent e with |x| < 2^e over the chunk is found
+// and each element is rounded to the fixed-point integer X = rint(|x| 2^(40-e))
+// (40 bits), written with five balanced base-256 digits: d_2..d_5 in
+// [-128, 127] (a digit >= 128 becomes d - 256 with a carry upward) and
+// d_1 in [0, 256].  The slices v_p = sign(x) d_p 2^(e - 8p) are exact in
+// BF16.  The exponent is folded into the slice values, so no exponent arrays
+// travel with them.
+//
+// Products.  For one output tile and one K chunk (K <= 128) the slice
+// products A_p B_q^T are accumulated on tcgen05 into four FP32 TMEM
+// accumulators, grouped by p + q (1-based):
+//   G2: (1,1)                 |sum| <= 128 * 256 * 256          = 2^23
+//   G3: (1,2) (2,1)           |sum| <= 128 * 2 * 256 * 128      = 2^23
+//   G4: (1,3) (2,2) (3,1)     |sum| <= 128 * (2^15+2^14+2^15)   < 2^24
+//   G56: the 9 pairs with p + q in {5, 6}
+// G2, G3 and G4 are sums of integers (in units of their slice scales) whose
+// partial sums all stay below 2^24, so the tensor core accumulates them
+// exactly whatever its internal rounding; G56 is rounded but lies 2^-32
+// below G2.  Pairs with p + q > 6 are dropped (2^-40 below G2 per term).  One
+// chunk's contribution is good to about 2^-38 relative to max|a| max|b|.
+//
+// Accumulation across chunks and into the output.  The output lives in
+// "double-float" storage: each 8-byte element holds an FP32 pair (hi, lo)
+// with value hi + lo (about 48 significant bits).  After each chunk the
+// epilogue warps read G2, G3, GL from TMEM and add them into (hi, lo) with
+// error-free FP32 two-sums.  This keeps the FP64 pipe -- a small fraction of
+// the FP32 and tensor rates on this part -- out of the inner loop; the
+// factorisation converts a block column to FP64 only when it becomes the
+// current panel.
+//
+// Kernel structure: persistent CTAs (one per SM), 6 warps: warp 0 issues TMA
+// loads of the slice tiles (64B-swizzled, K-major, 32 wide) into a 3-stage ring,
+// warp 1 owns TMEM and issues the MMAs from one thread, warps 2..5 are the
+// epilogue (one TMEM lane quarter each).  TMEM holds two accumulator sets, so
+// the epilogue of one chunk overlaps the MMAs of the next (4 x 64 columns per set, 512 in all).  Every mbarrier
+// wait is bounded in time; a timeout sets GPC_ERR_TIMEOUT in the error word,
+// drains the copies and MMAs already issued, frees TMEM and returns.
+#include "common.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+namespace gpc {
+namespace {
+
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32, OZ_CHUNK = 128, OZ_S = 5, OZ_STAGES = 3;
+constexpr int OZ_QPC = OZ_CHUNK / OZ_BK;                 // stages per chunk
+constexpr int OZ_THREADS = 192;
+constexpr int OZ_A_PLANE = OZ_BM * OZ_BK * 2;            // 8 KiB
+constexpr int OZ_B_PLANE = OZ_BN * OZ_BK * 2;            // 4 KiB
+constexpr int OZ_A_STAGE = OZ_S * OZ_A_PLANE;            // 40 KiB
+constexpr int OZ_B_STAGE = OZ_S * OZ_B_PLANE;            // 20 KiB
+constexpr int OZ_ACCS = 4;                               // G2, G3, G4, G56
+constexpr int OZ_ACC_COLS = OZ_ACCS * OZ_BN;             // one accumulator set
+constexpr int OZ_TMEM_COLS = 512;
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + 1024 /*barriers*/ + 1024 /*align*/;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+struct OzParams {
+  int M, N, chunks;
+  int a_row0, b_row0, a_k0, b_k0;
+  int lower, splits, tiles_m, tiles_n, num_work;
+  float alpha;
+  float2 *C;
+  long long ldc;
+  float2 *partial;
+  int *err;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, P;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false on timeout or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kWaitNs) return false;
+    }
+  }
+}
+// Wait that ignores the abort flag (used only to drain own work), bounded.
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 64B swizzle (rows of 32 BF16),
+// 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);       // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (16 B; unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;               // stride byte offset
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)4 << 61;                        // 64B swizzle
+  return d;
+}
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = OZ_BN.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                            ((uint32_t)(OZ_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------ double-float
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ float2 df_add3(float2 c, float x, float y, float z) {
+  float s = c.x, e = c.y, t;
+  two_sum(s, x, s, t);
+  e = __fadd_rn(e, t);
+  two_sum(s, y, s, t);
+  e = __fadd_rn(e, t);
+  two_sum(s, z, s, t);
+  e = __fadd_rn(e, t);
+  const float hi = __fadd_rn(s, e);
+  const float lo = __fsub_rn(e, __fsub_rn(hi, s));
+  return make_float2(hi, lo);
+}
+__device__ __forceinline__ float2 df_add4(float2 c, float x, float y, float z, float w) {
+  float s = c.x, e = c.y, t;
+  two_sum(s, x, s, t);
+  e = __fadd_rn(e, t);
+  two_sum(s, y, s, t);
+  e = __fadd_rn(e, t);
+  two_sum(s, z, s, t);
+  e = __fadd_rn(e, t);
+  two_sum(s, w, s, t);
+  e = __fadd_rn(e, t);
+  const float hi = __fadd_rn(s, e);
+  const float lo = __fsub_rn(e, __fsub_rn(hi, s));
+  return make_float2(hi, lo);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, t;
+  two_sum(a.x, b.x, s, t);
+  const float e = __fadd_rn(__fadd_rn(a.y, b.y), t);
+  const float hi = __fadd_rn(s, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
+// ------------------------------------------------------------------ work list
+__device__ __forceinline__ void work_coords(const OzParams &p, int w, int &tm, int &tn, int &c0, int &c1) {
+  const int split = w % p.splits;
+  int tile = w / p.splits;
+  if (p.lower) {
+    tm = 0;
+    for (;;) {
+      const int cnt = min(p.tiles_n, (tm * OZ_BM + OZ_BM - 1) / OZ_BN + 1);
+      if (tile < cnt) break;
+      tile -= cnt;
+      ++tm;
+    }
+    tn = tile;
+  } else {
+    tm = tile / p.tiles_n;
+    tn = tile - tm * p.tiles_n;
+  }
+  const int per = (p.chunks + p.splits - 1) / p.splits;
+  c0 = split * per;
+  c1 = min(p.chunks, c0 + per);
+}
+
+// ------------------------------------------------------------------ the GEMM
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *sA = smem;
+  unsigned char *sB = smem + OZ_STAGES * OZ_A_STAGE;
+  uint64_t *bars = (uint64_t *)(sB + OZ_STAGES * OZ_B_STAGE);
+  // bars: full[3], empty[3], tfull[2], tempty[2], drain
+  volatile int *abort_flag = (volatile int *)(bars + 16);
+  uint32_t *tmem_slot = (uint32_t *)(bars + 17);
+  const uint32_t full0 = smem_u32(bars + 0), empty0 = smem_u32(bars + OZ_STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * OZ_STAGES), tempty0 = smem_u32(bars + 2 * OZ_STAGES + 2);
+  const uint32_t drain = smem_u32(bars + 2 * OZ_STAGES + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < OZ_STAGES; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull0 + 8 * i, 1);
+      mbar_init(tempty0 + 8 * i, 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      long long issued = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < p.num_work && ok; w += gridDim.x) {
+        int tm, tn, c0, c1;
+        work_coords(p, w, tm, tn, c0, c1);
+        for (int c = c0; c < c1 && ok; ++c) {
+          for (int h = 0; h < OZ_QPC; ++h) {
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
+            mbar_expect_tx(full0 + 8 * stage, OZ_A_STAGE + OZ_B_STAGE);
+            const int ka = p.a_k0 + c * OZ_CHUNK + h * OZ_BK;
+            const int kb = p.b_k0 + c * OZ_CHUNK + h * OZ_BK;
+            tma_load_3d(smem_u32(sA + stage * OZ_A_STAGE), &tmA, ka, p.a_row0 + tm * OZ_BM, 0, full0 + 8 * stage);
+            tma_load_3d(smem_u32(sB + stage * OZ_B_STAGE), &tmB, kb, p.b_row0 + tn * OZ_BN, 0, full0 + 8 * stage);
+            ++issued;
+            if (++stage == OZ_STAGES) { stage = 0; phase ^= 1; }
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (p.err) atomicExch(p.err, GPC_ERR_TIMEOUT);
+        // Drain: wait for the copies of the last (up to OZ_STAGES) issued loads.
+        const long long first = issued > OZ_STAGES ? issued - OZ_STAGES : 0;
+        for (long long i = first; i < issued; ++i) {
+          const int st = (int)(i % OZ_STAGES);
+          const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
+          mbar_wait_drain(full0 + 8 * st, ph);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int buf = 0;
+      uint32_t tphase = 0;
+      bool ok = true;
+      bool any = false;
+      for (int w = blockIdx.x; w < p.num_work && ok; w += gridDim.x) {
+        int tm, tn, c0, c1;
+        work_coords(p, w, tm, tn, c0, c1);
+        for (int c = c0; c < c1 && ok; ++c) {
+          if (!mbar_wait(tempty0 + 8 * buf, tphase ^ 1, abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint32_t tacc = tbase + (uint32_t)(buf * OZ_ACC_COLS);
+          for (int h = 0; h < OZ_QPC && ok; ++h) {
+            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
+            fence_after();
+            const uint32_t a0 = smem_u32(sA + stage * OZ_A_STAGE);
+            const uint32_t b0 = smem_u32(sB + stage * OZ_B_STAGE);
+#pragma unroll
+            for (int k = 0; k < OZ_BK / 16; ++k) {
+              const uint32_t first = (h == 0 && k == 0) ? 0u : 1u;
+              const uint32_t ka = a0 + k * 32, kb = b0 + k * 32;
+#define OZ_MMA(P, Q, ACC, FIRST)                                                               \
+  mma_bf16(tacc + (ACC) * OZ_BN, sdesc(ka + (P) * OZ_A_PLANE), sdesc(kb + (Q) * OZ_B_PLANE), \
+           (FIRST) ? first : 1u)
+              OZ_MMA(0, 0, 0, 1);  // G2  (0-based slice indices)
+              OZ_MMA(0, 1, 1, 1);  // G3
+              OZ_MMA(1, 0, 1, 0);
+              OZ_MMA(0, 2, 2, 1);  // G4
+              OZ_MMA(1, 1, 2, 0);
+              OZ_MMA(2, 0, 2, 0);
+              OZ_MMA(0, 3, 3, 1);  // G56
+              OZ_MMA(1, 2, 3, 0);
+              OZ_MMA(2, 1, 3, 0);
+              OZ_MMA(3, 0, 3, 0);
+              OZ_MMA(0, 4, 3, 0);
+              OZ_MMA(1, 3, 3, 0);
+              OZ_MMA(2, 2, 3, 0);
+              OZ_MMA(3, 1, 3, 0);
+              OZ_MMA(4, 0, 3, 0);
+#undef OZ_MMA
+            }
+            mma_commit(empty0 + 8 * stage);
+            any = true;
+            if (++stage == OZ_STAGES) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(tfull0 + 8 * buf);
+          if (++buf == 2) { buf = 0; tphase ^= 1; }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (p.err) atomicExch(p.err, GPC_ERR_TIMEOUT);
+      }
+      // Drain: every MMA issued above completes before TMEM is released.
+      if (any) {
+        mma_commit(drain);
+        mbar_wait_drain(drain, 0);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
+    const int q = warp & 3;
+    int buf = 0;
+    uint32_t tphase = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < p.num_work && ok; w += gridDim.x) {
+      int tm, tn, c0, c1;
+      work_coords(p, w, tm, tn, c0, c1);
+      const int split = w % p.splits;
+      const int row = tm * OZ_BM + q * 32 + lane;
+      for (int c = c0; c < c1; ++c) {
+        if (!mbar_wait(tfull0 + 8 * buf, tphase, abort_flag)) { ok = false; break; }
+        fence_after();
+        const uint32_t tacc = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * OZ_ACC_COLS);
+        for (int cb = 0; cb < OZ_BN / 16; ++cb) {
+          float g2[16], g3[16], g4[16], g5[16];
+          tmem_ld16(tacc + 0 * OZ_BN + cb * 16, g2);
+          tmem_ld16(tacc + 1 * OZ_BN + cb * 16, g3);
+          tmem_ld16(tacc + 2 * OZ_BN + cb * 16, g4);
+          tmem_ld16(tacc + 3 * OZ_BN + cb * 16, g5);
+          tmem_wait_ld();
+          if (row < p.M) {
+            float2 *dst;
+            if (p.partial) dst = p.partial + ((size_t)split * p.M + row) * (size_t)p.N;
+            else dst = p.C + (long long)row * p.ldc;
+            const int col0 = tn * OZ_BN + cb * 16;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int col = col0 + i;
+              if (col >= p.N || (p.lower && col > row)) continue;
+              const float2 cv = dst[col];
+              dst[col] = df_add4(cv, p.alpha * g2[i], p.alpha * g3[i], p.alpha * g4[i], p.alpha * g5[i]);
+            }
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+        if (++buf == 2) { buf = 0; tphase ^= 1; }
+      }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      if (p.err) atomicExch(p.err, GPC_ERR_TIMEOUT);
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ splitting
+// Operand element (r, k) = src[r * rs + k * ks] for r < M, k < K.  Chunk 0
+// covers k in [0, first), chunk c >= 1 covers [first + 128 (c - 1), + 128).
+// Output planes: dst[p * plane + r * kpad + c * 128 + kk] (BF16), zero where
+// the operand has no element.  Grid: (chunks, rows_pad / 32), 256 threads.
+__global__ void __launch_bounds__(256)
+split_kernel(const double *src, long long rs, long long ks, int M, int K, int first, __nv_bfloat16 *dst,
+             long long plane, int kpad) {
+  __shared__ double tile[32][129];
+  const int c = blockIdx.x, r0 = blockIdx.y * 32;
+  const int kbeg = (c == 0) ? 0 : first + (c - 1) * OZ_CHUNK;
+  const int klen = (c == 0) ? min(first, K) : min(OZ_CHUNK, K - kbeg);
+  if (ks == 1) {
+    for (int idx = threadIdx.x; idx < 32 * 128; idx += blockDim.x) {
+      const int rr = idx >> 7, kk = idx & 127;
+      const int r = r0 + rr;
+      tile[rr][kk] = (r < M && kk < klen) ? src[(long long)r * rs + (kbeg + kk)] : 0.0;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < 32 * 128; idx += blockDim.x) {
+      const int kk = idx >> 5, rr = idx & 31;
+      const int r = r0 + rr;
+      tile[rr][kk] = (r < M && kk < klen) ? src[(long long)r * rs + (long long)(kbeg + kk) * ks] : 0.0;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int rr = warp * 4; rr < warp * 4 + 4; ++rr) {
+    unsigned long long bits[4];
+    int ex = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      bits[i] = (unsigned long long)__double_as_longlong(tile[rr][lane * 4 + i]);
+      const int e = (int)((bits[i] >> 52) & 0x7FF);
+      ex = max(ex, (e == 0x7FF) ? 0 : e);
+    }
+    const int emax = __reduce_max_sync(0xffffffffu, ex);
+    unsigned short out[OZ_S][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = (int)((bits[i] >> 52) & 0x7FF);
+      unsigned long long X = 0;
+      if (e != 0 && e != 0x7FF && emax != 0) {
+        const unsigned long long mant = (bits[i] & ((1ull << 52) - 1)) | (1ull << 52);
+        const int sh = 53 - 8 * OZ_S + (emax - e);  // >= 13
+        if (sh < 64) X = (mant + (1ull << (sh - 1))) >> sh;
+      }
+      const bool neg = (bits[i] >> 63) != 0;
+      // Balanced digits, least significant first: d in [-128, 127], carry up.
+      int dig[OZ_S];
+#pragma unroll
+      for (int pp = OZ_S - 1; pp >= 1; --pp) {
+        int t = (int)(X & 255u);
+        X >>= 8;
+        if (t >= 128) {
+          t -= 256;
+          X += 1;
+        }
+        dig[pp] = t;
+      }
+      dig[0] = (int)X;  // in [0, 256]
+      // e_chunk = emax - 1023 + 1: slice p (0-based) carries 2^(e_chunk - 8 (p + 1))
+#pragma unroll
+      for (int pp = 0; pp < OZ_S; ++pp) {
+        const int fexp = (emax - 1023 + 1) - 8 * (pp + 1) + 127;  // FP32 biased exponent of the scale
+        float v = 0.0f;
+        if (dig[pp] != 0 && fexp >= 1 && fexp <= 254) v = (float)dig[pp] * __int_as_float(fexp << 23);
+        if (neg) v = -v;
+        out[pp][i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+      }
+    }
+    const int r = r0 + rr;
+#pragma unroll
+    for (int pp = 0; pp < OZ_S; ++pp) {
+      uint2 pack;
+      pack.x = (unsigned)out[pp][0] | ((unsigned)out[pp][1] << 16);
+      pack.y = (unsigned)out[pp][2] | ((unsigned)out[pp][3] << 16);
+      *(uint2 *)(dst + pp * plane + (long long)r * kpad + c * OZ_CHUNK + lane * 4) = pack;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ conversions
+__global__ void to_df_lower_kernel(int n, const double *src, long long lds, float2 *dst, long long ldd) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+  float2 v = make_float2(0.f, 0.f);
+  if (j <= i) {
+    const double x = src[(long long)i * lds + j];
+    const float hi = __double2float_rn(x);
+    v = make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+  dst[(long long)i * ldd + j] = v;
+}
+
+__global__ void from_df_rect_kernel(int m, int c, double *p, long long ld) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * c) return;
+  const int i = (int)(idx / c), j = (int)(idx - (long long)i * c);
+  double *q = p + (long long)i * ld + j;
+  const float2 v = *(const float2 *)q;
+  *q = (double)v.x + (double)v.y;
+}
+
+__global__ void df_reduce_kernel(int M, int N, int splits, const float2 *partial, float2 *C, long long ldc,
+                                 int lower) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)M * N) return;
+  const int row = (int)(idx / N), col = (int)(idx - (long long)row * N);
+  if (lower && col > row) return;
+  float2 acc = C[(long long)row * ldc + col];
+  for (int s = 0; s < splits; ++s) acc = df_add(acc, partial[(size_t)s * M * N + idx]);
+  C[(long long)row * ldc + col] = acc;
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap *m, const SliceBuf &b, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)b.kpad, (cuuint64_t)b.rows_pad, (cuuint64_t)OZ_S};
+  cuuint64_t strides[2] = {(cuuint64_t)b.kpad * 2, (cuuint64_t)b.rows_pad * b.kpad * 2};
+  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)b.base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool g_oz_attr[64];
+
+}  // namespace
+
+int slices_count() { return OZ_S; }
+int slice_chunk() { return OZ_CHUNK; }
+
+size_t slice_bytes(int rows, int kchunks) {
+  const size_t rp = align_up((size_t)std::max(rows, 1), OZ_BM);
+  return align_up((size_t)OZ_S * rp * (size_t)kchunks * OZ_CHUNK * 2, 1024);
+}
+
+SliceBuf slice_view(void *base, int rows, int kchunks) {
+  SliceBuf b;
+  b.base = base;
+  b.rows_pad = (int)align_up((size_t)std::max(rows, 1), OZ_BM);
+  b.kpad = kchunks * OZ_CHUNK;
+  return b;
+}
+
+cudaError_t split_operand(const double *src, long long rs, long long ks, int M, int K, int first,
+                          const SliceBuf &out, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  const int chunks = out.kpad / OZ_CHUNK;
+  dim3 grid((unsigned)chunks, (unsigned)(out.rows_pad / 32));
+  const long long plane = (long long)out.rows_pad * out.kpad;
+  GPC_LAUNCH(GPC_TRACE_SPLIT, 0.0, 8.0 * M * K + 2.0 * OZ_S * (double)out.rows_pad * out.kpad, s,
+             split_kernel<<<grid, 256, 0, s>>>(src, rs, ks, M, K, first, (__nv_bfloat16 *)out.base, plane,
+                                               out.kpad));
+  return cudaGetLastError();
+}
+
+size_t ozaki_partial_bytes(int M, int N, int splits) {
+  return splits > 1 ? align_up((size_t)splits * M * N * sizeof(float2), 256) : 0;
+}
+
+cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &B, int b_row0, int b_k0,
+                       int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
+                       int splits, float2 *partial, int *err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || chunks <= 0) return cudaSuccess;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, OZ_BM) || !make_map(&mb, B, OZ_BN)) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !g_oz_attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    g_oz_attr[dev] = true;
+  }
+  OzParams p;
+  p.M = M;
+  p.N = N;
+  p.chunks = chunks;
+  p.a_row0 = a_row0;
+  p.b_row0 = b_row0;
+  p.a_k0 = a_k0;
+  p.b_k0 = b_k0;
+  p.lower = lower ? 1 : 0;
+  splits = std::max(1, std::min(splits, chunks));
+  p.splits = splits;
+  p.tiles_m = (M + OZ_BM - 1) / OZ_BM;
+  p.tiles_n = (N + OZ_BN - 1) / OZ_BN;
+  long long tiles = 0;
+  if (lower) {
+    for (int tm = 0; tm < p.tiles_m; ++tm) tiles += std::min(p.tiles_n, (tm * OZ_BM + OZ_BM - 1) / OZ_BN + 1);
+  } else {
+    tiles = (long long)p.tiles_m * p.tiles_n;
+  }
+  p.num_work = (int)(tiles * splits);
+  p.alpha = alpha;
+  p.C = C;
+  p.ldc = ldc;
+  p.partial = splits > 1 ? partial : nullptr;
+  p.err = err;
+  if (splits > 1) {
+    cudaError_t e = cudaMemsetAsync(partial, 0, (size_t)splits * M * N * sizeof(float2), s);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = std::min(p.num_work, sm_count());
+  const double mn = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
+  const double flops = 2.0 * mn * (double)chunks * OZ_CHUNK * 15.0;  // 15 slice products
+  GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, 16.0 * mn * chunks + (double)(M + N) * chunks * OZ_CHUNK * 2 * OZ_S, s,
+             ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  const long long total = (long long)M * N;
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (splits + 2) * mn, s,
+             df_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, N, splits, partial, C, ldc,
+                                                                           lower ? 1 : 0));
+  return cudaGetLastError();
+}
+
+cudaError_t to_df_lower(int n, const double *src, long long lds, double *dst, long long ldd, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long total = (long long)n * n;
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 12.0 * (double)total, s,
+             to_df_lower_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, src, lds, (float2 *)dst, ldd));
+  return cudaGetLastError();
+}
+
+cudaError_t from_df_rect(int m, int c, double *p, long long ld, cudaStream_t s) {
+  if (m <= 0 || c <= 0) return cudaSuccess;
+  const long long total = (long long)m * c;
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 16.0 * (double)total, s,
+             from_df_rect_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(m, c, p, ld));
+  return cudaGetLastError();
+}
+
+}  // namespace gpc

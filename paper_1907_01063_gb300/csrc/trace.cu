@@ -92,30 +92,37 @@ void trace_end(int cls, double flops, double bytes, cudaStream_t s) {
 
 namespace {
 
-// Issue-rate kernel for the FP64 tensor peak: two independent accumulator
-// chains of mma.sync m16n8k16 .f64 per warp, nothing else in the loop.
-constexpr int kPeakIters = 2048;
-__global__ void __launch_bounds__(256) fp64_peak_kernel(double *sink, double av, double bv) {
-  double a[8], b[4], c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+// Issue-rate kernel for the FP64 tensor peak: per warp, eight independent
+// accumulator chains of mma.sync m16n8k16 .f64, each with its own A and B
+// fragments so that no two chains compute the same values (identical chains
+// could legally be merged by the compiler and would overstate the rate).
+constexpr int kPeakIters = 512;
+constexpr int kPeakChains = 8;
+__global__ void __launch_bounds__(128) fp64_peak_kernel(double *sink, double av, double bv) {
+  double a[kPeakChains][8], b[4], c[kPeakChains][4];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) a[k] = av + k * 1e-13 + threadIdx.x * 1e-12;
+  for (int q = 0; q < kPeakChains; ++q) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[q][k] = av + q * 1e-3 + k * 1e-13 + threadIdx.x * 1e-12;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) c[q][r] = 0.0;
+  }
 #pragma unroll
   for (int k = 0; k < 4; ++k) b[k] = bv + k * 1e-13;
   for (int i = 0; i < kPeakIters; ++i) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
-        "{%4,%5,%6,%7,%8,%9,%10,%11}, {%12,%13,%14,%15}, {%0,%1,%2,%3};\n"
-        : "+d"(c0[0]), "+d"(c0[1]), "+d"(c0[2]), "+d"(c0[3])
-        : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(a[4]), "d"(a[5]), "d"(a[6]), "d"(a[7]),
-          "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
-        "{%4,%5,%6,%7,%8,%9,%10,%11}, {%12,%13,%14,%15}, {%0,%1,%2,%3};\n"
-        : "+d"(c1[0]), "+d"(c1[1]), "+d"(c1[2]), "+d"(c1[3])
-        : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(a[4]), "d"(a[5]), "d"(a[6]), "d"(a[7]),
-          "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
+#pragma unroll
+    for (int q = 0; q < kPeakChains; ++q)
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
+          "{%4,%5,%6,%7,%8,%9,%10,%11}, {%12,%13,%14,%15}, {%0,%1,%2,%3};\n"
+          : "+d"(c[q][0]), "+d"(c[q][1]), "+d"(c[q][2]), "+d"(c[q][3])
+          : "d"(a[q][0]), "d"(a[q][1]), "d"(a[q][2]), "d"(a[q][3]), "d"(a[q][4]), "d"(a[q][5]),
+            "d"(a[q][6]), "d"(a[q][7]), "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
   }
-  sink[blockIdx.x * blockDim.x + threadIdx.x] = c0[0] + c0[1] + c0[2] + c0[3] + c1[0] + c1[1] + c1[2] + c1[3];
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < kPeakChains; ++q) s += c[q][0] + c[q][1] + c[q][2] + c[q][3];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 }  // namespace
@@ -126,7 +133,7 @@ using namespace gpc;
 extern "C" {
 
 int gpc_fp64_peak(void *ws, size_t ws_bytes, double *gflops, gpc_stream_t stream) {
-  const int blocks = sm_count() * 8, threads = 256;
+  const int blocks = sm_count() * 8, threads = 128;
   if (!ws || !gflops || ws_bytes < (size_t)blocks * threads * sizeof(double)) return GPC_ERR_INVALID_ARG;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GPC_ERR_CUDA;
@@ -139,7 +146,7 @@ int gpc_fp64_peak(void *ws, size_t ws_bytes, double *gflops, gpc_stream_t stream
     err = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-    const double flops = 2.0 * 16 * 8 * 16 * 2.0 * kPeakIters * (double)blocks * (threads / 32);
+    const double flops = 2.0 * 16 * 8 * 16 * kPeakChains * (double)kPeakIters * blocks * (threads / 32);
     if (err == cudaSuccess && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e9);
   }
   cudaEventDestroy(e0);

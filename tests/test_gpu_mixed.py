@@ -1,0 +1,118 @@
+"""Mixed-precision path: split-BF16 tensor-core products against exact values
+and the FP64 oracle, through the C ABI.
+
+The product's error model: each K chunk is exact in its three high-order
+slice groups (integer sums below 2^24) and rounded only 2^-32 below them;
+the 40-bit split and the dropped slice pairs leave about 2^-38 relative to
+max|a| max|b| per chunk; accumulation is in double-float (about 2^-48).  Tolerances below are stated
+against that model (with a safety factor), or as exact equality where the
+operands have few enough significant bits for every step to be exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1907_01063_gb300 as gp
+from oracle import oracle as O
+from paper_1907_01063_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def int_operand(rows, k, bits, seed):
+    g = np.random.default_rng(seed)
+    return g.integers(-(2 ** bits - 1), 2 ** bits, size=(rows, k)).astype(np.int64)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (5, 7, 16), (128, 64, 128), (130, 70, 128), (257, 129, 100)])
+def test_ozaki_exact_on_16_bit_operands(M, N, K):
+    # 16-bit integer operands scaled by 2^-16: two slices hold them exactly, all
+    # partial sums stay below 2^24, so the product must be exact.
+    a = int_operand(M, K, 16, 1)
+    b = int_operand(N, K, 16, 2)
+    exact = (a @ b.T)  # |entries| < K 2^32 < 2^40: exact in int64 and in float64
+    C = gp.test_ozaki_gemm(dev(a * 2.0 ** -16), dev(b * 2.0 ** -16)).cpu().numpy()
+    assert np.array_equal(C, exact.astype(np.float64) * 2.0 ** -32)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (64, 64, 64), (128, 128, 128), (200, 130, 129),
+                                   (300, 257, 513), (128, 1000, 4096)])
+def test_ozaki_accuracy_random(M, N, K):
+    g = np.random.default_rng(M + N + K)
+    A = g.standard_normal((M, K))
+    B = g.standard_normal((N, K))
+    ref = A @ B.T
+    C = gp.test_ozaki_gemm(dev(A), dev(B)).cpu().numpy()
+    bound = np.abs(A) @ np.abs(B).T
+    err = np.abs(C - ref)
+    assert np.all(err <= 2.0 ** -35 * bound + 1e-300), float(np.max(err / bound))
+
+
+def test_ozaki_wide_dynamic_range():
+    g = np.random.default_rng(7)
+    # per-row scales of both operands are absorbed by the per-(row, chunk) exponents
+    A = g.standard_normal((130, 256)) * np.exp(g.uniform(-20, 20, size=(130, 1)))
+    B = g.standard_normal((90, 256)) * np.exp(g.uniform(-20, 20, size=(90, 1)))
+    ref = A @ B.T
+    C = gp.test_ozaki_gemm(dev(A), dev(B)).cpu().numpy()
+    bound = np.abs(A) @ np.abs(B).T
+    assert np.all(np.abs(C - ref) <= 2.0 ** -34 * bound)
+
+
+def se_problem(n, d=3, seed=0, jitter=1e-6, rho=1.0, sigma=0.3):
+    X = W.gp_inputs(n, d, seed)
+    return X, O.se_cov(X, 1.0, rho, sigma, jitter)
+
+
+MIXED_SIZES = [1, 2, 17, 127, 128, 129, 200, 257, 300, 513]
+
+
+@pytest.mark.parametrize("n", MIXED_SIZES)
+def test_chol_mixed_close_to_oracle(n):
+    _, K = se_problem(n, seed=n)
+    L = gp.chol(dev(K), precision="mixed").cpu().numpy()
+    Lo = O.chol(K)
+    assert np.all(np.triu(L, 1) == 0)
+    assert rel(L, Lo) <= 1e-9
+    ld, ldo = 2 * np.log(np.diag(L)).sum(), 2 * np.log(np.diag(Lo)).sum()
+    assert abs(ld - ldo) <= 1e-11 * max(1.0, abs(ldo))
+
+
+def test_chol_mixed_known_factor_and_in_place():
+    n = 700
+    L0 = W.known_factor(n, seed=3)
+    K = dev(L0) @ dev(L0).T
+    L = gp.chol(K.clone(), precision="mixed").cpu().numpy()
+    assert rel(L, L0) <= 1e-9
+    Kc = K.clone()
+    gp.chol(Kc, precision="mixed", out=Kc)
+    assert np.array_equal(Kc.cpu().numpy(), L)
+
+
+def test_chol_mixed_not_pd():
+    _, K = se_problem(300, seed=1)
+    K = K.copy()
+    K[200, 200] = -1.0
+    info = gp.new_info()
+    gp.chol(dev(K), precision="mixed", info=info, check=False)
+    assert info.tolist() == [200, gp.GPC_ERR_NOT_PD]
+
+
+@pytest.mark.parametrize("n", MIXED_SIZES)
+def test_adjoint_mixed_close_to_oracle(n):
+    _, K = se_problem(n, seed=20 + n, jitter=1e-4)
+    Lo = O.chol(K)
+    Lbar = W.random_lower(n, seed=n)
+    G = gp.chol_adjoint(dev(Lo), dev(Lbar), precision="mixed").cpu().numpy()
+    Go = O.chol_adjoint(Lo, Lbar)
+    assert np.all(np.triu(G, 1) == 0)
+    assert rel(G, Go) <= 1e-9
