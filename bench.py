@@ -46,7 +46,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--d", type=int, default=16)
-    p.add_argument("--precision", choices=["fp64"], default="fp64")
+    p.add_argument("--precision", choices=["fp64", "mixed", "both"], default="both",
+                   help="both: time the FP64 and the mixed path; the headline is the mixed path")
     p.add_argument("--block", type=int, default=0, help="block size b (0: library default)")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-sample", type=int, default=3072,
@@ -237,114 +238,128 @@ def main():
     dev = torch.device("cuda", local)
     if args.block:
         gp.set_tuning(gp.GPC_TUNE_BLOCK, args.block)
-    b = gp.get_tuning(gp.GPC_TUNE_BLOCK)
-    n, d, prec = args.n, args.d, args.precision
+    n, d = args.n, args.d
     X, y, hyp, jitter = workload(n, d)
     a, r, s = hyp
-    step_flops = chol_flops(n) + adjoint_flops(n, b)
+    precisions = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
 
     Xd = torch.as_tensor(X, device=dev)
     yd = torch.as_tensor(y, device=dev)
     K = torch.empty(n, n, dtype=torch.float64, device=dev)
     L = torch.empty_like(K)
     Kbar = torch.empty_like(K)
-    ws = gp.workspace(n, prec, dev)
+    ws = gp.workspace(n, "mixed" if "mixed" in precisions else "fp64", dev)
     hws = torch.empty(gp.se_hyper_grad_workspace_size(n), dtype=torch.uint8, device=dev)
     info = gp.new_info(dev)
     g3 = torch.empty(3, dtype=torch.float64, device=dev)
-
-    def step(Xs, ys):
-        gp.se_cov(Xs, a, r, s, jitter, out=K)
-        res = gp.gp_lml(K, ys, prec, L=L, ws=ws, info=info, check=False)
-        gp.gp_lml_grad(L, res["alpha"], 1.0, prec, out=Kbar, ws=ws)
-        gp.se_hyper_grad(Xs, a, r, s, Kbar, ws=hws, out=g3)
-        return res
+    stream = torch.cuda.current_stream()
 
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        res = step(Xd, yd)
-    barrier()
-    gp.check_info(info, "warm-up step")
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    gp.trace_enable(True)
-    launches0 = gp.launch_count()
-    barrier()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        res = step(Xd, yd)
-    ev1.record(stream)
-    barrier()
-    launches = gp.launch_count() - launches0
-    elapsed_ms = ev0.elapsed_time(ev1)
-    trace = gp.trace_summary()
-    gp.trace_enable(False)
-    clk = clocks.stop()
-    gp.check_info(info, "timed step")
-    value_rank = res["value"].item()
-    grad_rank = g3.tolist()
-
-    t_max = elapsed_ms
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = t.item()
-    value = world * args.steps * step_flops / (t_max / 1e3) / 1e9
+        return t.item()
 
-    # end to end: pinned host inputs in, scalars out, every step
-    Xh = torch.as_tensor(X).pin_memory()
-    yh = torch.as_tensor(y).pin_memory()
-    out_h = torch.empty(4, dtype=torch.float64).pin_memory()
-    Xe = torch.empty_like(Xd)
-    ye = torch.empty_like(yd)
-    e2e_steps = max(1, args.e2e_steps)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        Xe.copy_(Xh, non_blocking=True)
-        ye.copy_(yh, non_blocking=True)
-        res_e = step(Xe, ye)
-        out_h[0:1].copy_(res_e["value"].reshape(1), non_blocking=True)
-        out_h[1:4].copy_(g3, non_blocking=True)
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
-    e2e_value = world * e2e_steps * step_flops / (e2e_ms / 1e3) / 1e9
+    def run(prec):
+        b = gp.get_tuning(gp.GPC_TUNE_BLOCK) if prec == "fp64" else 128
+        step_flops = chol_flops(n) + adjoint_flops(n, b)
 
-    # roofline of the dominant kernel class (largest device time in the trace)
-    dom_name, dom = max(((k, v) for k, v in trace.items() if v["launches"]), key=lambda kv: kv[1]["ms"])
-    fp64_peak = gp.fp64_peak_gflops() if hasattr(gp, "fp64_peak_gflops") else None
+        def step(Xs, ys):
+            gp.se_cov(Xs, a, r, s, jitter, out=K)
+            res = gp.gp_lml(K, ys, prec, L=L, ws=ws, info=info, check=False)
+            gp.gp_lml_grad(L, res["alpha"], 1.0, prec, out=Kbar, ws=ws)
+            gp.se_hyper_grad(Xs, a, r, s, Kbar, ws=hws, out=g3)
+            return res
+
+        for _ in range(args.warmup):
+            res = step(Xd, yd)
+        barrier()
+        gp.check_info(info, f"warm-up step ({prec})")
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gp.trace_enable(True)
+        launches0 = gp.launch_count()
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step(Xd, yd)
+        ev1.record(stream)
+        barrier()
+        launches = gp.launch_count() - launches0
+        t_ms = max_over_ranks(ev0.elapsed_time(ev1))
+        trace = gp.trace_summary()
+        gp.trace_enable(False)
+        clk = clocks.stop()
+        st = info.tolist()
+        if st[1] not in (gp.GPC_OK, gp.GPC_ERR_NO_CONVERGENCE):
+            gp.check_info(info, f"timed step ({prec})")
+        out = {"prec": prec, "block": b, "step_flops": step_flops, "t_ms": t_ms, "launches": launches,
+               "trace": trace, "clocks": clk, "value": world * args.steps * step_flops / (t_ms / 1e3) / 1e9,
+               "lml": res["value"].item(), "logdet": res["logdet"].item(), "grad": g3.tolist(),
+               "refine_status": st[1]}
+        # end to end: pinned host inputs in, scalars out, every step
+        Xh = torch.as_tensor(X).pin_memory()
+        yh = torch.as_tensor(y).pin_memory()
+        out_h = torch.empty(4, dtype=torch.float64).pin_memory()
+        Xe, ye = torch.empty_like(Xd), torch.empty_like(yd)
+        e2e_steps = max(1, args.e2e_steps)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            Xe.copy_(Xh, non_blocking=True)
+            ye.copy_(yh, non_blocking=True)
+            res_e = step(Xe, ye)
+            out_h[0:1].copy_(res_e["value"].reshape(1), non_blocking=True)
+            out_h[1:4].copy_(g3, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+        out["e2e"] = {"value": world * e2e_steps * step_flops / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+                      "h2d_bytes_per_step": Xh.numel() * 8 + yh.numel() * 8, "d2h_bytes_per_step": 32,
+                      "ms_per_step": e2e_ms / e2e_steps}
+        return out
+
+    results = {p_: run(p_) for p_ in precisions}
+
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    fp64_peak = gp.fp64_peak_gflops(dev)
     nominal_fp64 = peaks.get("bf16_tflops", 1900.0) * 1e3 * 1.25 / 2250.0
-    if dom_name.startswith("gemm") or dom_name == "diag":
-        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0
-        peak = fp64_peak if fp64_peak else nominal_fp64
-        roof = {"kernel": "gemm_f64_kernel (FP64 mma.sync m16n8k16)" if dom_name == "gemm_f64" else dom_name,
-                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
-                "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1),
-                "peak_source": ("FP64 DMMA m16n8k16 throughput measured in this run"
-                                if fp64_peak else "of fallback: bf16 burst x 1.25/2250"),
-                "peak_nominal_ratio": nominal_fp64}
-    else:
+
+    def roofline(res):
+        trace = res["trace"]
+        dom_name, dom = max(((k, v) for k, v in trace.items() if v["launches"]), key=lambda kv: kv[1]["ms"])
+        avg = dom["ms"] / max(dom["launches"], 1)
+        if dom_name == "gemm_mixed":
+            peak = peaks.get("bf16_tflops_sustained", 1695.9)
+            achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12 if dom["ms"] else 0.0
+            return {"kernel": "ozaki_gemm_kernel (tcgen05 BF16 slice products, 15 per FP64 product)",
+                    "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "launches": dom["launches"],
+                    "avg_launch_ms": avg, "peak_source": "of measured: MEASURED_PEAKS bf16_tflops_sustained",
+                    "fp64_equivalent_gflops": dom["flops"] / 15.0 / (dom["ms"] / 1e3) / 1e9}
+        if dom_name in ("gemm_f64", "diag"):
+            achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0
+            return {"kernel": ("gemm_f64_kernel (FP64 mma.sync m16n8k16)" if dom_name == "gemm_f64"
+                               else "potrf_trtri_kernel"),
+                    "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None, "launches": dom["launches"],
+                    "avg_launch_ms": avg,
+                    "peak_source": "of measured: FP64 DMMA m16n8k16 issue rate measured in this run (gpc_fp64_peak)",
+                    "peak_nominal_ratio": nominal_fp64}
         achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0
         peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1)}
+        return {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "launches": dom["launches"], "avg_launch_ms": avg,
+                "peak_source": "of measured: MEASURED_PEAKS hbm_gbs"}
 
     if rank != 0:
         if world > 1:
@@ -353,22 +368,44 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(args.cpu_sample, d, hyp)
-    h2d = Xh.numel() * 8 + yh.numel() * 8
+    head = results["mixed"] if "mixed" in results else results["fp64"]
+    prec = head["prec"]
+
+    def summary(res):
+        return {"value": res["value"], "unit": "GFLOP/s", "ms_per_step": res["t_ms"] / args.steps,
+                "gpu_launches": res["launches"], "roofline": roofline(res), "e2e": res["e2e"],
+                "lml": res["lml"], "logdet": res["logdet"], "grad": res["grad"], "clocks": res["clocks"],
+                "kernel_time_ms": {k: round(v["ms"], 3) for k, v in res["trace"].items() if v["launches"]}}
+
     line = {
-        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": describe(n, d, hyp, b, prec),
-        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": 32, "ms_per_step": e2e_ms / e2e_steps},
-        "gpu_launches": launches,
-        "roofline": roof,
+        "metric": METRIC, "value": head["value"], "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["t_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x5+f64" if prec == "mixed" else "f64", "data": "synthetic",
+        "config": describe(n, d, hyp, head["block"], prec),
+        "e2e": head["e2e"],
+        "gpu_launches": head["launches"],
+        "roofline": roofline(head),
         "cpu_baseline": cpu,
-        "clocks": clk,
-        "lml": value_rank, "grad": grad_rank,
-        "flops_per_step": step_flops,
-        "kernel_time_ms": {k: round(v["ms"], 3) for k, v in trace.items() if v["launches"]},
+        "clocks": head["clocks"],
+        "flops_per_step": head["step_flops"],
+        "kernel_time_ms": {k: round(v["ms"], 3) for k, v in head["trace"].items() if v["launches"]},
     }
+    if "fp64" in results and "mixed" in results:
+        f, m = results["fp64"], results["mixed"]
+        gf, gm = f["grad"], m["grad"]
+        line["fp64"] = summary(f)
+        line["mixed"] = summary(m)
+        line["mixed_vs_fp64"] = {
+            "speedup": m["value"] / f["value"],
+            "lml_rel_err": abs(m["lml"] - f["lml"]) / abs(f["lml"]),
+            "logdet_rel_err": abs(m["logdet"] - f["logdet"]) / abs(f["logdet"]),
+            "grad_rel_err": math.sqrt(sum((x - y_) ** 2 for x, y_ in zip(gm, gf)) / sum(y_ ** 2 for y_ in gf)),
+            "meets_lml_1e-8": abs(m["lml"] - f["lml"]) / abs(f["lml"]) <= 1e-8,
+            "refine_status": m["refine_status"],
+        }
+    else:
+        line.update({"lml": head["lml"], "grad": head["grad"]})
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

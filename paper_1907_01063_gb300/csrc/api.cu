@@ -29,9 +29,13 @@ namespace {
 
 struct ApiWs {
   void *core;
-  double *vec;  // 4 n doubles
-  int *flags;   // triangular-solve tickets and ready flags
+  double *vec;   // 4 n doubles
+  void *refine;  // refinement residual, partial norms and state
+  int *flags;    // triangular-solve tickets and ready flags
 };
+
+constexpr int kRefineMaxIters = 10;
+constexpr double kRefineTol = 1e-14;
 
 size_t core_bytes(int n, int precision) {
   size_t c = std::max(chol_workspace_bytes(n, precision), adjoint_workspace_bytes(n, precision));
@@ -44,7 +48,7 @@ bool valid_precision(int p) { return p == GPC_FP64 || p == GPC_MIXED; }
 
 size_t total_bytes(int n, int precision) {
   return core_bytes(n, precision) + align_up(4 * (size_t)std::max(n, 1) * sizeof(double), 256) +
-         trsv_workspace_bytes(std::max(n, 1));
+         refine_workspace_bytes(std::max(n, 1)) + trsv_workspace_bytes(std::max(n, 1));
 }
 
 ApiWs carve(void *ws, int n, int precision) {
@@ -54,6 +58,8 @@ ApiWs carve(void *ws, int n, int precision) {
   p += core_bytes(n, precision);
   w.vec = (double *)p;
   p += align_up(4 * (size_t)std::max(n, 1) * sizeof(double), 256);
+  w.refine = p;
+  p += refine_workspace_bytes(std::max(n, 1));
   w.flags = (int *)p;
   return w;
 }
@@ -195,7 +201,7 @@ int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, si
 int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int ldl,
                int precision, double *logdet, double *alpha, double *value, void *ws,
                size_t ws_bytes, int *info, gpc_stream_t stream) {
-  if (n < 0 || precision != GPC_FP64 || !info || !logdet || !value) return GPC_ERR_INVALID_ARG;
+  if (n < 0 || !valid_precision(precision) || !info || !logdet || !value) return GPC_ERR_INVALID_ARG;
   if (n == 0) {
     cudaError_t e = reset_info(info, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(logdet, 0, sizeof(double), stream);
@@ -206,7 +212,7 @@ int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int 
       ws_bytes < total_bytes(n, precision))
     return GPC_ERR_INVALID_ARG;
   if ((const void *)K == (const void *)L) {
-    if (ldk != ldl) return GPC_ERR_INVALID_ARG;
+    if (ldk != ldl || precision == GPC_MIXED) return GPC_ERR_INVALID_ARG;
   } else if (overlaps(K, mat_bytes(n, ldk), L, mat_bytes(n, ldl))) {
     return GPC_ERR_INVALID_ARG;
   }
@@ -215,11 +221,18 @@ int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int 
     return GPC_ERR_INVALID_ARG;
   ApiWs w = carve(ws, n, precision);
   cudaError_t e = reset_info(info, stream);
-  if (e == cudaSuccess) e = copy_lower(n, K, ldk, L, ldl, stream);
-  if (e == cudaSuccess) e = chol_fp64(n, L, ldl, w.core, info, stream);
+  if (precision == GPC_MIXED) {
+    if (e == cudaSuccess) e = to_df_lower(n, K, ldk, L, ldl, stream);
+    if (e == cudaSuccess) e = chol_mixed(n, L, ldl, w.core, info, stream);
+  } else {
+    if (e == cudaSuccess) e = copy_lower(n, K, ldk, L, ldl, stream);
+    if (e == cudaSuccess) e = chol_fp64(n, L, ldl, w.core, info, stream);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(alpha, y, n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
   if (e == cudaSuccess) e = trsv(n, L, ldl, alpha, 0, w.flags, info, stream);
   if (e == cudaSuccess) e = trsv(n, L, ldl, alpha, 1, w.flags, info, stream);
+  if (precision == GPC_MIXED && e == cudaSuccess)
+    e = refine(n, K, ldk, L, ldl, y, alpha, w.refine, w.flags, info, kRefineMaxIters, kRefineTol, stream);
   if (e == cudaSuccess) e = lml_finalize(n, L, ldl, y, alpha, logdet, value, stream);
   return status_of(e);
 }
@@ -227,7 +240,7 @@ int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int 
 int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double gbar,
                     double *Kbar, int ldkb, int precision, void *ws, size_t ws_bytes,
                     gpc_stream_t stream) {
-  if (n < 0 || precision != GPC_FP64) return GPC_ERR_INVALID_ARG;
+  if (n < 0 || !valid_precision(precision)) return GPC_ERR_INVALID_ARG;
   if (n == 0) return GPC_OK;
   if (bad_square(n, L, ldl) || bad_square(n, Kbar, ldkb) || !alpha || !ws ||
       ws_bytes < total_bytes(n, precision))
@@ -237,7 +250,12 @@ int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double
   double *z = w.vec;
   cudaError_t e = ltv(n, L, ldl, alpha, z, w.core, stream);
   if (e == cudaSuccess) e = lml_lbar(n, L, ldl, alpha, z, gbar, Kbar, ldkb, stream);
-  if (e == cudaSuccess) e = chol_adjoint_fp64(n, L, ldl, Kbar, ldkb, w.core, stream);
+  if (precision == GPC_MIXED) {
+    if (e == cudaSuccess) e = to_df_lower(n, Kbar, ldkb, Kbar, ldkb, stream);
+    if (e == cudaSuccess) e = chol_adjoint_mixed(n, L, ldl, Kbar, ldkb, w.core, w.flags, stream);
+  } else {
+    if (e == cudaSuccess) e = chol_adjoint_fp64(n, L, ldl, Kbar, ldkb, w.core, stream);
+  }
   return status_of(e);
 }
 

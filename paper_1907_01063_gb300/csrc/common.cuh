@@ -77,8 +77,16 @@ size_t trsv_workspace_bytes(int n);
 cudaError_t chol_fp64(int n, double *L, long long ldl, void *ws, int *info, cudaStream_t s);
 cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, long long lda,
                               void *ws, cudaStream_t s);
+// skip (device int, may be null): when *skip != 0 the solve does nothing.
 cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, void *ws,
-                 int *info, cudaStream_t s);
+                 int *info, cudaStream_t s, const int *skip = nullptr);
+// FP64 iterative refinement of K x = y with the factor L (Section 3.2 solves):
+// r = y - K x, x += L^{-T} L^{-1} r, until |r| <= tol |y|, the residual stops
+// halving, or max_iters corrections; info[1] = GPC_ERR_NO_CONVERGENCE otherwise.
+size_t refine_workspace_bytes(int n);
+cudaError_t refine(int n, const double *K, long long ldk, const double *L, long long ldl, const double *y,
+                   double *x, void *ws, void *trsv_ws, int *info, int max_iters, double tol,
+                   cudaStream_t s);
 
 // ---------------------------------------------------------------- GP pieces
 constexpr int kMaxDim = 256;

@@ -139,7 +139,9 @@ constexpr long long kSpinLimit = 1LL << 22;
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
 
 __global__ void __launch_bounds__(256)
-trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sync, int *info) {
+trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sync, int *info,
+            const int *skip) {
+  if (skip && *skip) return;  // the same value for every CTA: nothing waits on anything
   __shared__ int s_order, s_abort;
   __shared__ double diag[TB][TB + 1];
   __shared__ double red[4][TB];
@@ -370,14 +372,140 @@ size_t trsv_workspace_bytes(int n) {
 }
 
 cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, void *ws,
-                 int *info, cudaStream_t s) {
+                 int *info, cudaStream_t s, const int *skip) {
   if (n <= 0) return cudaSuccess;
   const int nblk = (n + TB - 1) / TB;
   int *sync = (int *)ws;
   cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nblk + 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n, 4.0 * (double)n * (n + 1) + 16.0 * n, s,
-             trsv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, x, trans ? 1 : 0, sync, info));
+             trsv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, x, trans ? 1 : 0, sync, info, skip));
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- iterative refinement
+namespace {
+
+// r = y - K x with K symmetric, read from its lower triangle.  One CTA per
+// 64-row block I: row segments K[i, 0..i] (i in I) and column segments
+// K[j, I] (j > first row of I) cover every stored entry that row block needs,
+// so each lower entry is read twice over the grid and nothing is atomic.
+// partial[block] = sum of r_i^2 over the block.
+constexpr int RB = 64;
+__global__ void __launch_bounds__(256)
+symv_residual_kernel(int n, const double *K, long long ldk, const double *y, const double *x, double *r,
+                     double *partial, const int *skip) {
+  if (skip && *skip) return;
+  __shared__ double part1[RB];
+  __shared__ double part2[4][RB];
+  __shared__ double red[8];
+  const int i0 = blockIdx.x * RB, rows = min(RB, n - i0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int rr = warp; rr < rows; rr += 8) {
+    const int i = i0 + rr;
+    const double *row = K + (long long)i * ldk;
+    double acc = 0.0;
+    for (int j = lane; j <= i; j += 32) acc = fma(row[j], x[j], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part1[rr] = acc;
+  }
+  const int c = threadIdx.x & (RB - 1), jg = threadIdx.x >> 6;
+  double acc2 = 0.0;
+  if (c < rows) {
+    for (int j = i0 + 1 + jg; j < n; j += 4)
+      if (j > i0 + c) acc2 = fma(K[(long long)j * ldk + i0 + c], x[j], acc2);
+  }
+  part2[jg][c] = acc2;
+  __syncthreads();
+  double rr2 = 0.0;
+  if (threadIdx.x < RB && threadIdx.x < rows) {
+    const int i = i0 + threadIdx.x;
+    const double kx = part1[threadIdx.x] + ((part2[0][threadIdx.x] + part2[1][threadIdx.x]) +
+                                            (part2[2][threadIdx.x] + part2[3][threadIdx.x]));
+    const double ri = y[i] - kx;
+    r[i] = ri;
+    rr2 = ri * ri;
+  }
+  const double tot = block_sum_256(rr2, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// state[0] = done flag, state[1] = corrections applied; norms[0] = |y|^2,
+// norms[1] = previous |r|^2.  Ends the refinement when |r| <= tol |y| or when
+// |r| stopped halving (the FP64 residual floor has been reached).
+__global__ void __launch_bounds__(256)
+refine_check_kernel(int nblk, const double *partial, double *norms, double tol2, int *state) {
+  __shared__ double red[8];
+  if (state[0]) return;
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += partial[b];
+  const double rr = block_sum_256(a, red);
+  if (threadIdx.x == 0) {
+    const bool small = rr <= tol2 * norms[0];
+    const bool stalled = state[1] > 0 && rr > 0.25 * norms[1];
+    if (small || stalled) state[0] = 1;
+    norms[1] = rr;
+  }
+}
+
+__global__ void refine_axpy_kernel(int n, double *x, const double *d, int *state) {
+  if (state[0]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += d[i];
+  if (i == 0) atomicAdd(&state[1], 1);
+}
+
+__global__ void __launch_bounds__(256)
+refine_init_kernel(int n, const double *y, double *norms, int *state) {
+  __shared__ double red[8];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(y[i], y[i], a);
+  const double yy = block_sum_256(a, red);
+  if (threadIdx.x == 0) {
+    norms[0] = yy;
+    norms[1] = 0.0;
+    state[0] = 0;
+    state[1] = 0;
+  }
+}
+
+__global__ void refine_finish_kernel(int *state, int *info) {
+  if (!state[0] && info && info[1] == 0) info[1] = GPC_ERR_NO_CONVERGENCE;
+}
+
+}  // namespace
+
+size_t refine_workspace_bytes(int n) {
+  const int nblk = (n + RB - 1) / RB;
+  return align_up((size_t)n * sizeof(double), 256) + align_up((size_t)nblk * sizeof(double), 256) + 256;
+}
+
+cudaError_t refine(int n, const double *K, long long ldk, const double *L, long long ldl, const double *y,
+                   double *x, void *ws, void *trsv_ws, int *info, int max_iters, double tol,
+                   cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nblk = (n + RB - 1) / RB;
+  char *p = (char *)ws;
+  double *r = (double *)p;
+  p += align_up((size_t)n * sizeof(double), 256);
+  double *partial = (double *)p;
+  p += align_up((size_t)nblk * sizeof(double), 256);
+  double *norms = (double *)p;
+  int *state = (int *)(p + 2 * sizeof(double));
+  GPC_LAUNCH(GPC_TRACE_ELEM, 2.0 * n, 8.0 * n, s, refine_init_kernel<<<1, 256, 0, s>>>(n, y, norms, state));
+  for (int it = 0; it <= max_iters; ++it) {
+    GPC_LAUNCH(GPC_TRACE_TRSV, 2.0 * (double)n * n, 8.0 * (double)n * (n + 1), s,
+               symv_residual_kernel<<<nblk, 256, 0, s>>>(n, K, ldk, y, x, r, partial, state));
+    GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * nblk, s,
+               refine_check_kernel<<<1, 256, 0, s>>>(nblk, partial, norms, tol * tol, state));
+    if (it == max_iters) break;
+    cudaError_t e = trsv(n, L, ldl, r, 0, trsv_ws, info, s, state);
+    if (e == cudaSuccess) e = trsv(n, L, ldl, r, 1, trsv_ws, info, s, state);
+    if (e != cudaSuccess) return e;
+    GPC_LAUNCH(GPC_TRACE_ELEM, (double)n, 24.0 * n, s,
+               refine_axpy_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, r, state));
+  }
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0, s, refine_finish_kernel<<<1, 1, 0, s>>>(state, info));
   return cudaGetLastError();
 }
 

@@ -116,3 +116,40 @@ def test_adjoint_mixed_close_to_oracle(n):
     Go = O.chol_adjoint(Lo, Lbar)
     assert np.all(np.triu(G, 1) == 0)
     assert rel(G, Go) <= 1e-9
+
+
+def cond_problem(n, d=4, seed=0, cond=1e5):
+    """SE covariance with sigma^2 = lambda_max / cond (an ill-conditioned GP)."""
+    X = W.gp_inputs(n, d, seed)
+    Kf = O.se_cov(X, 1.0, 2.0, 0.0, 0.0, full=True)
+    lam = np.linalg.eigvalsh(Kf)[-1]
+    sigma = float(np.sqrt(lam / cond))
+    y = W.gp_targets(X, 1.0, 2.0, sigma, seed=seed + 1)
+    return X, y, (1.0, 2.0, sigma)
+
+
+@pytest.mark.parametrize("n", [256, 1000])
+def test_gp_lml_mixed_with_refinement(n):
+    X, y, (a, r, s) = cond_problem(n)
+    ref = O.gp_lml_and_grad(X, y, a, r, s, 0.0)
+    K = gp.se_cov(dev(X), a, r, s, 0.0)
+    res = gp.gp_lml(K, dev(y), precision="mixed", check=False)
+    pivot, status = res["info"].tolist()
+    assert status == gp.GPC_OK, gp.status_string(status)
+    assert abs(res["value"].item() - ref["value"]) <= 1e-10 * abs(ref["value"])
+    assert abs(res["logdet"].item() - ref["logdet"]) <= 1e-10 * abs(ref["logdet"])
+    # the refined solve reaches FP64 accuracy for this conditioning
+    assert rel(res["alpha"].cpu().numpy(), ref["alpha"]) <= 1e-9
+    Kbar = gp.gp_lml_grad(res["L"], res["alpha"], 1.0, precision="mixed").cpu().numpy()
+    assert rel(Kbar, ref["Kbar"]) <= 1e-8
+    g = gp.se_hyper_grad(dev(X), a, r, s, dev(Kbar)).cpu().numpy()
+    # the hyperparameter gradient sums K-bar against dK with cancellation; at
+    # condition 1e5 FP64 rounding alone moves it by ~1e-9 relative
+    assert rel(g, ref["grad"]) <= 1e-7
+
+
+def test_gp_lml_mixed_rejects_in_place():
+    X, y, (a, r, s) = cond_problem(64)
+    K = gp.se_cov(dev(X), a, r, s, 0.0)
+    with pytest.raises(gp.GpcholError):
+        gp.gp_lml(K, dev(y), precision="mixed", L=K)
