@@ -46,9 +46,15 @@ size_t core_bytes(int n, int precision) {
 
 bool valid_precision(int p) { return p == GPC_FP64 || p == GPC_MIXED; }
 
+// Ticket and ready flags of either solve kernel (blocks of 64 rows, or of the
+// factorisation's block size, which is at least 16).
+size_t flags_bytes(int n) {
+  return std::max(trsv_workspace_bytes(std::max(n, 1)), align_up(((size_t)(n + 15) / 16 + 1) * sizeof(int), 256));
+}
+
 size_t total_bytes(int n, int precision) {
   return core_bytes(n, precision) + align_up(4 * (size_t)std::max(n, 1) * sizeof(double), 256) +
-         refine_workspace_bytes(std::max(n, 1)) + trsv_workspace_bytes(std::max(n, 1));
+         refine_workspace_bytes(std::max(n, 1)) + flags_bytes(n);
 }
 
 ApiWs carve(void *ws, int n, int precision) {
@@ -228,11 +234,15 @@ int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int 
     if (e == cudaSuccess) e = copy_lower(n, K, ldk, L, ldl, stream);
     if (e == cudaSuccess) e = chol_fp64(n, L, ldl, w.core, info, stream);
   }
+  // the factorisation left every diagonal-block inverse at the start of the core workspace
+  const double *inv = (const double *)w.core;
+  const int b = chol_block_size(precision);
   if (e == cudaSuccess) e = cudaMemcpyAsync(alpha, y, n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
-  if (e == cudaSuccess) e = trsv(n, L, ldl, alpha, 0, w.flags, info, stream);
-  if (e == cudaSuccess) e = trsv(n, L, ldl, alpha, 1, w.flags, info, stream);
+  if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, alpha, 0, w.flags, info, stream);
+  if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, alpha, 1, w.flags, info, stream);
   if (precision == GPC_MIXED && e == cudaSuccess)
-    e = refine(n, K, ldk, L, ldl, y, alpha, w.refine, w.flags, info, kRefineMaxIters, kRefineTol, stream);
+    e = refine(n, K, ldk, L, ldl, inv, b, y, alpha, w.refine, w.flags, info, kRefineMaxIters, kRefineTol,
+               stream);
   if (e == cudaSuccess) e = lml_finalize(n, L, ldl, y, alpha, logdet, value, stream);
   return status_of(e);
 }

@@ -38,12 +38,14 @@ struct AdjWs {
 
 size_t block_sz() { return (size_t)tuning().block; }
 
+size_t nblocks(int n) { return (size_t)std::max(1, (n + (int)block_sz() - 1) / (int)block_sz()); }
+
 CholWs carve_chol(void *ws, int n) {
   const size_t b = block_sz();
   char *p = (char *)ws;
   CholWs w;
-  w.inv = (double *)p;
-  p += align_up(b * b * sizeof(double), 256);
+  w.inv = (double *)p;  // every diagonal-block inverse, block i at inv + i b^2
+  p += align_up(nblocks(n) * b * b * sizeof(double), 256);
   w.panel = (double *)p;
   p += align_up((size_t)n * b * sizeof(double), 256);
   w.scratch = (double *)p;
@@ -54,8 +56,8 @@ AdjWs carve_adj(void *ws, int n) {
   const size_t b = block_sz();
   char *p = (char *)ws;
   AdjWs w;
-  w.dinv = (double *)p;
-  p += align_up(b * b * sizeof(double), 256);
+  w.dinv = (double *)p;  // every diagonal-block inverse (blocks counted from the bottom)
+  p += align_up(nblocks(n) * b * b * sizeof(double), 256);
   w.m = (double *)p;
   p += align_up(b * b * sizeof(double), 256);
   w.t = (double *)p;
@@ -76,15 +78,17 @@ AdjWs carve_adj(void *ws, int n) {
 
 size_t chol_workspace_bytes(int n, int /*precision*/) {
   const size_t b = block_sz();
-  return align_up(b * b * sizeof(double), 256) + align_up((size_t)n * b * sizeof(double), 256) +
+  return align_up(nblocks(n) * b * b * sizeof(double), 256) + align_up((size_t)n * b * sizeof(double), 256) +
          gemm_f64_scratch_bytes();
 }
 
 size_t adjoint_workspace_bytes(int n, int /*precision*/) {
   const size_t b = block_sz();
-  return 3 * align_up(b * b * sizeof(double), 256) +
+  return align_up(nblocks(n) * b * b * sizeof(double), 256) + 2 * align_up(b * b * sizeof(double), 256) +
          align_up((size_t)n * b * sizeof(double), 256) + gemm_f64_scratch_bytes();
 }
+
+int chol_block_size(int precision) { return precision == GPC_MIXED ? 128 : (int)block_sz(); }
 
 cudaError_t chol_fp64(int n, double *L, long long ldl, void *ws, int *info, cudaStream_t s) {
   const int b = tuning().block;
@@ -92,17 +96,10 @@ cudaError_t chol_fp64(int n, double *L, long long ldl, void *ws, int *info, cuda
   for (int k0 = 0; k0 < n; k0 += b) {
     const int nb = std::min(b, n - k0), m = n - k0 - nb;
     double *A11 = L + (long long)k0 * ldl + k0;
-    TRY(potrf_trtri_diag(nb, A11, ldl, w.inv, info, k0, s));
+    TRY(potrf_diag(nb, A11, ldl, info, k0, s));
     if (m <= 0) continue;
     double *A21 = L + (long long)(k0 + nb) * ldl + k0;
-    TRY(copy_rect(m, nb, A21, ldl, w.panel, nb, s));
-    Gemm g;  // L21 = A21 * L11^{-T}
-    g.M = m; g.N = nb; g.K = nb;
-    g.A = w.panel; g.lda = nb;
-    g.B = w.inv; g.ldb = nb; g.transB = true;
-    g.C = A21; g.ldc = ldl;
-    g.algo_flops = (double)m * nb * (nb + 1);  // triangular B
-    TRY(gemm_f64(g, w.scratch, s));
+    TRY(trsm_rows(m, nb, A21, ldl, A11, ldl, 0, s));  // L21 = A21 L11^{-T}
     Gemm u;  // A22 -= L21 L21^T (lower tiles)
     u.M = m; u.N = m; u.K = nb;
     u.A = A21; u.lda = ldl;
@@ -111,29 +108,26 @@ cudaError_t chol_fp64(int n, double *L, long long ldl, void *ws, int *info, cuda
     u.alpha = -1.0; u.beta = 1.0; u.uplo = UPLO_LOWER;
     TRY(gemm_f64(u, w.scratch, s));
   }
-  return cudaSuccess;
+  // every diagonal-block inverse, for the solves that follow the factorisation
+  return trtri_batched(n, L, ldl, std::min(b, n), b, w.inv, s);
 }
 
 cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, long long lda,
                               void *ws, cudaStream_t s) {
   const int b = tuning().block;
   AdjWs w = carve_adj(ws, n);
-  for (int k = n; k > 0; k -= b) {
+  const int nblk = (int)nblocks(n), first = n - (nblk - 1) * b;
+  double *dinv_all = w.dinv;
+  TRY(trtri_batched(n, L, ldl, first, b, dinv_all, s));  // independent of the sweep: one launch
+  for (int k = n, ib = nblk - 1; k > 0; k -= b, --ib) {
     const int j = std::max(0, k - b), nb = k - j, m = n - k;
     const double *D = L + (long long)j * ldl + j;
     double *Dbar = A + (long long)j * lda + j;
-    TRY(trtri_diag(nb, D, ldl, w.dinv, s));
+    w.dinv = dinv_all + (size_t)ib * b * b;
     if (m > 0) {
       double *Cbar = A + (long long)k * lda + j;
       const double *C = L + (long long)k * ldl + j;
-      TRY(copy_rect(m, nb, Cbar, lda, w.panel, nb, s));
-      Gemm g;  // Cbar <- Cbar D^{-1}
-      g.M = m; g.N = nb; g.K = nb;
-      g.A = w.panel; g.lda = nb;
-      g.B = w.dinv; g.ldb = nb;
-      g.C = Cbar; g.ldc = lda;
-      g.algo_flops = (double)m * nb * (nb + 1);  // triangular B
-      TRY(gemm_f64(g, w.scratch, s));
+      TRY(trsm_rows(m, nb, Cbar, lda, D, ldl, 1, s));  // Cbar <- Cbar D^{-1}
       if (j > 0) {
         Gemm h;  // Bbar -= Cbar R
         h.M = m; h.N = j; h.K = nb;

@@ -15,7 +15,7 @@ namespace gpc {
 struct Tuning {
   int block = 128;        // b: block size of the blocked factorisation / adjoint
   int slices = 5;         // BF16 slices per FP64 operand on the mixed path
-  int splitk_min = 512;   // minimum K per split of a split-K product
+  int splitk_min = 32;    // minimum K per split of a split-K product
 };
 Tuning &tuning();
 
@@ -54,8 +54,19 @@ constexpr int kMaxBlock = 128;
 // pivot p records {pivot_offset + p, status} in info if info[1] is still 0.
 cudaError_t potrf_trtri_diag(int nb, double *A, long long lda, double *Winv, int *info,
                              int pivot_offset, cudaStream_t s);
+// Factor only (no inverse) of the nb x nb block at A, in place.
+cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_offset, cudaStream_t s);
+// In-place panel solve against the lower nb x nb block T: mode 0 X <- X T^{-T},
+// mode 1 X <- X T^{-1}.
+cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode,
+                      cudaStream_t s);
 // Inverse (lower, ld = nb) of the nb x nb lower block D.
 cudaError_t trtri_diag(int nb, const double *D, long long ldd, double *Dinv, cudaStream_t s);
+// Inverses of all diagonal blocks of L in one launch: block 0 = rows [0, first),
+// block ib >= 1 = [first + (ib-1) b, first + ib b); inverse ib at out + ib b^2
+// (leading dimension = block size).  n = total order.
+cudaError_t trtri_batched(int n, const double *L, long long ldl, int first, int b, double *out,
+                          cudaStream_t s);
 
 // ---------------------------------------------------------------- elementwise helpers
 // dst(i,j) = src(i,j) for j <= i; strict upper of dst set to 0 (src may == dst).
@@ -84,9 +95,16 @@ cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, vo
 // r = y - K x, x += L^{-T} L^{-1} r, until |r| <= tol |y|, the residual stops
 // halving, or max_iters corrections; info[1] = GPC_ERR_NO_CONVERGENCE otherwise.
 size_t refine_workspace_bytes(int n);
-cudaError_t refine(int n, const double *K, long long ldk, const double *L, long long ldl, const double *y,
-                   double *x, void *ws, void *trsv_ws, int *info, int max_iters, double tol,
-                   cudaStream_t s);
+cudaError_t refine(int n, const double *K, long long ldk, const double *L, long long ldl, const double *inv,
+                   int b, const double *y, double *x, void *ws, void *trsv_ws, int *info, int max_iters,
+                   double tol, cudaStream_t s);
+// Blocked solve with stored diagonal-block inverses (blocks of b rows from the
+// top, inverse I at inv + I b^2); ws as for trsv.
+cudaError_t trsv_inv(int n, const double *L, long long ldl, const double *inv, int b, double *x, int trans,
+                     void *ws, int *info, cudaStream_t s, const int *skip = nullptr);
+// Block size the factorisation uses at a precision, and where it leaves its
+// diagonal-block inverses (start of the workspace core).
+int chol_block_size(int precision);
 
 // ---------------------------------------------------------------- GP pieces
 constexpr int kMaxDim = 256;
@@ -130,9 +148,11 @@ size_t ozaki_partial_bytes(int M, int N, int splits);
 // C (double-float storage, ld in 8-byte elements) += alpha * A[a_row0 + i, a_k0 + k] B[b_row0 + j, b_k0 + k]
 // over `chunks` K chunks; lower: only col <= row (M == N).  splits > 1 sums
 // K ranges through `partial` (ozaki_partial_bytes) in fixed order.
+// lower with M != N keeps the entries with (local) col <= row.  max_ctas > 0
+// caps the persistent grid (leaves SMs free for work on another stream).
 cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &B, int b_row0, int b_k0,
                        int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
-                       int splits, float2 *partial, int *err, cudaStream_t s);
+                       int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas = 0);
 // Lower triangle of src (FP64) -> dst in double-float storage (upper set to 0); src may == dst.
 cudaError_t to_df_lower(int n, const double *src, long long lds, double *dst, long long ldd, cudaStream_t s);
 // m x c block in double-float storage -> FP64, in place.

@@ -34,9 +34,8 @@ __device__ void invert_lower_smem(double *s, int ld, int nb) {
   }
 }
 
-__global__ void __launch_bounds__(DIAG_THREADS)
-potrf_trtri_kernel(int nb, double *A, long long lda, double *Winv, int *info, int pivot_offset,
-                   int factor) {
+__device__ void potrf_trtri_body(int nb, double *A, long long lda, double *Winv, int *info, int pivot_offset,
+                                 int factor) {
   extern __shared__ double smem[];
   const int ld = nb + 1;
   __shared__ int fail;
@@ -85,6 +84,111 @@ potrf_trtri_kernel(int nb, double *A, long long lda, double *Winv, int *info, in
   for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
     const int i = idx / nb, j = idx - i * nb;
     Winv[idx] = (j <= i) ? S(smem, ld, i, j) : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+potrf_trtri_kernel(int nb, double *A, long long lda, double *Winv, int *info, int pivot_offset,
+                   int factor) {
+  potrf_trtri_body(nb, A, lda, Winv, info, pivot_offset, factor);
+}
+
+// All diagonal-block inverses of L at once, one CTA per block.  Block 0 is
+// rows [0, first), block ib >= 1 is [first + (ib - 1) b, first + ib b); the
+// inverse of block ib goes to out + ib * b * b with leading dimension equal to
+// its size.  (The per-block inverses of Section 3.2, computed as a batch.)
+__global__ void __launch_bounds__(DIAG_THREADS)
+trtri_batched_kernel(int n, const double *L, long long ldl, int first, int b, double *out) {
+  const int ib = blockIdx.x;
+  const int j0 = (ib == 0) ? 0 : first + (ib - 1) * b;
+  const int nb = (ib == 0) ? first : min(b, n - j0);
+  potrf_trtri_body(nb, const_cast<double *>(L) + (long long)j0 * ldl + j0, ldl, out + (size_t)ib * b * b,
+                   nullptr, 0, 0);
+}
+
+// Cholesky factor of one nb x nb diagonal block in shared memory, left-looking
+// by columns (each column j: s_i = A_ij - sum_{k<j} L_ik L_jk for all rows
+// i >= j at once, two threads per row; L_jj = sqrt(s_j); L_ij = s_i / L_jj).
+// Writes L11 in place with the upper part of the block zeroed; a failing
+// pivot is recorded like potrf_trtri_kernel.  No inverse is formed: the
+// panel below is solved by substitution (trsm_rows_kernel).
+__global__ void __launch_bounds__(DIAG_THREADS)
+potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset) {
+  extern __shared__ double smem[];
+  __shared__ double colv[kMaxBlock];
+  __shared__ int fail;
+  const int ld = nb + 1;
+  if (threadIdx.x == 0) fail = 0;
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx - i * nb;
+    S(smem, ld, i, j) = (j <= i) ? A[(long long)i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  const int i = threadIdx.x >> 1, h = threadIdx.x & 1;
+  for (int j = 0; j < nb; ++j) {
+    double sacc = 0.0;
+    if (i >= j && i < nb)
+      for (int k = h; k < j; k += 2) sacc = fma(S(smem, ld, i, k), S(smem, ld, j, k), sacc);
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+    if (h == 0 && i >= j && i < nb) colv[i] = S(smem, ld, i, j) - sacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double pv = colv[j];
+      if (pv > 0.0 && pv <= 1.79769313486231570e308) {
+        S(smem, ld, j, j) = sqrt(pv);
+      } else {
+        fail = 1;
+        if (info && info[1] == 0) {
+          info[0] = pivot_offset + j;
+          info[1] = (pv != pv || pv > 1.79769313486231570e308) ? GPC_ERR_NAN : GPC_ERR_NOT_PD;
+        }
+      }
+    }
+    __syncthreads();
+    if (fail) break;
+    if (h == 0 && i > j && i < nb) S(smem, ld, i, j) = colv[i] / S(smem, ld, j, j);
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx / nb, c = idx - r * nb;
+    A[(long long)r * lda + c] = (c <= r) ? S(smem, ld, r, c) : 0.0;
+  }
+}
+
+// Row-parallel triangular solve of an m x nb panel X (in place) against the
+// nb x nb lower block T (Section 3.3's panel step, by substitution instead of
+// a product with the inverse):
+//   mode 0: X <- X T^{-T}  (forward panel L21 = A21 L11^{-T}; columns ascending)
+//   mode 1: X <- X T^{-1}  (adjoint panel Cbar D^{-1}; columns descending)
+// One CTA per 32 rows, the rows in shared memory; T is read through L1.
+constexpr int TR_ROWS = 32;
+__global__ void __launch_bounds__(256)
+trsm_rows_kernel(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode) {
+  __shared__ double xs[TR_ROWS][kMaxBlock + 1];
+  __shared__ double rdiag[kMaxBlock];
+  const int r0 = blockIdx.x * TR_ROWS, rows = min(TR_ROWS, m - r0);
+  for (int idx = threadIdx.x; idx < TR_ROWS * nb; idx += blockDim.x) {
+    const int r = idx / nb, c = idx - r * nb;
+    xs[r][c] = (r < rows) ? X[(long long)(r0 + r) * ldx + c] : 0.0;
+  }
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) rdiag[j] = 1.0 / __ldg(&T[(long long)j * ldt + j]);
+  __syncthreads();
+  const int r = threadIdx.x & (TR_ROWS - 1), cg = threadIdx.x >> 5;  // 8 column groups
+  for (int step = 0; step < nb; ++step) {
+    const int j = mode == 0 ? step : nb - 1 - step;
+    if (threadIdx.x < TR_ROWS) xs[r][j] *= rdiag[j];
+    __syncthreads();
+    const double xj = xs[r][j];
+    if (mode == 0) {
+      for (int k = j + 1 + cg; k < nb; k += 8) xs[r][k] = fma(-xj, __ldg(&T[(long long)k * ldt + j]), xs[r][k]);
+    } else {
+      for (int k = cg; k < j; k += 8) xs[r][k] = fma(-xj, __ldg(&T[(long long)j * ldt + k]), xs[r][k]);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < TR_ROWS * nb; idx += blockDim.x) {
+    const int rr = idx / nb, c = idx - rr * nb;
+    if (rr < rows) X[(long long)(r0 + rr) * ldx + c] = xs[rr][c];
   }
 }
 
@@ -160,6 +264,53 @@ cudaError_t potrf_trtri_diag(int nb, double *A, long long lda, double *Winv, int
 
 cudaError_t trtri_diag(int nb, const double *D, long long ldd, double *Dinv, cudaStream_t s) {
   return launch_diag(nb, const_cast<double *>(D), ldd, Dinv, nullptr, 0, 0, s);
+}
+
+cudaError_t trtri_batched(int n, const double *L, long long ldl, int first, int b, double *out,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (b > kMaxBlock || first < 1 || first > b) return cudaErrorInvalidValue;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(trtri_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)kMaxBlock * (kMaxBlock + 1) * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const int nblk = 1 + (n - first + b - 1) / b;
+  const size_t smem = (size_t)b * (b + 1) * sizeof(double);
+  GPC_LAUNCH(GPC_TRACE_DIAG, (double)n * b * b / 3.0, 16.0 * (double)n * b, s,
+             trtri_batched_kernel<<<nblk, DIAG_THREADS, smem, s>>>(n, L, ldl, first, b, out));
+  return cudaGetLastError();
+}
+
+cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_offset, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  if (nb > kMaxBlock) return cudaErrorInvalidValue;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(potrf_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)kMaxBlock * (kMaxBlock + 1) * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const size_t smem = (size_t)nb * (nb + 1) * sizeof(double);
+  GPC_LAUNCH(GPC_TRACE_DIAG, (double)nb * nb * nb / 3.0, 16.0 * nb * nb, s,
+             potrf_diag_kernel<<<1, DIAG_THREADS, smem, s>>>(nb, A, lda, info, pivot_offset));
+  return cudaGetLastError();
+}
+
+cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode,
+                      cudaStream_t s) {
+  if (m <= 0 || nb <= 0) return cudaSuccess;
+  if (nb > kMaxBlock) return cudaErrorInvalidValue;
+  GPC_LAUNCH(GPC_TRACE_GEMM_F64, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
+             trsm_rows_kernel<<<(m + TR_ROWS - 1) / TR_ROWS, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
+  return cudaGetLastError();
 }
 
 cudaError_t copy_lower(int n, const double *src, long long lds, double *dst, long long ldd,

@@ -247,7 +247,7 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
 
   // Split K when the output alone cannot fill the machine.
   int splits = 1;
-  const long long target = 2LL * sm_count();
+  const long long target = 3LL * sm_count();  // three CTAs fit per SM
   const int kmin = std::max(tuning().splitk_min, BK);
   if (scratch && tiles < target && p.K >= 2 * kmin) {
     long long want = (target + tiles - 1) / tiles;

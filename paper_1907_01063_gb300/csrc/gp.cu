@@ -137,6 +137,11 @@ constexpr int TB = 64;
 constexpr long long kSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ unsigned long long clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __global__ void __launch_bounds__(256)
 trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sync, int *info,
@@ -256,6 +261,127 @@ trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sy
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicExch(&sync[1 + blk], 1);
+  }
+}
+
+// Blocked solve with the diagonal-block inverses the factorisation kept (the
+// paper's solve through the inverse, Section 3.2, applied block by block):
+//   forward   x_I = Dinv_I (y_I - L[I, <I] x_<I)
+//   transpose x_I = Dinv_I^T (z_I - L[>I, I]^T x_>I)
+// Blocks are b rows from the top (the last may be shorter); Dinv_I is at
+// inv + I b^2 with leading dimension equal to the block size.  Same ticket
+// order, ready flags and bounded waits as trsv_kernel.
+constexpr int TIB = 128;
+__device__ __forceinline__ bool wait_flag(const int *flag, int &value) {
+  const unsigned long long t0 = clock_ns();
+  for (unsigned it = 0;; ++it) {
+    value = ld_volatile(flag);
+    if (value != 0) return true;
+    if ((it & 255) == 255 && clock_ns() - t0 > 2000000000ull) return false;
+    if (it > 1024) __nanosleep(32);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b, double *x, int trans,
+                int *sync, int *info, const int *skip) {
+  if (skip && *skip) return;
+  __shared__ int s_order, s_abort;
+  __shared__ double vbuf[TIB];
+  __shared__ double red[2][TIB];
+  const int nblk = (n + b - 1) / b;
+  if (threadIdx.x == 0) {
+    s_order = atomicAdd(&sync[0], 1);
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int order = s_order;
+  const int blk = trans ? (nblk - 1 - order) : order;
+  const int i0 = blk * b, nb = min(b, n - i0);
+  const double *Dinv = inv + (size_t)blk * b * b;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (!trans) {
+    double acc[TIB / 8];
+#pragma unroll
+    for (int t = 0; t < TIB / 8; ++t) acc[t] = 0.0;
+    for (int c = 0; c < blk; ++c) {
+      if (threadIdx.x == 0) {
+        int f;
+        if (!wait_flag(&sync[1 + c], f) || f != 1) s_abort = 1;
+        __threadfence();
+      }
+      __syncthreads();
+      if (s_abort) break;
+      const int c0 = c * b;  // c < blk: a full block
+      double xq[TIB / 32];
+#pragma unroll
+      for (int u = 0; u < TIB / 32; ++u) xq[u] = (lane + 32 * u < b) ? __ldcg(&x[c0 + lane + 32 * u]) : 0.0;
+#pragma unroll
+      for (int t = 0; t < TIB / 8; ++t) {
+        const int r = warp + 8 * t;
+        if (r < nb) {
+          const double *row = L + (long long)(i0 + r) * ldl + c0;
+#pragma unroll
+          for (int u = 0; u < TIB / 32; ++u)
+            if (lane + 32 * u < b) acc[t] = fma(row[lane + 32 * u], xq[u], acc[t]);
+        }
+      }
+    }
+    if (!s_abort) {
+#pragma unroll
+      for (int t = 0; t < TIB / 8; ++t) {
+        double v = acc[t];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int r = warp + 8 * t;
+        if (lane == 0 && r < nb) vbuf[r] = x[i0 + r] - v;
+      }
+    }
+    __syncthreads();
+    if (!s_abort) {
+      for (int t = 0; t < TIB / 8; ++t) {
+        const int r = warp + 8 * t;
+        if (r >= nb) break;
+        double v = 0.0;
+        for (int k = lane; k <= r; k += 32) v = fma(Dinv[(size_t)r * nb + k], vbuf[k], v);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) x[i0 + r] = v;
+      }
+    }
+  } else {
+    const int i = threadIdx.x & (TIB - 1), rg = threadIdx.x >> 7;
+    double acc = 0.0;
+    for (int step = 0; step < order; ++step) {
+      const int c = nblk - 1 - step;
+      if (threadIdx.x == 0) {
+        int f;
+        if (!wait_flag(&sync[1 + c], f) || f != 1) s_abort = 1;
+        __threadfence();
+      }
+      __syncthreads();
+      if (s_abort) break;
+      const int c0 = c * b, cn = min(b, n - c0);
+      if (i < nb)
+        for (int r = rg; r < cn; r += 2) acc = fma(L[(long long)(c0 + r) * ldl + i0 + i], __ldcg(&x[c0 + r]), acc);
+    }
+    red[rg][i] = acc;
+    __syncthreads();
+    if (!s_abort && threadIdx.x < nb) vbuf[threadIdx.x] = x[i0 + threadIdx.x] - (red[0][threadIdx.x] + red[1][threadIdx.x]);
+    __syncthreads();
+    if (!s_abort) {
+      double v = 0.0;
+      if (i < nb)
+        for (int k = i + rg; k < nb; k += 2) v = fma(Dinv[(size_t)k * nb + i], vbuf[k], v);
+      red[rg][i] = v;
+    }
+    __syncthreads();
+    if (!s_abort && threadIdx.x < nb) x[i0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_abort && info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
+    __threadfence();
+    atomicExch(&sync[1 + blk], s_abort ? 2 : 1);
   }
 }
 
@@ -383,6 +509,19 @@ cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, vo
   return cudaGetLastError();
 }
 
+cudaError_t trsv_inv(int n, const double *L, long long ldl, const double *inv, int b, double *x, int trans,
+                     void *ws, int *info, cudaStream_t s, const int *skip) {
+  if (n <= 0) return cudaSuccess;
+  if (b < 1 || b > TIB) return cudaErrorInvalidValue;
+  const int nblk = (n + b - 1) / b;
+  int *sync = (int *)ws;
+  cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nblk + 1) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n + 2.0 * n * b, 4.0 * (double)n * (n + 1) + 8.0 * n * b, s,
+             trsv_inv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, inv, b, x, trans ? 1 : 0, sync, info, skip));
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- iterative refinement
 namespace {
 
@@ -480,9 +619,9 @@ size_t refine_workspace_bytes(int n) {
   return align_up((size_t)n * sizeof(double), 256) + align_up((size_t)nblk * sizeof(double), 256) + 256;
 }
 
-cudaError_t refine(int n, const double *K, long long ldk, const double *L, long long ldl, const double *y,
-                   double *x, void *ws, void *trsv_ws, int *info, int max_iters, double tol,
-                   cudaStream_t s) {
+cudaError_t refine(int n, const double *K, long long ldk, const double *L, long long ldl, const double *inv,
+                   int b, const double *y, double *x, void *ws, void *trsv_ws, int *info, int max_iters,
+                   double tol, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int nblk = (n + RB - 1) / RB;
   char *p = (char *)ws;
@@ -499,8 +638,8 @@ cudaError_t refine(int n, const double *K, long long ldk, const double *L, long 
     GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * nblk, s,
                refine_check_kernel<<<1, 256, 0, s>>>(nblk, partial, norms, tol * tol, state));
     if (it == max_iters) break;
-    cudaError_t e = trsv(n, L, ldl, r, 0, trsv_ws, info, s, state);
-    if (e == cudaSuccess) e = trsv(n, L, ldl, r, 1, trsv_ws, info, s, state);
+    cudaError_t e = trsv_inv(n, L, ldl, inv, b, r, 0, trsv_ws, info, s, state);
+    if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, r, 1, trsv_ws, info, s, state);
     if (e != cudaSuccess) return e;
     GPC_LAUNCH(GPC_TRACE_ELEM, (double)n, 24.0 * n, s,
                refine_axpy_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, r, state));

@@ -14,6 +14,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace gpc {
 namespace {
@@ -33,18 +34,42 @@ struct MixWs {
 };
 
 size_t b2() { return align_up((size_t)MB * MB * sizeof(double), 256); }
+
+// Per-device auxiliary stream and events for the factorisation's lookahead.
+struct Aux {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_split = nullptr, ev_rest = nullptr;
+};
+std::mutex g_aux_mu;
+Aux g_aux[64];
+
+cudaError_t aux_for_device(Aux **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_aux_mu);
+  Aux &a = g_aux[dev];
+  if (!a.st) {
+    if ((e = cudaStreamCreateWithFlags(&a.st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&a.ev_split, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&a.ev_rest, cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
+  *out = &a;
+  return cudaSuccess;
+}
 size_t scratch_bytes() { return std::max(gemm_f64_scratch_bytes(), kPartialCap); }
 int nchunks(int n) { return std::max(1, (n + MB - 1) / MB); }
 
 MixWs carve(void *ws, int n, bool adjoint) {
   char *p = (char *)ws;
   MixWs w{};
-  w.inv = (double *)p; p += b2();
+  w.inv = (double *)p; p += (size_t)nchunks(n) * b2();  // every diagonal-block inverse
   w.m = (double *)p; p += b2();
   w.t = (double *)p; p += b2();
   w.panel = (double *)p; p += align_up((size_t)n * MB * sizeof(double), 256);
   w.scratch = (double *)p; p += scratch_bytes();
-  w.sc = p; p += slice_bytes(n, 1);
+  w.sc = p; p += 2 * slice_bytes(n, 1);  // two buffers: the next panel's slices while the last are in use
   if (adjoint) {
     w.sdc = p; p += slice_bytes(MB, nchunks(n));
     w.lt = p; p += slice_bytes(n, nchunks(n));
@@ -56,34 +81,53 @@ MixWs carve(void *ws, int n, bool adjoint) {
 
 size_t mixed_workspace_bytes(int n) {
   n = std::max(n, 1);
-  return 3 * b2() + align_up((size_t)n * MB * sizeof(double), 256) + scratch_bytes() + slice_bytes(n, 1) +
-         slice_bytes(MB, nchunks(n)) + slice_bytes(n, nchunks(n)) + 1024;
+  return ((size_t)nchunks(n) + 2) * b2() + align_up((size_t)n * MB * sizeof(double), 256) + scratch_bytes() +
+         2 * slice_bytes(n, 1) + slice_bytes(MB, nchunks(n)) + slice_bytes(n, nchunks(n)) + 1024;
 }
 
+// Lookahead: the trailing update of step k is split into the next block
+// column (on the caller's stream, so step k+1 can start) and the rest (on an
+// auxiliary stream, one SM left free).  Step k+1's conversion and diagonal
+// factorisation then overlap the rest of step k's update; its panel product,
+// which needs the whole GPU, waits for it.  Slices alternate between two
+// buffers so a split never overwrites slices still being read.
 cudaError_t chol_mixed(int n, double *L, long long ldl, void *ws, int *info, cudaStream_t s) {
   MixWs w = carve(ws, n, false);
-  for (int k0 = 0; k0 < n; k0 += MB) {
+  Aux *aux = nullptr;
+  TRY(aux_for_device(&aux));
+  bool rest_pending = false;
+  int step = 0;
+  for (int k0 = 0; k0 < n; k0 += MB, ++step) {
     const int nb = std::min(MB, n - k0), m = n - k0 - nb;
     double *A11 = L + (long long)k0 * ldl + k0;
     TRY(from_df_rect(n - k0, nb, A11, ldl, s));
-    TRY(potrf_trtri_diag(nb, A11, ldl, w.inv, info, k0, s));
+    TRY(potrf_diag(nb, A11, ldl, info, k0, s));
+    if (rest_pending) {
+      TRY(cudaStreamWaitEvent(s, aux->ev_rest, 0));
+      rest_pending = false;
+    }
     if (m <= 0) continue;
     double *A21 = L + (long long)(k0 + nb) * ldl + k0;
-    TRY(copy_rect(m, nb, A21, ldl, w.panel, nb, s));
-    Gemm g;  // L21 = A21 * L11^{-T} (FP64)
-    g.M = m; g.N = nb; g.K = nb;
-    g.A = w.panel; g.lda = nb;
-    g.B = w.inv; g.ldb = nb; g.transB = true;
-    g.C = A21; g.ldc = ldl;
-    g.algo_flops = (double)m * nb * (nb + 1);
-    TRY(gemm_f64(g, w.scratch, s));
-    // A22 -= L21 L21^T on split-BF16 slices, lower tiles, double-float storage
-    SliceBuf S = slice_view(w.sc, m, 1);
+    TRY(trsm_rows(m, nb, A21, ldl, A11, ldl, 0, s));  // L21 = A21 L11^{-T} (FP64)
+    // A22 -= L21 L21^T on split-BF16 slices, lower part, double-float storage
+    SliceBuf S = slice_view((char *)w.sc + (size_t)(step & 1) * slice_bytes(n, 1), m, 1);
     TRY(split_operand(A21, ldl, 1, m, nb, nb, S, s));
-    TRY(ozaki_gemm(S, 0, 0, S, 0, 0, m, m, 1, true, -1.0f, (float2 *)(A21 + nb), ldl, 1, nullptr,
-                   info ? info + 1 : nullptr, s));
+    const int nb2 = std::min(MB, m);
+    float2 *T = (float2 *)(A21 + nb);
+    TRY(ozaki_gemm(S, 0, 0, S, 0, 0, m, nb2, 1, true, -1.0f, T, ldl, 1, nullptr, info ? info + 1 : nullptr, s));
+    if (m > nb2) {
+      TRY(cudaEventRecord(aux->ev_split, s));
+      TRY(cudaStreamWaitEvent(aux->st, aux->ev_split, 0));
+      TRY(ozaki_gemm(S, nb2, 0, S, nb2, 0, m - nb2, m - nb2, 1, true, -1.0f,
+                     (float2 *)(A21 + nb + (long long)nb2 * ldl + nb2), ldl, 1, nullptr,
+                     info ? info + 1 : nullptr, aux->st, sm_count() - 1));
+      TRY(cudaEventRecord(aux->ev_rest, aux->st));
+      rest_pending = true;
+    }
   }
-  return cudaSuccess;
+  if (rest_pending) TRY(cudaStreamWaitEvent(s, aux->ev_rest, 0));
+  // every diagonal-block inverse, for the solves that follow the factorisation
+  return trtri_batched(n, L, ldl, std::min(MB, n), MB, w.inv, s);
 }
 
 cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A, long long lda, void *ws,
@@ -94,25 +138,19 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
   // L^T slices: operand row t = column t of L, K = rows of L, chunked like the sweep's blocks.
   SliceBuf LT = slice_view(w.lt, n, nblk);
   TRY(split_operand(L, 1, ldl, n, n, first, LT, s));
+  TRY(trtri_batched(n, L, ldl, first, MB, w.inv, s));  // independent of the sweep: one launch
   for (int ib = nblk - 1; ib >= 0; --ib) {
     const int j = (ib == 0) ? 0 : first + (ib - 1) * MB;
     const int k = first + ib * MB;
     const int nb = k - j, m = n - k;
     const double *D = L + (long long)j * ldl + j;
     double *Dbar = A + (long long)j * lda + j;
+    const double *dinv = w.inv + (size_t)ib * MB * MB;
     TRY(from_df_rect(n - j, nb, Dbar, lda, s));
-    TRY(trtri_diag(nb, D, ldl, w.inv, s));
     if (m > 0) {
       double *Cbar = A + (long long)k * lda + j;
       const double *C = L + (long long)k * ldl + j;
-      TRY(copy_rect(m, nb, Cbar, lda, w.panel, nb, s));
-      Gemm g;  // Cbar <- Cbar D^{-1} (FP64)
-      g.M = m; g.N = nb; g.K = nb;
-      g.A = w.panel; g.lda = nb;
-      g.B = w.inv; g.ldb = nb;
-      g.C = Cbar; g.ldc = lda;
-      g.algo_flops = (double)m * nb * (nb + 1);
-      TRY(gemm_f64(g, w.scratch, s));
+      TRY(trsm_rows(m, nb, Cbar, lda, D, ldl, 1, s));  // Cbar <- Cbar D^{-1} (FP64)
       if (j > 0) {  // Bbar -= Cbar R on slices (Bbar in double-float storage)
         SliceBuf SC = slice_view(w.sc, m, 1);
         TRY(split_operand(Cbar, lda, 1, m, nb, nb, SC, s));
@@ -139,13 +177,13 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
       Gemm t;  // T = M D^{-1}
       t.M = nb; t.N = nb; t.K = nb;
       t.A = w.m; t.lda = nb;
-      t.B = w.inv; t.ldb = nb;
+      t.B = dinv; t.ldb = nb;
       t.C = w.t; t.ldc = nb;
       t.algo_flops = (double)nb * nb * (nb + 1);
       TRY(gemm_f64(t, w.scratch, s));
       Gemm d;  // Dbar = D^{-T} T, symmetric
       d.M = nb; d.N = nb; d.K = nb;
-      d.A = w.inv; d.lda = nb; d.transA = true;
+      d.A = dinv; d.lda = nb; d.transA = true;
       d.B = w.t; d.ldb = nb;
       d.C = Dbar; d.ldc = lda;
       d.uplo = UPLO_LOWER_MIRROR;

@@ -35,10 +35,12 @@
 // factorisation converts a block column to FP64 only when it becomes the
 // current panel.
 //
-// Kernel structure: persistent CTAs (one per SM), 6 warps: warp 0 issues TMA
+// Kernel structure: persistent CTAs (one per SM), 10 warps: warp 0 issues TMA
 // loads of the slice tiles (64B-swizzled, K-major, 32 wide) into a 3-stage ring,
-// warp 1 owns TMEM and issues the MMAs from one thread, warps 2..5 are the
-// epilogue (one TMEM lane quarter each).  TMEM holds two accumulator sets, so
+// warp 1 owns TMEM and issues the MMAs from one thread, warps 2..9 are the
+// epilogue (two per TMEM lane quarter, 32 columns each); they fetch their C
+// elements before waiting for the accumulators so the read-modify-write of
+// the output overlaps the MMAs.  TMEM holds two accumulator sets, so
 // the epilogue of one chunk overlaps the MMAs of the next (4 x 64 columns per set, 512 in all).  Every mbarrier
 // wait is bounded in time; a timeout sets GPC_ERR_TIMEOUT in the error word,
 // drains the copies and MMAs already issued, frees TMEM and returns.
@@ -56,7 +58,8 @@ namespace {
 
 constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32, OZ_CHUNK = 128, OZ_S = 5, OZ_STAGES = 3;
 constexpr int OZ_QPC = OZ_CHUNK / OZ_BK;                 // stages per chunk
-constexpr int OZ_THREADS = 192;
+constexpr int OZ_EPI_WARPS = 8;                         // two per TMEM lane quarter
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_A_PLANE = OZ_BM * OZ_BK * 2;            // 8 KiB
 constexpr int OZ_B_PLANE = OZ_BN * OZ_BK * 2;            // 4 KiB
 constexpr int OZ_A_STAGE = OZ_S * OZ_A_PLANE;            // 40 KiB
@@ -275,7 +278,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(tfull0 + 8 * i, 1);
-      mbar_init(tempty0 + 8 * i, 4);
+      mbar_init(tempty0 + 8 * i, OZ_EPI_WARPS);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -394,8 +397,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
-    const int q = warp & 3;
+    // ---------------- epilogue: warps 2..9; lane quarter = warp % 4, column half by warp pair
+    const int q = warp & 3, half = (warp - 2) >> 2;
     int buf = 0;
     uint32_t tphase = 0;
     bool ok = true;
@@ -404,35 +407,64 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       work_coords(p, w, tm, tn, c0, c1);
       const int split = w % p.splits;
       const int row = tm * OZ_BM + q * 32 + lane;
+      const bool row_ok = row < p.M;
+      float2 *dst = nullptr;
+      if (row_ok) {
+        if (p.partial) dst = p.partial + ((size_t)split * p.M + row) * (size_t)p.N;
+        else dst = p.C + (long long)row * p.ldc;
+      }
+      const int colh = tn * OZ_BN + half * 32;
+      // vector path: the 32 columns of this thread are in range, 16-byte aligned, and not cut by the diagonal
+      const bool vec = row_ok && colh + 32 <= p.N && (((uintptr_t)(dst + colh)) & 15) == 0 &&
+                       !(p.lower && colh + 31 > row);
       for (int c = c0; c < c1; ++c) {
+        float2 cv[32];
+        if (vec) {
+          const float4 *src = (const float4 *)(dst + colh);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const float4 t = src[u];
+            cv[2 * u] = make_float2(t.x, t.y);
+            cv[2 * u + 1] = make_float2(t.z, t.w);
+          }
+        } else if (row_ok) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int col = colh + i;
+            cv[i] = (col < p.N && !(p.lower && col > row)) ? dst[col] : make_float2(0.f, 0.f);
+          }
+        }
         if (!mbar_wait(tfull0 + 8 * buf, tphase, abort_flag)) { ok = false; break; }
         fence_after();
-        const uint32_t tacc = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * OZ_ACC_COLS);
-        for (int cb = 0; cb < OZ_BN / 16; ++cb) {
+        const uint32_t tacc = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * OZ_ACC_COLS) + half * 32;
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
           float g2[16], g3[16], g4[16], g5[16];
           tmem_ld16(tacc + 0 * OZ_BN + cb * 16, g2);
           tmem_ld16(tacc + 1 * OZ_BN + cb * 16, g3);
           tmem_ld16(tacc + 2 * OZ_BN + cb * 16, g4);
           tmem_ld16(tacc + 3 * OZ_BN + cb * 16, g5);
           tmem_wait_ld();
-          if (row < p.M) {
-            float2 *dst;
-            if (p.partial) dst = p.partial + ((size_t)split * p.M + row) * (size_t)p.N;
-            else dst = p.C + (long long)row * p.ldc;
-            const int col0 = tn * OZ_BN + cb * 16;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int col = col0 + i;
-              if (col >= p.N || (p.lower && col > row)) continue;
-              const float2 cv = dst[col];
-              dst[col] = df_add4(cv, p.alpha * g2[i], p.alpha * g3[i], p.alpha * g4[i], p.alpha * g5[i]);
-            }
-          }
+          for (int i = 0; i < 16; ++i)
+            cv[cb * 16 + i] = df_add4(cv[cb * 16 + i], p.alpha * g2[i], p.alpha * g3[i], p.alpha * g4[i],
+                                      p.alpha * g5[i]);
         }
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
         if (++buf == 2) { buf = 0; tphase ^= 1; }
+        if (vec) {
+          float4 *out = (float4 *)(dst + colh);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) out[u] = make_float4(cv[2 * u].x, cv[2 * u].y, cv[2 * u + 1].x, cv[2 * u + 1].y);
+        } else if (row_ok) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int col = colh + i;
+            if (col < p.N && !(p.lower && col > row)) dst[col] = cv[i];
+          }
+        }
       }
     }
     if (!ok && lane == 0) {
@@ -629,7 +661,7 @@ size_t ozaki_partial_bytes(int M, int N, int splits) {
 
 cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &B, int b_row0, int b_k0,
                        int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
-                       int splits, float2 *partial, int *err, cudaStream_t s) {
+                       int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas) {
   if (M <= 0 || N <= 0 || chunks <= 0) return cudaSuccess;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, OZ_BM) || !make_map(&mb, B, OZ_BN)) return cudaErrorInvalidValue;
@@ -669,7 +701,7 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
     cudaError_t e = cudaMemsetAsync(partial, 0, (size_t)splits * M * N * sizeof(float2), s);
     if (e != cudaSuccess) return e;
   }
-  const int grid = std::min(p.num_work, sm_count());
+  const int grid = std::min(p.num_work, max_ctas > 0 ? std::min(max_ctas, sm_count()) : sm_count());
   const double mn = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
   const double flops = 2.0 * mn * (double)chunks * OZ_CHUNK * 15.0;  // 15 slice products
   GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, 16.0 * mn * chunks + (double)(M + N) * chunks * OZ_CHUNK * 2 * OZ_S, s,

@@ -56,6 +56,12 @@ def test_chol_block_sizes(block):
         Lbar = W.random_lower(333, seed=3)
         G = gp.chol_adjoint(dev(L), dev(Lbar)).cpu().numpy()
         assert rel(G, O.chol_adjoint(L, Lbar)) <= TOL
+        # the likelihood's solves use the factorisation's block inverses at this block size
+        y = W.gp_inputs(333, 1, seed=4)[:, 0]
+        ref = O.gp_lml(K, y)
+        res = gp.gp_lml(dev(K), dev(y))
+        assert rel(res["alpha"].cpu().numpy(), ref["alpha"]) <= TOL
+        assert abs(res["value"].item() - ref["value"]) <= TOL * abs(ref["value"])
     finally:
         gp.set_tuning(gp.GPC_TUNE_BLOCK, old)
 
