@@ -142,8 +142,9 @@ int slice_chunk();
 size_t slice_bytes(int rows, int kchunks);
 SliceBuf slice_view(void *base, int rows, int kchunks);
 // Operand element (r, k) = src[r * rs + k * ks]; chunk 0 is k in [0, first).
+// chunk_offset: operand chunk c is written to slice chunk c + chunk_offset.
 cudaError_t split_operand(const double *src, long long rs, long long ks, int M, int K, int first,
-                          const SliceBuf &out, cudaStream_t s);
+                          const SliceBuf &out, cudaStream_t s, int chunk_offset = 0);
 size_t ozaki_partial_bytes(int M, int N, int splits);
 // C (double-float storage, ld in 8-byte elements) += alpha * A[a_row0 + i, a_k0 + k] B[b_row0 + j, b_k0 + k]
 // over `chunks` K chunks; lower: only col <= row (M == N).  splits > 1 sums

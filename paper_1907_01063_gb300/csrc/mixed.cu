@@ -143,13 +143,14 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
     const int j = (ib == 0) ? 0 : first + (ib - 1) * MB;
     const int k = first + ib * MB;
     const int nb = k - j, m = n - k;
+    const int chunks = nblk - ib;  // K chunks of the block column, rows j..n
     const double *D = L + (long long)j * ldl + j;
     double *Dbar = A + (long long)j * lda + j;
     const double *dinv = w.inv + (size_t)ib * MB * MB;
-    TRY(from_df_rect(n - j, nb, Dbar, lda, s));
+    SliceBuf SDC = slice_view(w.sdc, nb, chunks);
     if (m > 0) {
       double *Cbar = A + (long long)k * lda + j;
-      const double *C = L + (long long)k * ldl + j;
+      TRY(from_df_rect(m, nb, Cbar, lda, s));
       TRY(trsm_rows(m, nb, Cbar, lda, D, ldl, 1, s));  // Cbar <- Cbar D^{-1} (FP64)
       if (j > 0) {  // Bbar -= Cbar R on slices (Bbar in double-float storage)
         SliceBuf SC = slice_view(w.sc, m, 1);
@@ -157,14 +158,17 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
         TRY(ozaki_gemm(SC, 0, 0, LT, 0, ib * MB, m, j, 1, false, -1.0f, (float2 *)(A + (long long)k * lda),
                        lda, 1, nullptr, err, s));
       }
-      Gemm q;  // Dbar -= Cbar^T C (lower, FP64)
-      q.M = nb; q.N = nb; q.K = m;
-      q.A = Cbar; q.lda = lda; q.transA = true;
-      q.B = C; q.ldb = ldl;
-      q.C = Dbar; q.ldc = lda;
-      q.alpha = -1.0; q.beta = 1.0; q.uplo = UPLO_LOWER;
-      TRY(gemm_f64(q, w.scratch, s));
+      // Dbar -= Cbar^T C on slices, Dbar still in double-float storage: the
+      // columns of Cbar (K = rows k..n) fill chunks 1.. of the block column's
+      // slices; C^T is rows j..k of the L^T slices.
+      TRY(split_operand(Cbar, 1, lda, nb, m, MB, SDC, s, 1));
+      const int dch = chunks - 1;
+      int dsplits = std::max(1, std::min(dch, (2 * sm_count() + 1) / 2));
+      while (dsplits > 1 && ozaki_partial_bytes(nb, nb, dsplits) > kPartialCap) --dsplits;
+      TRY(ozaki_gemm(SDC, 0, MB, LT, j, (ib + 1) * MB, nb, nb, dch, true, -1.0f, (float2 *)Dbar, lda, dsplits,
+                     (float2 *)w.scratch, err, s));
     }
+    TRY(from_df_rect(nb, nb, Dbar, lda, s));
     {
       Gemm p;  // M = sym(tril(D^T Dbar))
       p.M = nb; p.N = nb; p.K = nb;
@@ -191,9 +195,7 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
       TRY(gemm_f64(d, w.scratch, s));
     }
     if (j > 0) {  // Rbar -= [Dbar; Cbar]^T [R; B] on slices (Rbar in double-float storage)
-      const int chunks = nblk - ib;
-      SliceBuf SDC = slice_view(w.sdc, nb, chunks);
-      TRY(split_operand(Dbar, 1, lda, nb, n - j, nb, SDC, s));
+      TRY(split_operand(Dbar, 1, lda, nb, nb, nb, SDC, s, 0));  // chunk 0: the finished Dbar
       const int tiles = (j + 63) / 64;
       int splits = std::max(1, std::min(chunks, (2 * sm_count() + tiles - 1) / tiles));
       while (splits > 1 && ozaki_partial_bytes(nb, j, splits) > kPartialCap) --splits;

@@ -644,14 +644,17 @@ SliceBuf slice_view(void *base, int rows, int kchunks) {
 }
 
 cudaError_t split_operand(const double *src, long long rs, long long ks, int M, int K, int first,
-                          const SliceBuf &out, cudaStream_t s) {
-  if (M <= 0) return cudaSuccess;
-  const int chunks = out.kpad / OZ_CHUNK;
+                          const SliceBuf &out, cudaStream_t s, int chunk_offset) {
+  if (M <= 0 || K <= 0) return cudaSuccess;
+  const int op_chunks = (K <= first) ? 1 : 1 + (K - first + OZ_CHUNK - 1) / OZ_CHUNK;
+  const int chunks = std::min(op_chunks, out.kpad / OZ_CHUNK - chunk_offset);
+  if (chunks <= 0) return cudaErrorInvalidValue;
   dim3 grid((unsigned)chunks, (unsigned)(out.rows_pad / 32));
   const long long plane = (long long)out.rows_pad * out.kpad;
-  GPC_LAUNCH(GPC_TRACE_SPLIT, 0.0, 8.0 * M * K + 2.0 * OZ_S * (double)out.rows_pad * out.kpad, s,
-             split_kernel<<<grid, 256, 0, s>>>(src, rs, ks, M, K, first, (__nv_bfloat16 *)out.base, plane,
-                                               out.kpad));
+  GPC_LAUNCH(GPC_TRACE_SPLIT, 0.0, 8.0 * M * K + 2.0 * OZ_S * (double)out.rows_pad * chunks * OZ_CHUNK, s,
+             split_kernel<<<grid, 256, 0, s>>>(src, rs, ks, M, K, first,
+                                               (__nv_bfloat16 *)out.base + (long long)chunk_offset * OZ_CHUNK,
+                                               plane, out.kpad));
   return cudaGetLastError();
 }
 
@@ -702,7 +705,9 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
     if (e != cudaSuccess) return e;
   }
   const int grid = std::min(p.num_work, max_ctas > 0 ? std::min(max_ctas, sm_count()) : sm_count());
-  const double mn = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
+  // output entries: the whole M x N block, or its lower part (col <= row)
+  const double mn = !lower ? (double)M * N
+                           : (M >= N ? 0.5 * (double)N * (N + 1) + (double)(M - N) * N : 0.5 * (double)M * (M + 1));
   const double flops = 2.0 * mn * (double)chunks * OZ_CHUNK * 15.0;  // 15 slice products
   GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, 16.0 * mn * chunks + (double)(M + N) * chunks * OZ_CHUNK * 2 * OZ_S, s,
              ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
