@@ -86,6 +86,7 @@ int gpc_workspace_size(int n, int precision, size_t *bytes);
 #define GPC_TUNE_BLOCK 0
 #define GPC_TUNE_SLICES 1
 #define GPC_TUNE_SPLITK_MIN 2
+#define GPC_TUNE_BATCH_BLOCK 3  /* block size inside gpc_batched_gp_lml_grad: 32 or 64 */
 int gpc_set_tuning(int key, int value);
 int gpc_get_tuning(int key, int *value);
 
@@ -203,6 +204,33 @@ int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, doub
 
 /* Workspace bytes gpc_se_hyper_grad needs at order n (*bytes: host pointer). */
 int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes);
+
+/*
+ * Batched Gaussian-process likelihood and gradient for many independent GPs of
+ * uneven size in one persistent launch.  The paper's batched diagonal
+ * inverses (Section 3.2) give each small problem its own thread block; here
+ * each thread block takes whole GPs from a device queue ordered by size,
+ * largest first, and runs for each: the SE covariance of gpc_se_cov (jitter 0),
+ * the Cholesky factorisation, the two solves, the log marginal likelihood of
+ * gpc_gp_lml, Kbar of gpc_gp_lml_grad and the gradient of gpc_se_hyper_grad.
+ * All arrays are device arrays:
+ *   n[i]       order of GP i (1 <= n[i] <= nmax; larger sizes set info[i] to
+ *              {-1, GPC_ERR_INVALID_ARG} on the device and skip the GP)
+ *   offK[i]    element offset of GP i's n[i] x n[i] matrix in Kws (ld = n[i]);
+ *              Kws receives the Cholesky factor (lower, zero upper)
+ *   rowX[i]    first row of GP i in X (n x d, row-major, ld = d) and in y
+ *   hyp[3i..]  (alpha, rho, sigma) of GP i
+ *   value[i], grad3[3i..3i+2], info[2i..2i+1]  outputs per GP (info as for
+ *              gpc_chol; a GP whose factorisation fails gets NaN outputs)
+ * nmax: host int, at most 4096; workspace from gpc_batched_workspace_size.
+ * Only precision GPC_FP64 is accepted.  Results do not depend on the order in
+ * which thread blocks take GPs.  No counterpart of the API itself is in the paper.
+ */
+int gpc_batched_workspace_size(int batch, int nmax, int precision, size_t *bytes);
+int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *offK, const long long *rowX, int d,
+                            const double *X, const double *y, const double *hyp, int precision, double *Kws,
+                            double *value, double *grad3, int *info, void *ws, size_t ws_bytes,
+                            gpc_stream_t stream);
 
 /*
  * Launch trace (no counterpart in the paper; measurement support).  The

@@ -34,6 +34,7 @@ GPC_MIXED = 1
 GPC_TUNE_BLOCK = 0
 GPC_TUNE_SLICES = 1
 GPC_TUNE_SPLITK_MIN = 2
+GPC_TUNE_BATCH_BLOCK = 3
 
 PRECISIONS = {"fp64": GPC_FP64, "mixed": GPC_MIXED, GPC_FP64: GPC_FP64, GPC_MIXED: GPC_MIXED}
 
@@ -62,6 +63,9 @@ _SIGNATURES = {
     "gpc_se_hyper_grad_workspace_size": ([_c_int, ctypes.POINTER(_c_size)], _c_int),
     "gpc_test_ozaki_workspace_size": ([_c_int, _c_int, _c_int, ctypes.POINTER(_c_size)], _c_int),
     "gpc_test_ozaki_gemm": ([_c_int, _c_int, _c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_size, _c_vp, _c_vp], _c_int),
+    "gpc_batched_workspace_size": ([_c_int, _c_int, _c_int, ctypes.POINTER(_c_size)], _c_int),
+    "gpc_batched_gp_lml_grad": ([_c_int, _c_int, _c_vp, _c_vp, _c_vp, _c_int, _c_vp, _c_vp, _c_vp, _c_int,
+                                 _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
     "gpc_launch_count": ([ctypes.POINTER(ctypes.c_longlong)], _c_int),
     "gpc_fp64_peak": ([_c_vp, _c_size, ctypes.POINTER(_c_double), _c_vp], _c_int),
     "gpc_trace_enable": ([_c_int], _c_int),
@@ -370,6 +374,64 @@ def test_ozaki_gemm(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     if int(err.item()) != 0:
         raise GpcholError(int(err.item()), "gpc_test_ozaki_gemm")
     return C
+
+
+class Batch:
+    """Device layout of a batch of GPs for batched_gp_lml_grad.
+
+    sizes: host sequence of n_i; the covariance/factor of GP i occupies
+    n_i^2 doubles of K at offK[i]; its inputs are rows rowX[i] .. of X and y.
+    """
+
+    def __init__(self, sizes, device=None):
+        device = device if device is not None else "cuda"
+        self.sizes = [int(v) for v in sizes]
+        self.batch = len(self.sizes)
+        self.nmax = max(self.sizes) if self.sizes else 1
+        offk, rowx, ok, rx = [], [], 0, 0
+        for v in self.sizes:
+            offk.append(ok)
+            rowx.append(rx)
+            ok += v * v
+            rx += v
+        self.total_k, self.total_rows = ok, rx
+        self.n = torch.tensor(self.sizes, dtype=torch.int32, device=device)
+        self.offK = torch.tensor(offk, dtype=torch.int64, device=device)
+        self.rowX = torch.tensor(rowx, dtype=torch.int64, device=device)
+        self.K = torch.empty(max(ok, 1), dtype=torch.float64, device=device)
+        self.value = torch.empty(self.batch, dtype=torch.float64, device=device)
+        self.grad3 = torch.empty(self.batch, 3, dtype=torch.float64, device=device)
+        self.info = torch.empty(self.batch, 2, dtype=torch.int32, device=device)
+        nbytes = ctypes.c_size_t()
+        _check(capi.gpc_batched_workspace_size(self.batch, self.nmax, GPC_FP64, ctypes.byref(nbytes)),
+               "gpc_batched_workspace_size")
+        self.ws = torch.empty(nbytes.value, dtype=torch.uint8, device=device)
+
+    def factor(self, i):
+        """Cholesky factor of GP i (a view into K)."""
+        o = int(self.offK[i].item())
+        v = self.sizes[i]
+        return self.K[o:o + v * v].view(v, v)
+
+
+def batched_gp_lml_grad(batch: Batch, X: torch.Tensor, y: torch.Tensor, hyp: torch.Tensor,
+                        precision="fp64"):
+    """Log marginal likelihood and (alpha, rho, sigma) gradient of every GP in
+    the batch in one launch; returns (value [batch], grad3 [batch, 3], info [batch, 2])."""
+    if not (X.is_cuda and X.dtype == torch.float64 and X.dim() == 2 and X.is_contiguous()):
+        raise ValueError("X must be a contiguous float64 CUDA matrix")
+    if X.shape[0] != batch.total_rows or y.numel() != batch.total_rows:
+        raise ValueError("X and y must hold sum(n_i) rows")
+    hyp = hyp.to(device=X.device, dtype=torch.float64).contiguous()
+    if hyp.numel() != 3 * batch.batch:
+        raise ValueError("hyp must have shape (batch, 3)")
+    _check(capi.gpc_batched_gp_lml_grad(batch.batch, batch.nmax, batch.n.data_ptr(), batch.offK.data_ptr(),
+                                        batch.rowX.data_ptr(), X.shape[1], X.data_ptr(), y.data_ptr(),
+                                        hyp.data_ptr(), precision_code(precision), batch.K.data_ptr(),
+                                        batch.value.data_ptr(), batch.grad3.data_ptr(), batch.info.data_ptr(),
+                                        batch.ws.data_ptr(), batch.ws.numel(), _stream()),
+           "gpc_batched_gp_lml_grad")
+    return batch.value, batch.grad3, batch.info
 
 
 # ---------------------------------------------------------------- autograd

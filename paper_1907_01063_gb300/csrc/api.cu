@@ -117,6 +117,10 @@ int gpc_set_tuning(int key, int value) {
       if (value < 16 || value > (1 << 20)) return GPC_ERR_INVALID_ARG;
       tuning().splitk_min = value;
       return GPC_OK;
+    case GPC_TUNE_BATCH_BLOCK:
+      if (value != 32 && value != 64) return GPC_ERR_INVALID_ARG;
+      tuning().batch_block = value;
+      return GPC_OK;
     default:
       return GPC_ERR_INVALID_ARG;
   }
@@ -128,6 +132,7 @@ int gpc_get_tuning(int key, int *value) {
     case GPC_TUNE_BLOCK: *value = tuning().block; return GPC_OK;
     case GPC_TUNE_SLICES: *value = tuning().slices; return GPC_OK;
     case GPC_TUNE_SPLITK_MIN: *value = tuning().splitk_min; return GPC_OK;
+    case GPC_TUNE_BATCH_BLOCK: *value = tuning().batch_block; return GPC_OK;
     default: return GPC_ERR_INVALID_ARG;
   }
 }
@@ -277,6 +282,28 @@ int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, doub
                 !ws || ws_bytes < se_hyper_grad_workspace_bytes(n)))
     return GPC_ERR_INVALID_ARG;
   return status_of(se_hyper_grad(n, d, X, ldx, alpha, rho, sigma, Kbar, ldkb, grad3, ws, stream));
+}
+
+constexpr int kBatchMaxN = 4096;
+
+int gpc_batched_workspace_size(int batch, int nmax, int precision, size_t *bytes) {
+  if (!bytes || batch < 0 || nmax < 1 || nmax > kBatchMaxN || precision != GPC_FP64) return GPC_ERR_INVALID_ARG;
+  *bytes = batched_workspace_bytes(std::max(batch, 1), nmax);
+  return GPC_OK;
+}
+
+int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *offK, const long long *rowX, int d,
+                            const double *X, const double *y, const double *hyp, int precision, double *Kws,
+                            double *value, double *grad3, int *info, void *ws, size_t ws_bytes,
+                            gpc_stream_t stream) {
+  if (batch < 0 || nmax < 1 || nmax > kBatchMaxN || d < 1 || d > kMaxDim || precision != GPC_FP64)
+    return GPC_ERR_INVALID_ARG;
+  if (batch == 0) return GPC_OK;
+  if (!n || !offK || !rowX || !X || !y || !hyp || !Kws || !value || !grad3 || !info || !ws ||
+      ws_bytes < batched_workspace_bytes(batch, nmax))
+    return GPC_ERR_INVALID_ARG;
+  return status_of(batched_gp_lml_grad(batch, n, offK, rowX, d, X, y, hyp, Kws, value, grad3, info, nmax, ws,
+                                       stream));
 }
 
 int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes) {

@@ -16,6 +16,8 @@ struct Tuning {
   int block = 128;        // b: block size of the blocked factorisation / adjoint
   int slices = 5;         // BF16 slices per FP64 operand on the mixed path
   int splitk_min = 32;    // minimum K per split of a split-K product
+  int batch_block = 64;   // block size inside the batched per-GP pass (32 or 64)
+  int batch_ctas_per_sm = 1;
 };
 Tuning &tuning();
 
@@ -160,6 +162,11 @@ cudaError_t to_df_lower(int n, const double *src, long long lds, double *dst, lo
 cudaError_t from_df_rect(int m, int c, double *p, long long ld, cudaStream_t s);
 size_t mixed_workspace_bytes(int n);
 cudaError_t chol_mixed(int n, double *L, long long ldl, void *ws, int *info, cudaStream_t s);
+// Batched per-GP pass (batched.cu); rowX[i] = first row of GP i in X (d per row) and y.
+size_t batched_workspace_bytes(int batch, int nmax);
+cudaError_t batched_gp_lml_grad(int batch, const int *n, const long long *offK, const long long *rowX, int d,
+                                const double *X, const double *y, const double *hyp, double *K, double *value,
+                                double *grad3, int *info, int nmax, void *ws, cudaStream_t s);
 cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A, long long lda, void *ws,
                                int *err, cudaStream_t s);
 

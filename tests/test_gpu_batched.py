@@ -1,0 +1,130 @@
+"""Batched GPs in one persistent launch, against the CPU oracle per GP."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1907_01063_gb300 as gp
+from oracle import oracle as O
+from paper_1907_01063_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(sizes, d=4, seed=0, sigma=0.1):
+    rho = W.batch_lengthscales(len(sizes), 0.2, 2.0, seed=seed + 1)
+    Xs, ys, hyps = [], [], []
+    for i, n in enumerate(sizes):
+        X = W.gp_inputs(n, d, seed=1000 + i)
+        y = W.gp_targets(X, 1.0, float(rho[i]), sigma, seed=2000 + i)
+        Xs.append(X)
+        ys.append(y)
+        hyps.append((1.0, float(rho[i]), sigma))
+    return Xs, ys, np.array(hyps)
+
+
+def run_batch(sizes, Xs, ys, hyps, block=None):
+    b = gp.Batch(sizes)
+    X = torch.as_tensor(np.concatenate(Xs), device="cuda").contiguous()
+    y = torch.as_tensor(np.concatenate(ys), device="cuda").contiguous()
+    old = gp.get_tuning(gp.GPC_TUNE_BATCH_BLOCK)
+    try:
+        if block:
+            gp.set_tuning(gp.GPC_TUNE_BATCH_BLOCK, block)
+        v, g, info = gp.batched_gp_lml_grad(b, X, y, torch.as_tensor(hyps))
+        torch.cuda.synchronize()
+    finally:
+        gp.set_tuning(gp.GPC_TUNE_BATCH_BLOCK, old)
+    return b, v.cpu().numpy(), g.cpu().numpy(), info.cpu().numpy()
+
+
+SIZES = [1, 5, 33, 64, 65, 100, 128, 129, 200, 257, 63, 3]
+
+
+@pytest.mark.parametrize("block", [32, 64])
+def test_batched_matches_oracle(block):
+    Xs, ys, hyps = make_batch(SIZES, seed=block)
+    b, v, g, info = run_batch(SIZES, Xs, ys, hyps, block)
+    assert np.all(info[:, 1] == gp.GPC_OK)
+    for i, n in enumerate(SIZES):
+        ref = O.gp_lml_and_grad(Xs[i], ys[i], *hyps[i], 0.0)
+        assert abs(v[i] - ref["value"]) <= 1e-10 * max(1.0, abs(ref["value"])), (i, n)
+        assert np.linalg.norm(g[i] - ref["grad"]) <= 1e-8 * np.linalg.norm(ref["grad"]), (i, n)
+        if n in (65, 257):
+            L = b.factor(i).cpu().numpy()
+            assert np.linalg.norm(L - ref["L"]) <= 1e-10 * np.linalg.norm(ref["L"])
+
+
+def test_batched_equals_single_gp_path():
+    sizes = [300, 77, 513]
+    Xs, ys, hyps = make_batch(sizes, seed=5)
+    _, v, g, info = run_batch(sizes, Xs, ys, hyps)
+    for i, n in enumerate(sizes):
+        X = torch.as_tensor(Xs[i], device="cuda")
+        h = torch.tensor(hyps[i], dtype=torch.float64, requires_grad=True)
+        val = gp.gp_lml_value(X, torch.as_tensor(ys[i], device="cuda"), h, 0.0)
+        val.backward()
+        assert abs(v[i] - val.item()) <= 1e-11 * abs(val.item())
+        assert np.linalg.norm(g[i] - h.grad.numpy()) <= 1e-9 * np.linalg.norm(h.grad.numpy())
+
+
+def test_batched_failure_is_isolated():
+    # one GP with a NaN noise level has a NaN diagonal: only it fails
+    sizes = [40, 50, 60]
+    Xs, ys, hyps = make_batch(sizes, seed=9)
+    hyps[1, 2] = np.nan
+    _, v, g, info = run_batch(sizes, Xs, ys, hyps)
+    assert info[1, 1] in (gp.GPC_ERR_NOT_PD, gp.GPC_ERR_NAN)
+    assert np.isnan(v[1])
+    for i in (0, 2):
+        ref = O.gp_lml_and_grad(Xs[i], ys[i], *hyps[i], 0.0)
+        assert info[i, 1] == gp.GPC_OK
+        assert abs(v[i] - ref["value"]) <= 1e-10 * abs(ref["value"])
+
+
+def test_batched_rejects_sizes_above_nmax_on_device():
+    sizes = [10, 20]
+    Xs, ys, hyps = make_batch(sizes, seed=3)
+    b = gp.Batch(sizes)
+    X = torch.as_tensor(np.concatenate(Xs), device="cuda").contiguous()
+    y = torch.as_tensor(np.concatenate(ys), device="cuda").contiguous()
+    hyp = torch.as_tensor(hyps, device="cuda").contiguous()
+    st = gp.capi.gpc_batched_gp_lml_grad(2, 10, b.n.data_ptr(), b.offK.data_ptr(), b.rowX.data_ptr(), 4,
+                                         X.data_ptr(), y.data_ptr(), hyp.data_ptr(), 0, b.K.data_ptr(),
+                                         b.value.data_ptr(), b.grad3.data_ptr(), b.info.data_ptr(),
+                                         b.ws.data_ptr(), b.ws.numel(), torch.cuda.current_stream().cuda_stream)
+    assert st == gp.GPC_OK
+    info = b.info.cpu().numpy()
+    assert info[0, 1] == gp.GPC_OK and info[1, 1] == gp.GPC_ERR_INVALID_ARG
+
+
+def test_batched_config5_sample():
+    # the batch workload's size mix (n ~ U{64..1024}, d = 4, rho ~ U(0.2, 2)),
+    # checked on a few members against the oracle
+    sizes = list(W.batch_sizes(64, 64, 1024, seed=0))
+    Xs, ys, hyps = make_batch(sizes, seed=0)
+    _, v, g, info = run_batch(sizes, Xs, ys, hyps)
+    assert np.all(info[:, 1] == gp.GPC_OK)
+    for i in np.argsort(sizes)[:3]:
+        ref = O.gp_lml_and_grad(Xs[i], ys[i], *hyps[i], 0.0)
+        assert abs(v[i] - ref["value"]) <= 1e-10 * max(1.0, abs(ref["value"]))
+        assert np.linalg.norm(g[i] - ref["grad"]) <= 1e-8 * np.linalg.norm(ref["grad"])
+
+
+def test_batched_graph_replay_matches_direct_call():
+    sizes = [90, 17, 150, 64]
+    Xs, ys, hyps = make_batch(sizes, seed=11)
+    b = gp.Batch(sizes)
+    X = torch.as_tensor(np.concatenate(Xs), device="cuda").contiguous()
+    y = torch.as_tensor(np.concatenate(ys), device="cuda").contiguous()
+    hyp = torch.as_tensor(hyps, device="cuda").contiguous()
+    gp.batched_gp_lml_grad(b, X, y, hyp)
+    torch.cuda.synchronize()
+    v0, g0 = b.value.clone(), b.grad3.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gp.batched_gp_lml_grad(b, X, y, hyp)
+    b.value.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(b.value, v0) and torch.equal(b.grad3, g0)
