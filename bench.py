@@ -50,6 +50,8 @@ def parse_args():
                    help="both: time the FP64 and the mixed path; the headline is the mixed path")
     p.add_argument("--block", type=int, default=0, help="block size b (0: library default)")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--trace-steps", type=int, default=2,
+                   help="steps repeated with per-launch events for the roofline")
     p.add_argument("--cpu-sample", type=int, default=3072,
                    help="order of the leading block the oracle factors for cpu_baseline")
     p.add_argument("--ref-sample", type=int, default=2048,
@@ -342,7 +344,6 @@ def main():
         clocks = ClockSampler(local)
         clocks.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        gp.trace_enable(True)
         launches0 = gp.launch_count()
         barrier()
         ev0.record(stream)
@@ -352,6 +353,18 @@ def main():
         barrier()
         launches = gp.launch_count() - launches0
         t_ms = max_over_ranks(ev0.elapsed_time(ev1))
+        # per-launch device times for the roofline: the same steps again with an
+        # event pair around every launch (kept out of the region above because
+        # ~3000 event pairs per mixed step add a few percent to its time)
+        trace_steps = max(1, min(args.trace_steps, args.steps))
+        gp.trace_enable(True)
+        barrier()
+        ev0.record(stream)
+        for _ in range(trace_steps):
+            step(Xd, yd)
+        ev1.record(stream)
+        barrier()
+        traced_ms = ev0.elapsed_time(ev1) / trace_steps
         trace = gp.trace_summary()
         gp.trace_enable(False)
         clk = clocks.stop()
@@ -359,7 +372,7 @@ def main():
         if st[1] not in (gp.GPC_OK, gp.GPC_ERR_NO_CONVERGENCE):
             gp.check_info(info, f"timed step ({prec})")
         out = {"prec": prec, "block": b, "step_flops": step_flops, "t_ms": t_ms, "launches": launches,
-               "trace": trace, "clocks": clk, "value": world * args.steps * step_flops / (t_ms / 1e3) / 1e9,
+               "trace": trace, "trace_steps": trace_steps, "traced_ms_per_step": traced_ms, "clocks": clk, "value": world * args.steps * step_flops / (t_ms / 1e3) / 1e9,
                "lml": res["value"].item(), "logdet": res["logdet"].item(), "grad": g3.tolist(),
                "refine_status": st[1]}
         # end to end: pinned host inputs in, scalars out, every step
@@ -402,7 +415,9 @@ def main():
     nominal_fp64 = peaks.get("bf16_tflops", 1900.0) * 1e3 * 1.25 / 2250.0
 
     def roofline(res):
-        trace = res["trace"]
+        trace = {k: dict(v, ms=v["ms"] / res["trace_steps"], flops=v["flops"] / res["trace_steps"],
+                         bytes=v["bytes"] / res["trace_steps"], launches=v["launches"] / res["trace_steps"])
+                 for k, v in res["trace"].items()}
         dom_name, dom = max(((k, v) for k, v in trace.items() if v["launches"]), key=lambda kv: kv[1]["ms"])
         avg = dom["ms"] / max(dom["launches"], 1)
         if dom_name == "gemm_mixed":
@@ -410,22 +425,24 @@ def main():
             achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12 if dom["ms"] else 0.0
             return {"kernel": "ozaki_gemm_kernel (tcgen05 BF16 slice products, 15 per FP64 product)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "launches": dom["launches"],
+                    "frac": achieved / peak, "traffic": None, "launches_per_step": dom["launches"],
                     "avg_launch_ms": avg, "peak_source": "of measured: MEASURED_PEAKS bf16_tflops_sustained",
                     "fp64_equivalent_gflops": dom["flops"] / 15.0 / (dom["ms"] / 1e3) / 1e9}
-        if dom_name in ("gemm_f64", "diag"):
+        if dom_name in ("gemm_f64", "diag", "trsm"):
             achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0
-            return {"kernel": ("gemm_f64_kernel (FP64 mma.sync m16n8k16)" if dom_name == "gemm_f64"
-                               else "potrf_trtri_kernel"),
-                    "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": None, "launches": dom["launches"],
+            names = {"gemm_f64": "gemm_f64_kernel (FP64 mma.sync m16n8k16)",
+                     "diag": "diagonal-block kernels (potrf_diag, trtri_batched)",
+                     "trsm": "trsm_rows_kernel (FP64 panel solves)"}
+            return {"kernel": names[dom_name],
+                    "bound": "tensor" if dom_name == "gemm_f64" else "alu", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None, "launches_per_step": dom["launches"],
                     "avg_launch_ms": avg,
                     "peak_source": "of measured: FP64 DMMA m16n8k16 issue rate measured in this run (gpc_fp64_peak)",
                     "peak_nominal_ratio": nominal_fp64}
         achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0
         peak = peaks.get("hbm_gbs", 6800.0)
         return {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "launches": dom["launches"], "avg_launch_ms": avg,
+                "frac": achieved / peak, "traffic": None, "launches_per_step": dom["launches"], "avg_launch_ms": avg,
                 "peak_source": "of measured: MEASURED_PEAKS hbm_gbs"}
 
     if rank != 0:
@@ -438,11 +455,14 @@ def main():
     head = results["mixed"] if "mixed" in results else results["fp64"]
     prec = head["prec"]
 
+    def kernel_ms(res):
+        return {k: round(v["ms"] / res["trace_steps"], 3) for k, v in res["trace"].items() if v["launches"]}
+
     def summary(res):
         return {"value": res["value"], "unit": "GFLOP/s", "ms_per_step": res["t_ms"] / args.steps,
                 "gpu_launches": res["launches"], "roofline": roofline(res), "e2e": res["e2e"],
                 "lml": res["lml"], "logdet": res["logdet"], "grad": res["grad"], "clocks": res["clocks"],
-                "kernel_time_ms": {k: round(v["ms"], 3) for k, v in res["trace"].items() if v["launches"]}}
+                "kernel_ms_per_step": kernel_ms(res), "traced_ms_per_step": res["traced_ms_per_step"]}
 
     line = {
         "metric": METRIC, "value": head["value"], "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -456,7 +476,8 @@ def main():
         "cpu_baseline": cpu,
         "clocks": head["clocks"],
         "flops_per_step": head["step_flops"],
-        "kernel_time_ms": {k: round(v["ms"], 3) for k, v in head["trace"].items() if v["launches"]},
+        "kernel_ms_per_step": kernel_ms(head),
+        "traced_ms_per_step": head["traced_ms_per_step"],
     }
     if batched is not None:
         line["batched"] = batched

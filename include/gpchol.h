@@ -242,7 +242,7 @@ int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *
  * launches, their summed device time in ms and their summed algorithmic
  * flops and bytes (host pointers).  Not thread-safe; meant for benchmarks.
  */
-#define GPC_TRACE_GEMM_F64 0   /* FP64 DMMA products (panel, trailing update, adjoint) */
+#define GPC_TRACE_GEMM_F64 0   /* FP64 DMMA products (trailing update, adjoint) */
 #define GPC_TRACE_DIAG 1       /* diagonal-block factor / inverse */
 #define GPC_TRACE_TRSV 2       /* triangular solves */
 #define GPC_TRACE_SECOV 3      /* covariance build */
@@ -250,7 +250,8 @@ int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *
 #define GPC_TRACE_ELEM 5       /* copies, reductions and other small kernels */
 #define GPC_TRACE_GEMM_MIXED 6 /* split-BF16 tensor-core products */
 #define GPC_TRACE_SPLIT 7      /* FP64 -> BF16 slice splitting */
-#define GPC_TRACE_CLASSES 8
+#define GPC_TRACE_TRSM 8       /* FP64 panel solves against a diagonal block */
+#define GPC_TRACE_CLASSES 9
 int gpc_launch_count(long long *count);
 
 /*

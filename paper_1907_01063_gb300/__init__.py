@@ -74,7 +74,7 @@ _SIGNATURES = {
 }
 
 TRACE_CLASSES = {"gemm_f64": 0, "diag": 1, "trsv": 2, "se_cov": 3, "hyper_grad": 4, "elementwise": 5,
-                 "gemm_mixed": 6, "split": 7}
+                 "gemm_mixed": 6, "split": 7, "trsm": 8}
 
 
 class GpcholError(RuntimeError):

@@ -308,7 +308,7 @@ cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, 
                       cudaStream_t s) {
   if (m <= 0 || nb <= 0) return cudaSuccess;
   if (nb > kMaxBlock) return cudaErrorInvalidValue;
-  GPC_LAUNCH(GPC_TRACE_GEMM_F64, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
+  GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
              trsm_rows_kernel<<<(m + TR_ROWS - 1) / TR_ROWS, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
   return cudaGetLastError();
 }
