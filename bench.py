@@ -331,10 +331,10 @@ def main():
         step_flops = chol_flops(n) + adjoint_flops(n, b)
 
         def step(Xs, ys):
-            gp.se_cov(Xs, a, r, s, jitter, out=K)
+            gp.se_cov(Xs, a, r, s, jitter, out=K, precision=prec)
             res = gp.gp_lml(K, ys, prec, L=L, ws=ws, info=info, check=False)
             gp.gp_lml_grad(L, res["alpha"], 1.0, prec, out=Kbar, ws=ws)
-            gp.se_hyper_grad(Xs, a, r, s, Kbar, ws=hws, out=g3)
+            gp.se_hyper_grad(Xs, a, r, s, Kbar, ws=hws, out=g3, precision=prec)
             return res
 
         for _ in range(args.warmup):

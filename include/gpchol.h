@@ -97,10 +97,14 @@ int gpc_get_tuning(int key, int *value);
  * discussion lists covariance functions as GPU work to add (Section 5).
  * Writes the lower triangle of K (ldk >= n); full != 0 mirrors it into the
  * upper triangle, full == 0 leaves the upper triangle untouched.
- * Requires rho > 0; d >= 1.
+ * precision GPC_FP64: FP64 arithmetic throughout.  GPC_MIXED: r^2 and the
+ * exponential in double-float arithmetic (pairs of FP32 numbers, about 2^-46
+ * relative error per entry, far below the mixed factorisation's own error),
+ * one conversion to FP64 per entry; the diagonal is exact.
+ * Requires rho > 0; 1 <= d <= 256.
  */
 int gpc_se_cov(int n, int d, const double *X, int ldx, double alpha, double rho, double sigma,
-               double jitter, double *K, int ldk, int full, gpc_stream_t stream);
+               double jitter, double *K, int ldk, int full, int precision, gpc_stream_t stream);
 
 /*
  * Cholesky factor L (lower, K = L L^T) of the SPD matrix whose lower triangle
@@ -194,13 +198,15 @@ int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double
  *   d K_ij/d alpha = 2 K^f_ij / alpha, d K_ij/d rho = K^f_ij r2_ij / rho^3,
  *   d K_ii/d sigma = 2 sigma   (K^f: the noise-free part; jitter is constant),
  * summed over i >= j.  K^f is recomputed from X; grad3: 3 device doubles.
+ * precision as for gpc_se_cov (GPC_MIXED: K^f and the per-thread sums in
+ * double-float arithmetic, the per-tile sums in FP64).
  * The sums are formed per tile and then added in a fixed order, so repeated
  * calls give bitwise-identical results.  ws/ws_bytes: at least
  * gpc_se_hyper_grad_workspace_size(n) bytes.  Requires alpha != 0, rho > 0.
  */
 int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, double rho,
-                      double sigma, const double *Kbar, int ldkb, double *grad3, void *ws,
-                      size_t ws_bytes, gpc_stream_t stream);
+                      double sigma, const double *Kbar, int ldkb, double *grad3, int precision,
+                      void *ws, size_t ws_bytes, gpc_stream_t stream);
 
 /* Workspace bytes gpc_se_hyper_grad needs at order n (*bytes: host pointer). */
 int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes);
@@ -237,10 +243,18 @@ int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *
  * library counts every kernel it launches; gpc_launch_count returns the
  * running total (host pointer *count).  gpc_trace_enable(1) clears the
  * per-class totals and starts recording a CUDA event pair around each launch
- * on the launching stream; gpc_trace_enable(0) stops.  gpc_trace_summary
- * synchronises the recorded events and returns, for one class, the number of
- * launches, their summed device time in ms and their summed algorithmic
- * flops and bytes (host pointers).  Not thread-safe; meant for benchmarks.
+ * on the launching stream; gpc_trace_enable(2) does the same and also keeps a
+ * timeline (one span per launch, cleared by this call); gpc_trace_enable(0)
+ * stops and keeps what was recorded; other values return GPC_ERR_INVALID_ARG.
+ * gpc_trace_summary synchronises the recorded events and returns, for one
+ * class, the number of launches, their summed device time in ms and their
+ * summed algorithmic flops and bytes (host pointers).
+ * gpc_trace_timeline synchronises and copies up to max spans, in launch
+ * order, into caller host arrays: class, kernel-name id, stream handle,
+ * start (ms after the first traced launch began) and device duration (ms);
+ * *count receives the number of spans held (at most 2^21).  gpc_trace_name
+ * writes the NUL-terminated kernel name of a name id into buf (truncated to
+ * buf_bytes - 1 characters).  Not thread-safe; meant for benchmarks.
  */
 #define GPC_TRACE_GEMM_F64 0   /* FP64 DMMA products (trailing update, adjoint) */
 #define GPC_TRACE_DIAG 1       /* diagonal-block factor / inverse */
@@ -266,6 +280,9 @@ int gpc_launch_count(long long *count);
 int gpc_fp64_peak(void *ws, size_t ws_bytes, double *gflops, gpc_stream_t stream);
 int gpc_trace_enable(int on);
 int gpc_trace_summary(int cls, long long *launches, double *ms, double *flops, double *bytes);
+int gpc_trace_timeline(long long max, int *cls, int *name, unsigned long long *stream, float *start_ms,
+                       float *dur_ms, long long *count);
+int gpc_trace_name(int name, char *buf, size_t buf_bytes);
 
 #ifdef __cplusplus
 }

@@ -48,7 +48,7 @@ _SIGNATURES = {
     "gpc_set_tuning": ([_c_int, _c_int], _c_int),
     "gpc_get_tuning": ([_c_int, ctypes.POINTER(_c_int)], _c_int),
     "gpc_se_cov": ([_c_int, _c_int, _c_vp, _c_int, _c_double, _c_double, _c_double, _c_double,
-                    _c_vp, _c_int, _c_int, _c_vp], _c_int),
+                    _c_vp, _c_int, _c_int, _c_int, _c_vp], _c_int),
     "gpc_chol": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_int, _c_vp, _c_size, _c_vp, _c_vp], _c_int),
     "gpc_chol_adjoint": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_int, _c_int,
                           _c_vp, _c_size, _c_vp], _c_int),
@@ -59,7 +59,7 @@ _SIGNATURES = {
     "gpc_gp_lml_grad": ([_c_int, _c_vp, _c_int, _c_vp, _c_double, _c_vp, _c_int, _c_int, _c_vp,
                          _c_size, _c_vp], _c_int),
     "gpc_se_hyper_grad": ([_c_int, _c_int, _c_vp, _c_int, _c_double, _c_double, _c_double, _c_vp,
-                           _c_int, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
+                           _c_int, _c_vp, _c_int, _c_vp, _c_size, _c_vp], _c_int),
     "gpc_se_hyper_grad_workspace_size": ([_c_int, ctypes.POINTER(_c_size)], _c_int),
     "gpc_test_ozaki_workspace_size": ([_c_int, _c_int, _c_int, ctypes.POINTER(_c_size)], _c_int),
     "gpc_test_ozaki_gemm": ([_c_int, _c_int, _c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_size, _c_vp, _c_vp], _c_int),
@@ -71,6 +71,10 @@ _SIGNATURES = {
     "gpc_trace_enable": ([_c_int], _c_int),
     "gpc_trace_summary": ([_c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_c_double),
                            ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)], _c_int),
+    "gpc_trace_timeline": ([ctypes.c_longlong, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                            ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_float),
+                            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_longlong)], _c_int),
+    "gpc_trace_name": ([_c_int, ctypes.c_char_p, _c_size], _c_int),
 }
 
 TRACE_CLASSES = {"gemm_f64": 0, "diag": 1, "trsv": 2, "se_cov": 3, "hyper_grad": 4, "elementwise": 5,
@@ -222,9 +226,34 @@ def fp64_peak_gflops(device=None) -> float:
     return v.value
 
 
-def trace_enable(on: bool = True):
-    """Start (clearing totals) or stop per-launch CUDA-event timing."""
-    _check(capi.gpc_trace_enable(1 if on else 0), "gpc_trace_enable")
+def trace_enable(on: bool = True, timeline: bool = False):
+    """Start (clearing totals) or stop per-launch CUDA-event timing; with
+    timeline=True every launch's start and duration is kept as well."""
+    _check(capi.gpc_trace_enable((2 if timeline else 1) if on else 0), "gpc_trace_enable")
+
+
+def trace_timeline() -> list:
+    """Recorded launches in order: class, kernel, stream, start and duration (ms)."""
+    count = ctypes.c_longlong()
+    _check(capi.gpc_trace_timeline(0, None, None, None, None, None, ctypes.byref(count)), "gpc_trace_timeline")
+    n = count.value
+    cls = (ctypes.c_int * max(n, 1))()
+    name = (ctypes.c_int * max(n, 1))()
+    stream = (ctypes.c_ulonglong * max(n, 1))()
+    start = (ctypes.c_float * max(n, 1))()
+    dur = (ctypes.c_float * max(n, 1))()
+    _check(capi.gpc_trace_timeline(n, cls, name, stream, start, dur, ctypes.byref(count)), "gpc_trace_timeline")
+    classes = {v: k for k, v in TRACE_CLASSES.items()}
+    names = {}
+    buf = ctypes.create_string_buffer(256)
+    out = []
+    for i in range(min(n, count.value)):
+        if name[i] not in names:
+            _check(capi.gpc_trace_name(name[i], buf, 256), "gpc_trace_name")
+            names[name[i]] = buf.value.decode()
+        out.append({"class": classes.get(cls[i], str(cls[i])), "kernel": names[name[i]], "stream": stream[i],
+                    "start_ms": start[i], "dur_ms": dur[i]})
+    return out
 
 
 def trace_summary() -> dict:
@@ -240,15 +269,17 @@ def trace_summary() -> dict:
 
 # ---------------------------------------------------------------- tensor API
 def se_cov(X: torch.Tensor, alpha: float, rho: float, sigma: float, jitter: float = 0.0,
-           full: bool = False, out: torch.Tensor | None = None) -> torch.Tensor:
-    """Squared-exponential covariance of the rows of X (lower triangle, or full)."""
+           full: bool = False, out: torch.Tensor | None = None, precision="fp64") -> torch.Tensor:
+    """Squared-exponential covariance of the rows of X (lower triangle, or full);
+    precision "mixed" evaluates r^2 and the exponential in double-float."""
     if not (X.is_cuda and X.dtype == torch.float64 and X.dim() == 2 and X.stride(1) == 1):
         raise ValueError("X must be a row-major float64 CUDA matrix")
     n, d = X.shape
     K = out if out is not None else torch.zeros(n, n, dtype=torch.float64, device=X.device)
     ldk = _square(K, "K")
     _check(capi.gpc_se_cov(n, d, _ptr(X), max(int(X.stride(0)), d), float(alpha), float(rho),
-                           float(sigma), float(jitter), _ptr(K), ldk, 1 if full else 0, _stream()),
+                           float(sigma), float(jitter), _ptr(K), ldk, 1 if full else 0,
+                           precision_code(precision), _stream()),
            "gpc_se_cov")
     return K
 
@@ -344,7 +375,8 @@ def se_hyper_grad_workspace_size(n: int) -> int:
 
 
 def se_hyper_grad(X: torch.Tensor, alpha: float, rho: float, sigma: float, Kbar: torch.Tensor,
-                  ws: torch.Tensor | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+                  ws: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                  precision="fp64") -> torch.Tensor:
     """(d/d alpha, d/d rho, d/d sigma) as a 3-vector on the device."""
     n, d = X.shape
     ldkb = _square(Kbar, "Kbar")
@@ -352,8 +384,8 @@ def se_hyper_grad(X: torch.Tensor, alpha: float, rho: float, sigma: float, Kbar:
     need = se_hyper_grad_workspace_size(n)
     wsb = ws if ws is not None else torch.empty(need, dtype=torch.uint8, device=X.device)
     _check(capi.gpc_se_hyper_grad(n, d, _ptr(X), max(int(X.stride(0)), d), float(alpha), float(rho),
-                                  float(sigma), _ptr(Kbar), ldkb, _ptr(g), _ptr(wsb),
-                                  wsb.numel() * wsb.element_size(), _stream()),
+                                  float(sigma), _ptr(Kbar), ldkb, _ptr(g), precision_code(precision),
+                                  _ptr(wsb), wsb.numel() * wsb.element_size(), _stream()),
            "gpc_se_hyper_grad")
     return g
 
@@ -465,7 +497,7 @@ class GPLml(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, y, hyp, jitter=0.0, precision="fp64"):
         a, r, s = (float(v) for v in hyp.detach().cpu().tolist())
-        K = se_cov(X, a, r, s, jitter)
+        K = se_cov(X, a, r, s, jitter, precision=precision)
         res = gp_lml(K, y, precision, L=K if precision_code(precision) == GPC_FP64 else None)
         ctx.save_for_backward(X, res["L"], res["alpha"])
         ctx.hyp = (a, r, s)
@@ -478,7 +510,7 @@ class GPLml(torch.autograd.Function):
         X, L, alpha = ctx.saved_tensors
         a, r, s = ctx.hyp
         Kbar = gp_lml_grad(L, alpha, 1.0, ctx.precision)
-        g = se_hyper_grad(X, a, r, s, Kbar)
+        g = se_hyper_grad(X, a, r, s, Kbar, precision=ctx.precision)
         return None, None, (g * gvalue).to(ctx.hyp_device), None, None
 
 

@@ -144,11 +144,11 @@ int gpc_workspace_size(int n, int precision, size_t *bytes) {
 }
 
 int gpc_se_cov(int n, int d, const double *X, int ldx, double alpha, double rho, double sigma,
-               double jitter, double *K, int ldk, int full, gpc_stream_t stream) {
-  if (n < 0 || d < 1 || d > kMaxDim) return GPC_ERR_INVALID_ARG;
+               double jitter, double *K, int ldk, int full, int precision, gpc_stream_t stream) {
+  if (n < 0 || d < 1 || d > kMaxDim || !valid_precision(precision)) return GPC_ERR_INVALID_ARG;
   if (n == 0) return GPC_OK;
   if (!X || ldx < d || bad_square(n, K, ldk) || !(rho > 0.0)) return GPC_ERR_INVALID_ARG;
-  return status_of(se_cov(n, d, X, ldx, alpha, rho, sigma, jitter, K, ldk, full, stream));
+  return status_of(se_cov(n, d, X, ldx, alpha, rho, sigma, jitter, K, ldk, full, precision == GPC_MIXED, stream));
 }
 
 int gpc_chol(int n, const double *K, int ldk, double *L, int ldl, int precision, void *ws,
@@ -275,13 +275,14 @@ int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double
 }
 
 int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, double rho,
-                      double sigma, const double *Kbar, int ldkb, double *grad3, void *ws,
+                      double sigma, const double *Kbar, int ldkb, double *grad3, int precision, void *ws,
                       size_t ws_bytes, gpc_stream_t stream) {
-  if (n < 0 || d < 1 || d > kMaxDim || !grad3) return GPC_ERR_INVALID_ARG;
+  if (n < 0 || d < 1 || d > kMaxDim || !grad3 || !valid_precision(precision)) return GPC_ERR_INVALID_ARG;
   if (n > 0 && (!X || ldx < d || bad_square(n, Kbar, ldkb) || !(rho > 0.0) || !(alpha != 0.0) ||
                 !ws || ws_bytes < se_hyper_grad_workspace_bytes(n)))
     return GPC_ERR_INVALID_ARG;
-  return status_of(se_hyper_grad(n, d, X, ldx, alpha, rho, sigma, Kbar, ldkb, grad3, ws, stream));
+  return status_of(
+      se_hyper_grad(n, d, X, ldx, alpha, rho, sigma, Kbar, ldkb, grad3, ws, precision == GPC_MIXED, stream));
 }
 
 constexpr int kBatchMaxN = 4096;

@@ -110,13 +110,14 @@ int chol_block_size(int precision);
 
 // ---------------------------------------------------------------- GP pieces
 constexpr int kMaxDim = 256;
+// mixed: r^2 and the exponential in double-float arithmetic (about 2^-46 per entry)
 cudaError_t se_cov(int n, int d, const double *X, long long ldx, double alpha, double rho,
-                   double sigma, double jitter, double *K, long long ldk, int full,
+                   double sigma, double jitter, double *K, long long ldk, int full, bool mixed,
                    cudaStream_t s);
 size_t se_hyper_grad_workspace_bytes(int n);
 cudaError_t se_hyper_grad(int n, int d, const double *X, long long ldx, double alpha,
                           double rho, double sigma, const double *Kbar, long long ldkb,
-                          double *grad3, void *ws, cudaStream_t s);
+                          double *grad3, void *ws, bool mixed, cudaStream_t s);
 // scal[0] = logdet = 2 sum log L_ii, scal[1] = y . alpha, value = -1/2 scal[1] - 1/2 logdet
 // - n/2 log(2 pi).  logdet/value may be null.
 cudaError_t lml_finalize(int n, const double *L, long long ldl, const double *y,
@@ -176,12 +177,13 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
 // (gpc_trace_enable) CUDA events are also recorded on the launching stream
 // so per-class device time can be read back with gpc_trace_summary.
 // Classes match the GPC_TRACE_* values of the public header.
-void trace_begin(int cls, cudaStream_t s);
+// The launch expression's text names the kernel in the timeline.
+void trace_begin(int cls, const char *what, cudaStream_t s);
 void trace_end(int cls, double flops, double bytes, cudaStream_t s);
-#define GPC_LAUNCH(cls, flops, bytes, stream, ...) \
-  do {                                              \
-    ::gpc::trace_begin((cls), (stream));            \
-    __VA_ARGS__;                                    \
+#define GPC_LAUNCH(cls, flops, bytes, stream, ...)     \
+  do {                                                  \
+    ::gpc::trace_begin((cls), #__VA_ARGS__, (stream));  \
+    __VA_ARGS__;                                        \
     ::gpc::trace_end((cls), (flops), (bytes), (stream)); \
   } while (0)
 

@@ -106,16 +106,25 @@ trtri_batched_kernel(int n, const double *L, long long ldl, int first, int b, do
                    nullptr, 0, 0);
 }
 
-// Cholesky factor of one nb x nb diagonal block in shared memory, left-looking
-// by columns (each column j: s_i = A_ij - sum_{k<j} L_ik L_jk for all rows
-// i >= j at once, two threads per row; L_jj = sqrt(s_j); L_ij = s_i / L_jj).
-// Writes L11 in place with the upper part of the block zeroed; a failing
-// pivot is recorded like potrf_trtri_kernel.  No inverse is formed: the
-// panel below is solved by substitution (trsm_rows_kernel).
+// Cholesky factor of one nb x nb diagonal block in shared memory (the small-
+// block step of Section 3.3), blocked right-looking with panels of PF_PW
+// columns.  Per panel: warp 0 factors the PF_PW x PF_PW diagonal sub-block
+// column by column (pivot, one reciprocal, scaled column, rank-1 update);
+// one thread per row below solves that row against the sub-block and also
+// writes it, transposed, into a panel buffer; then every thread updates 4 x 4
+// tiles of the trailing lower triangle from the panel buffer (row and column
+// quadruples read as contiguous pairs, so the loads are conflict-free).  The
+// FP64 pipe of one SM bounds it: about nb^3/6 fused multiply-adds.  Writes L11
+// in place with the upper part of the block zeroed; the first failing pivot is
+// recorded in info (GPC_ERR_NOT_PD, or GPC_ERR_NAN for NaN/Inf) and the rest of
+// the block is written back unfinished.  No inverse is formed: the panel below
+// is solved by substitution (trsm_rows_kernel).
+constexpr int PF_PW = 16;
 __global__ void __launch_bounds__(DIAG_THREADS)
 potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset) {
-  extern __shared__ double smem[];
-  __shared__ double colv[kMaxBlock];
+  extern __shared__ double smem[];                       // nb x (nb + 1)
+  __shared__ __align__(16) double pt[PF_PW][kMaxBlock + 4];  // panel rows below, transposed
+  __shared__ double rdiag[PF_PW];
   __shared__ int fail;
   const int ld = nb + 1;
   if (threadIdx.x == 0) fail = 0;
@@ -124,29 +133,101 @@ potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset)
     S(smem, ld, i, j) = (j <= i) ? A[(long long)i * lda + j] : 0.0;
   }
   __syncthreads();
-  const int i = threadIdx.x >> 1, h = threadIdx.x & 1;
-  for (int j = 0; j < nb; ++j) {
-    double sacc = 0.0;
-    if (i >= j && i < nb)
-      for (int k = h; k < j; k += 2) sacc = fma(S(smem, ld, i, k), S(smem, ld, j, k), sacc);
-    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
-    if (h == 0 && i >= j && i < nb) colv[i] = S(smem, ld, i, j) - sacc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double pv = colv[j];
-      if (pv > 0.0 && pv <= 1.79769313486231570e308) {
-        S(smem, ld, j, j) = sqrt(pv);
-      } else {
-        fail = 1;
-        if (info && info[1] == 0) {
-          info[0] = pivot_offset + j;
-          info[1] = (pv != pv || pv > 1.79769313486231570e308) ? GPC_ERR_NAN : GPC_ERR_NOT_PD;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int p0 = 0; p0 < nb; p0 += PF_PW) {
+    const int pw = min(PF_PW, nb - p0), m0 = p0 + pw;
+    // 1. diagonal sub-block, warp 0: lane l owns row jj + 1 + l of the sub-block
+    if (warp == 0) {
+      for (int j = 0; j < pw; ++j) {
+        const int jj = p0 + j;
+        const double pv = S(smem, ld, jj, jj);
+        if (!(pv > 0.0 && pv <= 1.79769313486231570e308)) {
+          if (lane == 0) {
+            fail = 1;
+            if (info && info[1] == 0) {
+              info[0] = pivot_offset + jj;
+              info[1] = (pv != pv || pv > 1.79769313486231570e308) ? GPC_ERR_NAN : GPC_ERR_NOT_PD;
+            }
+          }
+          break;
         }
+        const double d = sqrt(pv), r = 1.0 / d;
+        const int i = jj + 1 + lane;
+        double lij = 0.0;
+        if (i < m0) lij = S(smem, ld, i, jj) * r;
+        __syncwarp();
+        if (lane == 0) {
+          S(smem, ld, jj, jj) = d;
+          rdiag[j] = r;
+        }
+        if (i < m0) S(smem, ld, i, jj) = lij;
+        __syncwarp();
+        if (i < m0)
+          for (int k = jj + 1; k <= i; ++k) S(smem, ld, i, k) = fma(-lij, S(smem, ld, k, jj), S(smem, ld, i, k));
+        __syncwarp();
       }
     }
     __syncthreads();
     if (fail) break;
-    if (h == 0 && i > j && i < nb) S(smem, ld, i, j) = colv[i] / S(smem, ld, j, j);
+    // 2. rows below the sub-block: x = a L_pp^{-T} by forward substitution
+    for (int i = m0 + threadIdx.x; i < nb; i += blockDim.x) {
+      double x[PF_PW];
+#pragma unroll
+      for (int j = 0; j < PF_PW; ++j) x[j] = (j < pw) ? S(smem, ld, i, p0 + j) : 0.0;
+#pragma unroll
+      for (int j = 0; j < PF_PW; ++j) {
+        if (j < pw) {
+          double v = x[j];
+#pragma unroll
+          for (int k = 0; k < j; ++k) v = fma(-x[k], S(smem, ld, p0 + j, p0 + k), v);
+          x[j] = v * rdiag[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < PF_PW; ++j) {
+        if (j < pw) {
+          S(smem, ld, i, p0 + j) = x[j];
+          pt[j][i - m0] = x[j];
+        }
+      }
+    }
+    __syncthreads();
+    // 3. trailing update of the lower triangle, rows and columns in [m0, nb)
+    const int m = nb - m0;
+    if (m > 0) {
+      const int tb = (m + 3) >> 2, ntiles = tb * (tb + 1) / 2;
+      for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        while (ti * (ti + 1) / 2 > t) --ti;
+        const int tk = t - ti * (ti + 1) / 2;
+        const int r0 = 4 * ti, c0 = 4 * tk;  // offsets from m0
+        double acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+#pragma unroll
+        for (int q = 0; q < PF_PW; ++q) {
+          if (q < pw) {
+            const double2 a01 = *(const double2 *)&pt[q][r0], a23 = *(const double2 *)&pt[q][r0 + 2];
+            const double2 b01 = *(const double2 *)&pt[q][c0], b23 = *(const double2 *)&pt[q][c0 + 2];
+            const double a[4] = {a01.x, a01.y, a23.x, a23.y}, bc[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bc[v], acc[u][v]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int i = m0 + r0 + u, k = m0 + c0 + v;
+            if (i < nb && k <= i) S(smem, ld, i, k) -= acc[u][v];
+          }
+      }
+    }
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {

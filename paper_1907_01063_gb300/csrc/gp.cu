@@ -3,6 +3,7 @@
 // adjoint Lbar and the hyperparameter gradient (GP regression of Section 4.2;
 // triangular solves of Section 3.2).
 #include "common.cuh"
+#include "df.cuh"
 
 namespace gpc {
 namespace {
@@ -47,6 +48,56 @@ se_cov_kernel(int n, int d, const double *X, long long ldx, double a2, double in
         r2 = fma(df, df, r2);
       }
       v = a2 * exp(-r2 * inv2r2);
+    }
+    K[(long long)i * ldk + j] = v;
+    if (full && i != j) K[(long long)j * ldk + i] = v;
+  }
+}
+
+// Mixed-precision covariance: the same matrix with r^2 and the exponential in
+// double-float arithmetic (FP32 pairs, about 2^-46 relative per entry; see
+// df.cuh) and one conversion to FP64 per entry.  Entries with
+// r^2 / (2 rho^2) > 80 (below 2^-115 alpha^2) take FP64's exp instead.
+__device__ __forceinline__ dfa::df se_r2_df(const dfa::df *xi, const dfa::df *xj, int d) {
+  dfa::df r2 = {0.0f, 0.0f};
+  for (int t = 0; t < d; ++t) {
+    const dfa::df df_ = dfa::add(xi[t], dfa::neg(xj[t]));
+    r2 = dfa::add_same_sign(r2, dfa::mul(df_, df_));
+  }
+  return r2;
+}
+
+__global__ void __launch_bounds__(256)
+se_cov_df_kernel(int n, int d, const double *X, long long ldx, double a2, dfa::df inv2r2, double diagv,
+                 double *K, long long ldk, int full) {
+  extern __shared__ double xs_raw[];  // [2][CT][d] double-floats
+  dfa::df *xi = (dfa::df *)xs_raw, *xj = xi + CT * d;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int i0 = ti * CT, j0 = tj * CT;
+  for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
+    const int r = idx / d, t = idx - r * d;
+    xi[idx] = dfa::from_double((i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0);
+    xj[idx] = dfa::from_double((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
+  }
+  __syncthreads();
+  const int c = threadIdx.x & (CT - 1);
+  const int j = j0 + c;
+  for (int r = threadIdx.x >> 5; r < CT; r += blockDim.x >> 5) {
+    const int i = i0 + r;
+    if (i >= n || j >= n || j > i) continue;
+    double v;
+    if (i == j) {
+      v = a2 + diagv;
+    } else {
+      const dfa::df t = dfa::mul(se_r2_df(xi + r * d, xj + c * d, d), inv2r2);
+      if (t.hi <= 80.0f) {
+        int k;
+        const dfa::df m = dfa::exp_neg(t, k);
+        v = dfa::to_double(m) * (a2 * dfa::pow2(k));
+      } else {
+        v = a2 * exp(-dfa::to_double(t));
+      }
     }
     K[(long long)i * ldk + j] = v;
     if (full && i != j) K[(long long)j * ldk + i] = v;
@@ -98,6 +149,68 @@ se_hyper_grad_kernel(int n, int d, const double *X, long long ldx, double alpha,
     gr = fma(kb, kf * r2 * inv_r3, gr);
     if (i == j) gs = fma(kb, 2.0 * sigma, gs);
   }
+  const double sa = block_sum_256(ga, red);
+  const double sr = block_sum_256(gr, red);
+  const double ss = block_sum_256(gs, red);
+  if (threadIdx.x == 0) {
+    partial[3 * (size_t)blockIdx.x + 0] = sa;
+    partial[3 * (size_t)blockIdx.x + 1] = sr;
+    partial[3 * (size_t)blockIdx.x + 2] = ss;
+  }
+}
+
+// Mixed-precision hyperparameter gradient: the sums sum Kbar_ij e_ij and
+// sum Kbar_ij e_ij r2_ij (e_ij = exp(-r2_ij / (2 rho^2))) are accumulated per
+// thread in double-float, then reduced in FP64; partial = (2 alpha S_e,
+// alpha^2 / rho^3 S_er, 2 sigma sum Kbar_ii) per tile as in the FP64 kernel.
+__global__ void __launch_bounds__(256)
+se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alpha, double rho,
+                        double sigma, dfa::df inv2r2, const double *Kbar, long long ldkb, double *partial) {
+  extern __shared__ double xs_raw[];
+  __shared__ double red[8];
+  dfa::df *xi = (dfa::df *)xs_raw, *xj = xi + CT * d;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int i0 = ti * CT, j0 = tj * CT;
+  for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
+    const int r = idx / d, t = idx - r * d;
+    xi[idx] = dfa::from_double((i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0);
+    xj[idx] = dfa::from_double((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
+  }
+  __syncthreads();
+  const int c = threadIdx.x & (CT - 1);
+  const int j = j0 + c;
+  dfa::df se = {0.0f, 0.0f}, ser = {0.0f, 0.0f};
+  double big_e = 0.0, big_er = 0.0, gs = 0.0;  // entries past the double-float range, in FP64
+  for (int r = threadIdx.x >> 5; r < CT; r += blockDim.x >> 5) {
+    const int i = i0 + r;
+    if (i >= n || j >= n || j > i) continue;
+    const double kb = Kbar[(long long)i * ldkb + j];
+    if (i == j) {
+      se = dfa::add(se, dfa::from_double(kb));  // e_ii = 1, r2_ii = 0
+      gs = fma(kb, 2.0 * sigma, gs);
+      continue;
+    }
+    const dfa::df r2 = se_r2_df(xi + r * d, xj + c * d, d);
+    const dfa::df t = dfa::mul(r2, inv2r2);
+    if (t.hi <= 80.0f) {
+      int k;
+      const dfa::df m = dfa::exp_neg(t, k);
+      const float sc = __int_as_float((k + 127) << 23);  // 2^k, k >= -116
+      const dfa::df e = {m.hi * sc, m.lo * sc};
+      const dfa::df w = dfa::mul(dfa::from_double(kb), e);
+      se = dfa::add(se, w);
+      ser = dfa::add(ser, dfa::mul(w, r2));
+    } else {
+      const double r2d = dfa::to_double(r2);
+      const double w = kb * exp(-dfa::to_double(t));
+      big_e += w;
+      big_er = fma(w, r2d, big_er);
+    }
+  }
+  const double a2 = alpha * alpha, inv_r3 = 1.0 / (rho * rho * rho);
+  const double ga = 2.0 * alpha * (dfa::to_double(se) + big_e);
+  const double gr = a2 * inv_r3 * (dfa::to_double(ser) + big_er);
   const double sa = block_sum_256(ga, red);
   const double sr = block_sum_256(gr, red);
   const double ss = block_sum_256(gs, red);
@@ -282,106 +395,167 @@ __device__ __forceinline__ bool wait_flag(const int *flag, int &value) {
   }
 }
 
-__global__ void __launch_bounds__(256)
+// Latency matters more than bandwidth here: every block waits for the one
+// before it.  So the CTA loads its inverse block into shared memory at start,
+// and the slice of L it multiplies by the next ready block of x is loaded into
+// registers while the CTA waits for that block's flag; once the last flag it
+// needs arrives, only one register-resident product, a shuffle reduction and
+// the product with the shared-memory inverse stand between it and its own flag.
+// The abort word is double-buffered by step parity so that a CTA's thread 0
+// can record a failed wait while slower warps still read the previous step's.
+constexpr int TI_ROWS = TIB / 8;  // rows per warp in the forward solve
+constexpr int TI_KU = TIB / 32;   // columns per lane in the forward solve
+constexpr int TI_RT = TIB / 2;    // rows per thread in the transposed solve
+
+__global__ void __launch_bounds__(256, 1)
 trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b, double *x, int trans,
                 int *sync, int *info, const int *skip) {
   if (skip && *skip) return;
-  __shared__ int s_order, s_abort;
+  extern __shared__ double dinv_s[];  // nb x nb inverse of this CTA's diagonal block
+  __shared__ int s_order, s_ab[2];
   __shared__ double vbuf[TIB];
+  __shared__ double xs[TIB];
   __shared__ double red[2][TIB];
   const int nblk = (n + b - 1) / b;
   if (threadIdx.x == 0) {
     s_order = atomicAdd(&sync[0], 1);
-    s_abort = 0;
+    s_ab[0] = s_ab[1] = 0;
   }
   __syncthreads();
   const int order = s_order;
   const int blk = trans ? (nblk - 1 - order) : order;
   const int i0 = blk * b, nb = min(b, n - i0);
   const double *Dinv = inv + (size_t)blk * b * b;
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) dinv_s[idx] = __ldg(Dinv + idx);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool aborted = false;
 
   if (!trans) {
-    double acc[TIB / 8];
+    double acc[TI_ROWS], lv[TI_ROWS][TI_KU];
 #pragma unroll
-    for (int t = 0; t < TIB / 8; ++t) acc[t] = 0.0;
+    for (int t = 0; t < TI_ROWS; ++t) {
+      acc[t] = 0.0;
+#pragma unroll
+      for (int u = 0; u < TI_KU; ++u) {
+        const int r = warp + 8 * t, k = lane + 32 * u;
+        lv[t][u] = (blk > 0 && r < nb && k < b) ? __ldg(L + (long long)(i0 + r) * ldl + k) : 0.0;
+      }
+    }
     for (int c = 0; c < blk; ++c) {
       if (threadIdx.x == 0) {
         int f;
-        if (!wait_flag(&sync[1 + c], f) || f != 1) s_abort = 1;
+        if (!wait_flag(&sync[1 + c], f) || f != 1) s_ab[c & 1] = 1;
         __threadfence();
       }
       __syncthreads();
-      if (s_abort) break;
+      if (s_ab[c & 1]) {
+        aborted = true;
+        break;
+      }
       const int c0 = c * b;  // c < blk: a full block
-      double xq[TIB / 32];
+      double xq[TI_KU];
 #pragma unroll
-      for (int u = 0; u < TIB / 32; ++u) xq[u] = (lane + 32 * u < b) ? __ldcg(&x[c0 + lane + 32 * u]) : 0.0;
+      for (int u = 0; u < TI_KU; ++u) xq[u] = (lane + 32 * u < b) ? __ldcg(&x[c0 + lane + 32 * u]) : 0.0;
 #pragma unroll
-      for (int t = 0; t < TIB / 8; ++t) {
-        const int r = warp + 8 * t;
-        if (r < nb) {
-          const double *row = L + (long long)(i0 + r) * ldl + c0;
+      for (int t = 0; t < TI_ROWS; ++t)
 #pragma unroll
-          for (int u = 0; u < TIB / 32; ++u)
-            if (lane + 32 * u < b) acc[t] = fma(row[lane + 32 * u], xq[u], acc[t]);
-        }
+        for (int u = 0; u < TI_KU; ++u) acc[t] = fma(lv[t][u], xq[u], acc[t]);
+      if (c + 1 < blk) {
+        const int c1 = c0 + b;
+#pragma unroll
+        for (int t = 0; t < TI_ROWS; ++t)
+#pragma unroll
+          for (int u = 0; u < TI_KU; ++u) {
+            const int r = warp + 8 * t, k = lane + 32 * u;
+            lv[t][u] = (r < nb && k < b) ? __ldg(L + (long long)(i0 + r) * ldl + c1 + k) : 0.0;
+          }
       }
     }
-    if (!s_abort) {
+    if (!aborted) {
 #pragma unroll
-      for (int t = 0; t < TIB / 8; ++t) {
+      for (int t = 0; t < TI_ROWS; ++t) {
         double v = acc[t];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int r = warp + 8 * t;
         if (lane == 0 && r < nb) vbuf[r] = x[i0 + r] - v;
       }
     }
-    __syncthreads();
-    if (!s_abort) {
-      for (int t = 0; t < TIB / 8; ++t) {
+    __syncthreads();  // vbuf and dinv_s complete
+    if (!aborted) {
+#pragma unroll
+      for (int t = 0; t < TI_ROWS; ++t) {
         const int r = warp + 8 * t;
-        if (r >= nb) break;
-        double v = 0.0;
-        for (int k = lane; k <= r; k += 32) v = fma(Dinv[(size_t)r * nb + k], vbuf[k], v);
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) x[i0 + r] = v;
+        if (r < nb) {
+          double v = 0.0;
+#pragma unroll
+          for (int u = 0; u < TI_KU; ++u) {
+            const int k = lane + 32 * u;
+            if (k <= r) v = fma(dinv_s[r * nb + k], vbuf[k], v);
+          }
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) {
+            x[i0 + r] = v;
+            __threadfence();
+          }
+        }
       }
     }
   } else {
     const int i = threadIdx.x & (TIB - 1), rg = threadIdx.x >> 7;
-    double acc = 0.0;
+    double acc = 0.0, lv[TI_RT];
+    {
+      const int c0 = (nblk - 1) * b, cn = n - c0;
+#pragma unroll
+      for (int m = 0; m < TI_RT; ++m) {
+        const int r = rg + 2 * m;
+        lv[m] = (order > 0 && i < nb && r < cn) ? __ldg(L + (long long)(c0 + r) * ldl + i0 + i) : 0.0;
+      }
+    }
     for (int step = 0; step < order; ++step) {
       const int c = nblk - 1 - step;
       if (threadIdx.x == 0) {
         int f;
-        if (!wait_flag(&sync[1 + c], f) || f != 1) s_abort = 1;
+        if (!wait_flag(&sync[1 + c], f) || f != 1) s_ab[step & 1] = 1;
         __threadfence();
       }
       __syncthreads();
-      if (s_abort) break;
+      if (s_ab[step & 1]) {
+        aborted = true;
+        break;
+      }
       const int c0 = c * b, cn = min(b, n - c0);
-      if (i < nb)
-        for (int r = rg; r < cn; r += 2) acc = fma(L[(long long)(c0 + r) * ldl + i0 + i], __ldcg(&x[c0 + r]), acc);
+      if (threadIdx.x < TIB) xs[threadIdx.x] = threadIdx.x < cn ? __ldcg(&x[c0 + threadIdx.x]) : 0.0;
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < TI_RT; ++m) acc = fma(lv[m], xs[rg + 2 * m], acc);
+      if (step + 1 < order) {
+        const int p0 = c0 - b;  // the next block up is a full block
+#pragma unroll
+        for (int m = 0; m < TI_RT; ++m) {
+          const int r = rg + 2 * m;
+          lv[m] = (i < nb && r < b) ? __ldg(L + (long long)(p0 + r) * ldl + i0 + i) : 0.0;
+        }
+      }
     }
     red[rg][i] = acc;
+    __syncthreads();  // red and dinv_s complete
+    if (!aborted && threadIdx.x < nb) vbuf[threadIdx.x] = x[i0 + threadIdx.x] - (red[0][threadIdx.x] + red[1][threadIdx.x]);
     __syncthreads();
-    if (!s_abort && threadIdx.x < nb) vbuf[threadIdx.x] = x[i0 + threadIdx.x] - (red[0][threadIdx.x] + red[1][threadIdx.x]);
+    double v = 0.0;
+    if (!aborted && i < nb)
+      for (int k = i + rg; k < nb; k += 2) v = fma(dinv_s[k * nb + i], vbuf[k], v);
+    red[rg][i] = v;
     __syncthreads();
-    if (!s_abort) {
-      double v = 0.0;
-      if (i < nb)
-        for (int k = i + rg; k < nb; k += 2) v = fma(Dinv[(size_t)k * nb + i], vbuf[k], v);
-      red[rg][i] = v;
+    if (!aborted && threadIdx.x < nb) {
+      x[i0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+      __threadfence();
     }
-    __syncthreads();
-    if (!s_abort && threadIdx.x < nb) x[i0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (s_abort && info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
+    if (aborted && info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
     __threadfence();
-    atomicExch(&sync[1 + blk], s_abort ? 2 : 1);
+    atomicExch(&sync[1 + blk], aborted ? 2 : 1);
   }
 }
 
@@ -438,7 +612,7 @@ __global__ void lml_lbar_kernel(int n, const double *L, long long ldl, const dou
   Lbar[(long long)i * ldlb + j] = v;
 }
 
-bool g_attr[64][2];
+bool g_attr[64][4];
 
 cudaError_t set_dyn_smem(const void *fn, int which) {
   int dev = 0;
@@ -451,21 +625,33 @@ cudaError_t set_dyn_smem(const void *fn, int which) {
   return e;
 }
 
+dfa::df host_df(double v) {
+  const float h = (float)v;
+  return dfa::df{h, (float)(v - (double)h)};
+}
+
 }  // namespace
 
 cudaError_t se_cov(int n, int d, const double *X, long long ldx, double alpha, double rho,
-                   double sigma, double jitter, double *K, long long ldk, int full,
+                   double sigma, double jitter, double *K, long long ldk, int full, bool mixed,
                    cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  cudaError_t e = set_dyn_smem((const void *)se_cov_kernel, 0);
+  cudaError_t e = mixed ? set_dyn_smem((const void *)se_cov_df_kernel, 2)
+                        : set_dyn_smem((const void *)se_cov_kernel, 0);
   if (e != cudaSuccess) return e;
   const long long T = (n + CT - 1) / CT;
   const size_t smem = 2 * CT * (size_t)d * sizeof(double);
   const double tri = 0.5 * (double)n * (n + 1);
-  GPC_LAUNCH(GPC_TRACE_SECOV, tri * 3.0 * d, 8.0 * (full ? 2.0 * tri - n : tri) + 8.0 * n * d, s,
-             se_cov_kernel<<<(unsigned)(T * (T + 1) / 2), 256, smem, s>>>(
-                 n, d, X, ldx, alpha * alpha, 1.0 / (2.0 * rho * rho), sigma * sigma + jitter, K,
-                 ldk, full));
+  const double inv2r2 = 1.0 / (2.0 * rho * rho);
+  if (mixed) {
+    GPC_LAUNCH(GPC_TRACE_SECOV, tri * 3.0 * d, 8.0 * (full ? 2.0 * tri - n : tri) + 8.0 * n * d, s,
+               se_cov_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, smem, s>>>(
+                   n, d, X, ldx, alpha * alpha, host_df(inv2r2), sigma * sigma + jitter, K, ldk, full));
+  } else {
+    GPC_LAUNCH(GPC_TRACE_SECOV, tri * 3.0 * d, 8.0 * (full ? 2.0 * tri - n : tri) + 8.0 * n * d, s,
+               se_cov_kernel<<<(unsigned)(T * (T + 1) / 2), 256, smem, s>>>(
+                   n, d, X, ldx, alpha * alpha, inv2r2, sigma * sigma + jitter, K, ldk, full));
+  }
   return cudaGetLastError();
 }
 
@@ -476,18 +662,25 @@ size_t se_hyper_grad_workspace_bytes(int n) {
 
 cudaError_t se_hyper_grad(int n, int d, const double *X, long long ldx, double alpha, double rho,
                           double sigma, const double *Kbar, long long ldkb, double *grad3,
-                          void *ws, cudaStream_t s) {
+                          void *ws, bool mixed, cudaStream_t s) {
   if (n <= 0) return cudaMemsetAsync(grad3, 0, 3 * sizeof(double), s);
-  cudaError_t e = set_dyn_smem((const void *)se_hyper_grad_kernel, 1);
+  cudaError_t e = mixed ? set_dyn_smem((const void *)se_hyper_grad_df_kernel, 3)
+                        : set_dyn_smem((const void *)se_hyper_grad_kernel, 1);
   if (e != cudaSuccess) return e;
   const long long T = (n + CT - 1) / CT;
   const long long tiles = T * (T + 1) / 2;
   const size_t smem = 2 * CT * (size_t)d * sizeof(double);
   double *partial = (double *)ws;
   const double tri = 0.5 * (double)n * (n + 1);
-  GPC_LAUNCH(GPC_TRACE_HYPER, tri * (3.0 * d + 6.0), 8.0 * tri + 8.0 * n * d, s,
-             se_hyper_grad_kernel<<<(unsigned)tiles, 256, smem, s>>>(n, d, X, ldx, alpha, rho,
-                                                                     sigma, Kbar, ldkb, partial));
+  if (mixed) {
+    GPC_LAUNCH(GPC_TRACE_HYPER, tri * (3.0 * d + 6.0), 8.0 * tri + 8.0 * n * d, s,
+               se_hyper_grad_df_kernel<<<(unsigned)tiles, 256, smem, s>>>(
+                   n, d, X, ldx, alpha, rho, sigma, host_df(1.0 / (2.0 * rho * rho)), Kbar, ldkb, partial));
+  } else {
+    GPC_LAUNCH(GPC_TRACE_HYPER, tri * (3.0 * d + 6.0), 8.0 * tri + 8.0 * n * d, s,
+               se_hyper_grad_kernel<<<(unsigned)tiles, 256, smem, s>>>(n, d, X, ldx, alpha, rho,
+                                                                       sigma, Kbar, ldkb, partial));
+  }
   GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 24.0 * tiles, s, sum3_kernel<<<1, 256, 0, s>>>(partial, tiles, grad3));
   return cudaGetLastError();
 }
@@ -517,8 +710,18 @@ cudaError_t trsv_inv(int n, const double *L, long long ldl, const double *inv, i
   int *sync = (int *)ws;
   cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nblk + 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    e = cudaFuncSetAttribute(trsv_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(TIB * TIB * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const size_t smem = (size_t)b * b * sizeof(double);
   GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n + 2.0 * n * b, 4.0 * (double)n * (n + 1) + 8.0 * n * b, s,
-             trsv_inv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, inv, b, x, trans ? 1 : 0, sync, info, skip));
+             trsv_inv_kernel<<<nblk, 256, smem, s>>>(n, L, ldl, inv, b, x, trans ? 1 : 0, sync, info, skip));
   return cudaGetLastError();
 }
 

@@ -88,9 +88,9 @@ size_t mixed_workspace_bytes(int n) {
 // Lookahead: the trailing update of step k is split into the next block
 // column (on the caller's stream, so step k+1 can start) and the rest (on an
 // auxiliary stream, one SM left free).  Step k+1's conversion and diagonal
-// factorisation then overlap the rest of step k's update; its panel product,
-// which needs the whole GPU, waits for it.  Slices alternate between two
-// buffers so a split never overwrites slices still being read.
+// factorisation then overlap the rest of step k's update; its panel solve,
+// which needs the whole GPU's FP64 rate, waits for it.  Slices alternate
+// between two buffers so a split never overwrites slices still being read.
 cudaError_t chol_mixed(int n, double *L, long long ldl, void *ws, int *info, cudaStream_t s) {
   MixWs w = carve(ws, n, false);
   Aux *aux = nullptr;

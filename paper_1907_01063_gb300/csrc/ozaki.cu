@@ -417,8 +417,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       // vector path: the 32 columns of this thread are in range, 16-byte aligned, and not cut by the diagonal
       const bool vec = row_ok && colh + 32 <= p.N && (((uintptr_t)(dst + colh)) & 15) == 0 &&
                        !(p.lower && colh + 31 > row);
-      for (int c = c0; c < c1; ++c) {
-        float2 cv[32];
+      // the double-float sum of this work item stays in registers across its
+      // chunks: C is read once before the first chunk and written once after the last
+      // (a split-K partial tile starts from zero and is written whole, so it is not read)
+      float2 cv[32];
+      if (p.partial) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) cv[i] = make_float2(0.f, 0.f);
+      } else {
         if (vec) {
           const float4 *src = (const float4 *)(dst + colh);
 #pragma unroll
@@ -434,6 +440,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             cv[i] = (col < p.N && !(p.lower && col > row)) ? dst[col] : make_float2(0.f, 0.f);
           }
         }
+      }
+      for (int c = c0; c < c1; ++c) {
         if (!mbar_wait(tfull0 + 8 * buf, tphase, abort_flag)) { ok = false; break; }
         fence_after();
         const uint32_t tacc = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * OZ_ACC_COLS) + half * 32;
@@ -454,6 +462,9 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
         if (++buf == 2) { buf = 0; tphase ^= 1; }
+      }
+      if (!ok) break;
+      {
         if (vec) {
           float4 *out = (float4 *)(dst + colh);
 #pragma unroll
@@ -700,10 +711,6 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
   p.ldc = ldc;
   p.partial = splits > 1 ? partial : nullptr;
   p.err = err;
-  if (splits > 1) {
-    cudaError_t e = cudaMemsetAsync(partial, 0, (size_t)splits * M * N * sizeof(float2), s);
-    if (e != cudaSuccess) return e;
-  }
   const int grid = std::min(p.num_work, max_ctas > 0 ? std::min(max_ctas, sm_count()) : sm_count());
   // output entries: the whole M x N block, or its lower part (col <= row)
   const double mn = !lower ? (double)M * N

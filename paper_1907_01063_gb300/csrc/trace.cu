@@ -2,8 +2,11 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 namespace gpc {
@@ -11,9 +14,19 @@ namespace {
 
 struct Rec {
   int cls;
+  int name;
+  cudaStream_t stream;
   cudaEvent_t e0, e1;
   double flops, bytes;
 };
+
+struct Span {
+  int cls, name;
+  unsigned long long stream;
+  float start_ms, dur_ms;
+};
+
+constexpr size_t kMaxSpans = 1u << 21;
 
 struct TraceState {
   std::mutex mu;
@@ -22,6 +35,14 @@ struct TraceState {
   std::deque<Rec> recs;
   std::vector<cudaEvent_t> pool;
   cudaEvent_t pending = nullptr;  // begin event of the launch in progress
+  int pending_name = -1;
+  cudaStream_t pending_stream = nullptr;
+  // timeline mode: one span per launch, start relative to the first traced launch
+  bool timeline = false;
+  cudaEvent_t base = nullptr;
+  std::vector<Span> spans;
+  std::vector<std::string> names;
+  std::unordered_map<const char *, int> name_ids;
   long long cls_launches[GPC_TRACE_CLASSES] = {};
   double cls_ms[GPC_TRACE_CLASSES] = {};
   double cls_flops[GPC_TRACE_CLASSES] = {};
@@ -62,7 +83,12 @@ void drain(TraceState &t, bool block) {
     t.cls_launches[r.cls] += 1;
     t.cls_flops[r.cls] += r.flops;
     t.cls_bytes[r.cls] += r.bytes;
-    if (r.e0) t.pool.push_back(r.e0);
+    if (t.timeline && r.e0 && t.spans.size() < kMaxSpans) {
+      float start = 0.f;
+      if (t.base) cudaEventElapsedTime(&start, t.base, r.e0);
+      t.spans.push_back(Span{r.cls, r.name, (unsigned long long)(uintptr_t)r.stream, start, ms});
+    }
+    if (r.e0 && r.e0 != t.base) t.pool.push_back(r.e0);
     if (r.e1) t.pool.push_back(r.e1);
     t.recs.pop_front();
   }
@@ -70,12 +96,31 @@ void drain(TraceState &t, bool block) {
 
 }  // namespace
 
-void trace_begin(int /*cls*/, cudaStream_t s) {
+// The kernel's name is the launch expression's text up to "<<<".
+int name_id(TraceState &t, const char *what) {
+  auto it = t.name_ids.find(what);
+  if (it != t.name_ids.end()) return it->second;
+  std::string n(what);
+  const size_t cut = n.find("<<<");
+  if (cut != std::string::npos) n.resize(cut);
+  while (!n.empty() && (n.back() == ' ' || n.back() == '\n')) n.pop_back();
+  const int id = (int)t.names.size();
+  t.names.push_back(n);
+  t.name_ids.emplace(what, id);
+  return id;
+}
+
+void trace_begin(int /*cls*/, const char *what, cudaStream_t s) {
   TraceState &t = st();
   if (!t.on) return;
   std::lock_guard<std::mutex> g(t.mu);
   t.pending = get_event(t);
-  if (t.pending) cudaEventRecord(t.pending, s);
+  t.pending_name = name_id(t, what);
+  t.pending_stream = s;
+  if (t.pending) {
+    cudaEventRecord(t.pending, s);
+    if (t.timeline && !t.base) t.base = t.pending;
+  }
 }
 
 void trace_end(int cls, double flops, double bytes, cudaStream_t s) {
@@ -85,7 +130,7 @@ void trace_end(int cls, double flops, double bytes, cudaStream_t s) {
   if (!t.on) return;
   cudaEvent_t e1 = get_event(t);
   if (e1) cudaEventRecord(e1, s);
-  t.recs.push_back(Rec{cls, t.pending, e1, flops, bytes});
+  t.recs.push_back(Rec{cls, t.pending_name, t.pending_stream, t.pending, e1, flops, bytes});
   t.pending = nullptr;
   if (t.recs.size() >= 4096) drain(t, t.recs.size() >= (1u << 20));
 }
@@ -164,6 +209,7 @@ int gpc_launch_count(long long *count) {
 }
 
 int gpc_trace_enable(int on) {
+  if (on < 0 || on > 2) return GPC_ERR_INVALID_ARG;
   TraceState &t = st();
   std::lock_guard<std::mutex> g(t.mu);
   drain(t, true);
@@ -172,8 +218,46 @@ int gpc_trace_enable(int on) {
       t.cls_launches[c] = 0;
       t.cls_ms[c] = t.cls_flops[c] = t.cls_bytes[c] = 0.0;
     }
+    if (on == 2) {
+      if (t.base) t.pool.push_back(t.base);
+      t.base = nullptr;
+      t.spans.clear();
+    }
   }
+  if (on) t.timeline = on == 2;  // stopping keeps the spans recorded so far
   t.on = on != 0;
+  return GPC_OK;
+}
+
+int gpc_trace_timeline(long long max, int *cls, int *name, unsigned long long *stream, float *start_ms,
+                       float *dur_ms, long long *count) {
+  if (!count || max < 0 || (max > 0 && (!cls || !name || !stream || !start_ms || !dur_ms)))
+    return GPC_ERR_INVALID_ARG;
+  TraceState &t = st();
+  std::lock_guard<std::mutex> g(t.mu);
+  drain(t, true);
+  const long long n = (long long)t.spans.size();
+  *count = n;
+  for (long long i = 0; i < std::min(n, max); ++i) {
+    const Span &sp = t.spans[(size_t)i];
+    cls[i] = sp.cls;
+    name[i] = sp.name;
+    stream[i] = sp.stream;
+    start_ms[i] = sp.start_ms;
+    dur_ms[i] = sp.dur_ms;
+  }
+  return GPC_OK;
+}
+
+int gpc_trace_name(int name, char *buf, size_t buf_bytes) {
+  if (!buf || buf_bytes == 0) return GPC_ERR_INVALID_ARG;
+  TraceState &t = st();
+  std::lock_guard<std::mutex> g(t.mu);
+  if (name < 0 || name >= (int)t.names.size()) return GPC_ERR_INVALID_ARG;
+  const std::string &n = t.names[(size_t)name];
+  const size_t len = std::min(n.size(), buf_bytes - 1);
+  std::memcpy(buf, n.data(), len);
+  buf[len] = '\0';
   return GPC_OK;
 }
 

@@ -80,13 +80,14 @@ def test_argument_checks_return_before_any_launch():
     assert c.gpc_chol_adjoint(10, fake, 10, 0x100000, 10, 0x100000, 10, 0, 0, fake, 16, None) == bad
     assert c.gpc_chol_adjoint(10, fake, 10, 0x100000, 10, fake, 10, 0, 0, fake, 1 << 30, None) == bad
     assert c.gpc_trsv(10, None, 10, fake, 0, fake, 1 << 20, None) == bad
-    assert c.gpc_se_cov(10, 0, fake, 1, 1.0, 1.0, 0.1, 0.0, fake, 10, 0, None) == bad
-    assert c.gpc_se_cov(10, 2, fake, 2, 1.0, 0.0, 0.1, 0.0, fake, 10, 0, None) == bad
-    assert c.gpc_se_cov(10, 2, fake, 2, 1.0, -1.0, 0.1, 0.0, fake, 10, 0, None) == bad
+    assert c.gpc_se_cov(10, 0, fake, 1, 1.0, 1.0, 0.1, 0.0, fake, 10, 0, 0, None) == bad
+    assert c.gpc_se_cov(10, 2, fake, 2, 1.0, 0.0, 0.1, 0.0, fake, 10, 0, 0, None) == bad
+    assert c.gpc_se_cov(10, 2, fake, 2, 1.0, -1.0, 0.1, 0.0, fake, 10, 0, 0, None) == bad
     assert c.gpc_gp_lml(10, fake, 10, fake, 0x100000, 10, 0, None, fake, fake, fake, 1 << 30,
                         fake, None) == bad
-    assert c.gpc_se_hyper_grad(10, 2, fake, 2, 1.0, 1.0, 0.1, fake, 10, None, fake, 1 << 20, None) == bad
+    assert c.gpc_se_hyper_grad(10, 2, fake, 2, 1.0, 1.0, 0.1, fake, 10, None, 0, fake, 1 << 20, None) == bad
     # zero-size calls that need no device work
     assert c.gpc_chol_adjoint(0, None, 0, None, 0, None, 0, 0, 0, None, 0, None) == gp.GPC_OK
     assert c.gpc_trsv(0, None, 0, None, 0, None, 0, None) == gp.GPC_OK
-    assert c.gpc_se_cov(0, 1, None, 1, 1.0, 1.0, 0.1, 0.0, None, 0, 0, None) == gp.GPC_OK
+    assert c.gpc_se_cov(0, 1, None, 1, 1.0, 1.0, 0.1, 0.0, None, 0, 0, 0, None) == gp.GPC_OK
+    assert c.gpc_se_cov(10, 2, fake, 2, 1.0, 1.0, 0.1, 0.0, fake, 10, 0, 7, None) == bad  # precision

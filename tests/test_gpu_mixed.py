@@ -153,3 +153,46 @@ def test_gp_lml_mixed_rejects_in_place():
     K = gp.se_cov(dev(X), a, r, s, 0.0)
     with pytest.raises(gp.GpcholError):
         gp.gp_lml(K, dev(y), precision="mixed", L=K)
+
+
+@pytest.mark.parametrize("n,d,rho", [(1, 1, 1.0), (33, 16, 4.0), (257, 3, 0.3), (300, 7, 1.3), (130, 2, 0.05)])
+def test_se_cov_mixed_double_float(n, d, rho):
+    # r^2 and exp in double-float: about 2^-46 per entry against the FP64 oracle;
+    # rho = 0.05 sends many entries past r^2 / (2 rho^2) = 80 (the FP64 fallback)
+    X = W.gp_inputs(n, d, seed=n + d)
+    Ko = O.se_cov(X, 1.3, rho, 0.2, 1e-8, full=True)
+    K = gp.se_cov(dev(X), 1.3, rho, 0.2, 1e-8, full=True, precision="mixed").cpu().numpy()
+    # an absolute error of ~2^-46 t in the exponent t = r^2 / (2 rho^2) moves
+    # e^{-t} by ~2^-46 t relative (the same growth FP64 has at 2^-53)
+    off = ~np.eye(n, dtype=bool)
+    t = np.ones_like(Ko)
+    with np.errstate(divide="ignore"):
+        t[off] = np.maximum(1.0, -np.log(Ko[off] / 1.3 ** 2))
+    t[~np.isfinite(t)] = 1.0  # FP64 underflow to zero: the absolute term covers it
+    assert np.all(np.abs(K - Ko) <= 2e-13 * t * np.abs(Ko) + 1e-300)
+    assert np.array_equal(np.diag(K), np.diag(Ko))
+
+
+def test_hyper_grad_mixed_close_to_oracle_and_deterministic():
+    n, d = 513, 4
+    X = W.gp_inputs(n, d, seed=5)
+    Kbar = np.tril(W.random_lower(n, seed=6))
+    ref = O.se_hyper_grad(X, 1.1, 0.7, 0.3, Kbar)
+    g1 = gp.se_hyper_grad(dev(X), 1.1, 0.7, 0.3, dev(Kbar), precision="mixed")
+    g2 = gp.se_hyper_grad(dev(X), 1.1, 0.7, 0.3, dev(Kbar), precision="mixed")
+    assert torch.equal(g1, g2)
+    # relative to the sum of absolute terms (Kbar has mixed signs)
+    absref = O.se_hyper_grad(X, 1.1, 0.7, 0.3, np.abs(Kbar))
+    assert np.all(np.abs(g1.cpu().numpy() - ref) <= 1e-12 * np.abs(absref))
+
+
+def test_gp_step_mixed_covariance_end_to_end():
+    X, y, (a, r, s) = cond_problem(1000)
+    ref = O.gp_lml_and_grad(X, y, a, r, s, 0.0)
+    K = gp.se_cov(dev(X), a, r, s, 0.0, precision="mixed")
+    res = gp.gp_lml(K, dev(y), precision="mixed", check=False)
+    assert res["info"].tolist()[1] == gp.GPC_OK
+    assert abs(res["value"].item() - ref["value"]) <= 1e-10 * abs(ref["value"])
+    Kbar = gp.gp_lml_grad(res["L"], res["alpha"], 1.0, precision="mixed")
+    g = gp.se_hyper_grad(dev(X), a, r, s, Kbar, precision="mixed").cpu().numpy()
+    assert rel(g, ref["grad"]) <= 1e-7

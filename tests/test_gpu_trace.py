@@ -1,0 +1,35 @@
+"""Launch trace and timeline (measurement support) through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1907_01063_gb300 as gp
+from paper_1907_01063_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_timeline_lists_every_launch_in_order():
+    n = 300
+    L0 = torch.as_tensor(W.known_factor(n, seed=1), device="cuda")
+    K = L0 @ L0.T
+    torch.cuda.synchronize()
+    c0 = gp.launch_count()
+    gp.trace_enable(True, timeline=True)
+    gp.chol(K)
+    torch.cuda.synchronize()
+    gp.trace_enable(False)
+    spans = gp.trace_timeline()
+    assert len(spans) == gp.launch_count() - c0 > 0
+    names = [s["kernel"] for s in spans]
+    assert names.count("potrf_diag_kernel") == (n + 127) // 128
+    assert all(s["dur_ms"] > 0 for s in spans)
+    starts = [s["start_ms"] for s in spans]
+    assert starts[0] == 0.0 and all(b >= a for a, b in zip(starts, starts[1:]))
+    summary = gp.trace_summary()
+    assert sum(v["launches"] for v in summary.values()) == len(spans)
+    # plain tracing (no timeline) leaves the recorded spans alone
+    gp.trace_enable(True)
+    gp.chol(K)
+    gp.trace_enable(False)
+    assert len(gp.trace_timeline()) == len(spans)
