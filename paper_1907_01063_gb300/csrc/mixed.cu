@@ -34,6 +34,7 @@ struct MixWs {
 };
 
 size_t b2() { return align_up((size_t)MB * MB * sizeof(double), 256); }
+constexpr int kSideSMs = 16;  // SMs left to the caller's stream while the adjoint's Bbar update runs
 
 // Per-device auxiliary stream and events for the factorisation's lookahead.
 struct Aux {
@@ -139,6 +140,15 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
   SliceBuf LT = slice_view(w.lt, n, nblk);
   TRY(split_operand(L, 1, ldl, n, n, first, LT, s));
   TRY(trtri_batched(n, L, ldl, first, MB, w.inv, s));  // independent of the sweep: one launch
+  Aux *aux = nullptr;
+  TRY(aux_for_device(&aux));
+  // Within a step the Bbar update (rows below, columns left: the largest
+  // product) runs on the auxiliary stream on all but kSideSMs SMs while the
+  // caller's stream takes the rest of the Dbar chain (three small FP64
+  // products that fill only a few SMs) on the others; Rbar follows the chain
+  // and takes SMs as the Bbar update frees them, and the next step's Cbar,
+  // which both updates write, waits for both.
+  const int side = std::min(kSideSMs, sm_count() / 4);
   for (int ib = nblk - 1; ib >= 0; --ib) {
     const int j = (ib == 0) ? 0 : first + (ib - 1) * MB;
     const int k = first + ib * MB;
@@ -148,16 +158,11 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
     double *Dbar = A + (long long)j * lda + j;
     const double *dinv = w.inv + (size_t)ib * MB * MB;
     SliceBuf SDC = slice_view(w.sdc, nb, chunks);
+    bool bbar_pending = false;
     if (m > 0) {
       double *Cbar = A + (long long)k * lda + j;
       TRY(from_df_rect(m, nb, Cbar, lda, s));
       TRY(trsm_rows(m, nb, Cbar, lda, D, ldl, 1, s));  // Cbar <- Cbar D^{-1} (FP64)
-      if (j > 0) {  // Bbar -= Cbar R on slices (Bbar in double-float storage)
-        SliceBuf SC = slice_view(w.sc, m, 1);
-        TRY(split_operand(Cbar, lda, 1, m, nb, nb, SC, s));
-        TRY(ozaki_gemm(SC, 0, 0, LT, 0, ib * MB, m, j, 1, false, -1.0f, (float2 *)(A + (long long)k * lda),
-                       lda, 1, nullptr, err, s));
-      }
       // Dbar -= Cbar^T C on slices, Dbar still in double-float storage: the
       // columns of Cbar (K = rows k..n) fill chunks 1.. of the block column's
       // slices; C^T is rows j..k of the L^T slices.
@@ -167,6 +172,16 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
       while (dsplits > 1 && ozaki_partial_bytes(nb, nb, dsplits) > kPartialCap) --dsplits;
       TRY(ozaki_gemm(SDC, 0, MB, LT, j, (ib + 1) * MB, nb, nb, dch, true, -1.0f, (float2 *)Dbar, lda, dsplits,
                      (float2 *)w.scratch, err, s));
+      if (j > 0) {  // Bbar -= Cbar R on slices (Bbar in double-float storage)
+        SliceBuf SC = slice_view(w.sc, m, 1);
+        TRY(split_operand(Cbar, lda, 1, m, nb, nb, SC, s));
+        TRY(cudaEventRecord(aux->ev_split, s));
+        TRY(cudaStreamWaitEvent(aux->st, aux->ev_split, 0));
+        TRY(ozaki_gemm(SC, 0, 0, LT, 0, ib * MB, m, j, 1, false, -1.0f, (float2 *)(A + (long long)k * lda),
+                       lda, 1, nullptr, err, aux->st, sm_count() - side));
+        TRY(cudaEventRecord(aux->ev_rest, aux->st));
+        bbar_pending = true;
+      }
     }
     TRY(from_df_rect(nb, nb, Dbar, lda, s));
     {
@@ -203,6 +218,10 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
                      lda, splits, (float2 *)w.scratch, err, s));
     }
     TRY(phi_block(nb, Dbar, lda, s));
+    if (bbar_pending) {
+      TRY(cudaStreamWaitEvent(s, aux->ev_rest, 0));
+      bbar_pending = false;
+    }
   }
   return cudaSuccess;
 }
