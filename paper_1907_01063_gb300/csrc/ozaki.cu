@@ -67,7 +67,10 @@ constexpr int OZ_B_STAGE = OZ_S * OZ_B_PLANE;            // 20 KiB
 constexpr int OZ_ACCS = 4;                               // G2, G3, G4, G56
 constexpr int OZ_ACC_COLS = OZ_ACCS * OZ_BN;             // one accumulator set
 constexpr int OZ_TMEM_COLS = 512;
-constexpr int OZ_SMEM_BYTES = OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + 1024 /*barriers*/ + 1024 /*align*/;
+constexpr int OZ_EPI_LD = 17;                           // padded row of an epilogue transpose buffer (float2)
+constexpr int OZ_EPI_BUF = 32 * OZ_EPI_LD * 8;           // 32 rows x 16 columns of double-floats per warp
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + OZ_EPI_WARPS * OZ_EPI_BUF +
+                              1024 /*barriers*/ + 1024 /*align*/;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct OzParams {
@@ -151,16 +154,44 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   d |= (uint64_t)4 << 61;                        // 64B swizzle
   return d;
 }
-// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = OZ_BN.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                            ((uint32_t)(OZ_BM >> 4) << 24);
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+// The 15 slice products of one K = 16 step in 9 MMAs.  The B slice planes
+// lie one after another in shared memory (64 rows each, same swizzle), so
+// planes q..q+c-1 form one operand of N = 64 c rows, and a_p times that
+// operand writes the products a_p b_q .. a_p b_{q+c-1} into consecutive
+// 64-column accumulators.  With the accumulators G2 | G3 | G4 | G56 at
+// columns 0, 64, 128, 192 of a set, a_p b_1.. lands in the group p + q
+// wherever p + q <= 4, and every product with p + q in {5, 6} goes to G56:
+//   a1 [b1 b2 b3 b4] -> G2 G3 G4 G56   a1 b5 -> G56
+//   a2 [b1 b2 b3]    -> G3 G4 G56      a2 b4 -> G56
+//   a3 [b1 b2]       -> G4 G56         a3 b3 -> G56
+//   a4 b1, a4 b2, a5 b1                -> G56
+// The first MMA of a chunk (first == 0) overwrites all four accumulators.
+__device__ __forceinline__ void ozaki_kstep(uint32_t tacc, uint32_t ka, uint32_t kb, uint32_t first) {
+  constexpr uint32_t n64 = idesc_n(64), n128 = idesc_n(128), n192 = idesc_n(192), n256 = idesc_n(256);
+  const uint32_t g56 = tacc + 3 * OZ_BN;
+  mma_bf16(tacc, sdesc(ka), sdesc(kb), n256, first);
+  mma_bf16(g56, sdesc(ka), sdesc(kb + 4 * OZ_B_PLANE), n64, 1u);
+  mma_bf16(tacc + OZ_BN, sdesc(ka + OZ_A_PLANE), sdesc(kb), n192, 1u);
+  mma_bf16(g56, sdesc(ka + OZ_A_PLANE), sdesc(kb + 3 * OZ_B_PLANE), n64, 1u);
+  mma_bf16(tacc + 2 * OZ_BN, sdesc(ka + 2 * OZ_A_PLANE), sdesc(kb), n128, 1u);
+  mma_bf16(g56, sdesc(ka + 2 * OZ_A_PLANE), sdesc(kb + 2 * OZ_B_PLANE), n64, 1u);
+  mma_bf16(g56, sdesc(ka + 3 * OZ_A_PLANE), sdesc(kb), n64, 1u);
+  mma_bf16(g56, sdesc(ka + 3 * OZ_A_PLANE), sdesc(kb + OZ_B_PLANE), n64, 1u);
+  mma_bf16(g56, sdesc(ka + 4 * OZ_A_PLANE), sdesc(kb), n64, 1u);
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -262,7 +293,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *sA = smem;
   unsigned char *sB = smem + OZ_STAGES * OZ_A_STAGE;
-  uint64_t *bars = (uint64_t *)(sB + OZ_STAGES * OZ_B_STAGE);
+  float2 *epi_buf = (float2 *)(sB + OZ_STAGES * OZ_B_STAGE);
+  uint64_t *bars = (uint64_t *)((unsigned char *)epi_buf + OZ_EPI_WARPS * OZ_EPI_BUF);
   // bars: full[3], empty[3], tfull[2], tempty[2], drain
   volatile int *abort_flag = (volatile int *)(bars + 16);
   uint32_t *tmem_slot = (uint32_t *)(bars + 17);
@@ -354,29 +386,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             const uint32_t a0 = smem_u32(sA + stage * OZ_A_STAGE);
             const uint32_t b0 = smem_u32(sB + stage * OZ_B_STAGE);
 #pragma unroll
-            for (int k = 0; k < OZ_BK / 16; ++k) {
-              const uint32_t first = (h == 0 && k == 0) ? 0u : 1u;
-              const uint32_t ka = a0 + k * 32, kb = b0 + k * 32;
-#define OZ_MMA(P, Q, ACC, FIRST)                                                               \
-  mma_bf16(tacc + (ACC) * OZ_BN, sdesc(ka + (P) * OZ_A_PLANE), sdesc(kb + (Q) * OZ_B_PLANE), \
-           (FIRST) ? first : 1u)
-              OZ_MMA(0, 0, 0, 1);  // G2  (0-based slice indices)
-              OZ_MMA(0, 1, 1, 1);  // G3
-              OZ_MMA(1, 0, 1, 0);
-              OZ_MMA(0, 2, 2, 1);  // G4
-              OZ_MMA(1, 1, 2, 0);
-              OZ_MMA(2, 0, 2, 0);
-              OZ_MMA(0, 3, 3, 1);  // G56
-              OZ_MMA(1, 2, 3, 0);
-              OZ_MMA(2, 1, 3, 0);
-              OZ_MMA(3, 0, 3, 0);
-              OZ_MMA(0, 4, 3, 0);
-              OZ_MMA(1, 3, 3, 0);
-              OZ_MMA(2, 2, 3, 0);
-              OZ_MMA(3, 1, 3, 0);
-              OZ_MMA(4, 0, 3, 0);
-#undef OZ_MMA
-            }
+            for (int k = 0; k < OZ_BK / 16; ++k)
+              ozaki_kstep(tacc, a0 + k * 32, b0 + k * 32, (h == 0 && k == 0) ? 0u : 1u);
             mma_commit(empty0 + 8 * stage);
             any = true;
             if (++stage == OZ_STAGES) { stage = 0; phase ^= 1; }
@@ -398,7 +409,13 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     }
   } else {
     // ---------------- epilogue: warps 2..9; lane quarter = warp % 4, column half by warp pair
+    // Each warp owns a 32 x 32 block of the output: thread r holds row r's 32
+    // columns (the TMEM lane layout).  C moves between global memory and the
+    // registers through a padded shared-memory buffer, 16 columns at a time,
+    // so that every global access of the warp covers two 128-byte row pieces.
     const int q = warp & 3, half = (warp - 2) >> 2;
+    float2 *tb = epi_buf + (size_t)(warp - 2) * (OZ_EPI_BUF / 8);
+    const int rl_lo = lane >> 4, cl = lane & 15;
     int buf = 0;
     uint32_t tphase = 0;
     bool ok = true;
@@ -406,17 +423,17 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       int tm, tn, c0, c1;
       work_coords(p, w, tm, tn, c0, c1);
       const int split = w % p.splits;
-      const int row = tm * OZ_BM + q * 32 + lane;
-      const bool row_ok = row < p.M;
-      float2 *dst = nullptr;
-      if (row_ok) {
-        if (p.partial) dst = p.partial + ((size_t)split * p.M + row) * (size_t)p.N;
-        else dst = p.C + (long long)row * p.ldc;
-      }
+      const int row0 = tm * OZ_BM + q * 32;
       const int colh = tn * OZ_BN + half * 32;
-      // vector path: the 32 columns of this thread are in range, 16-byte aligned, and not cut by the diagonal
-      const bool vec = row_ok && colh + 32 <= p.N && (((uintptr_t)(dst + colh)) & 15) == 0 &&
-                       !(p.lower && colh + 31 > row);
+      float2 *base;
+      long long ld;
+      if (p.partial) {
+        base = p.partial + (size_t)split * p.M * (size_t)p.N;
+        ld = p.N;
+      } else {
+        base = p.C;
+        ld = p.ldc;
+      }
       // the double-float sum of this work item stays in registers across its
       // chunks: C is read once before the first chunk and written once after the last
       // (a split-K partial tile starts from zero and is written whole, so it is not read)
@@ -425,20 +442,23 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
         for (int i = 0; i < 32; ++i) cv[i] = make_float2(0.f, 0.f);
       } else {
-        if (vec) {
-          const float4 *src = (const float4 *)(dst + colh);
+        // all 32 loads in flight at once (cv holds them in the coalesced layout first)
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const float4 t = src[u];
-            cv[2 * u] = make_float2(t.x, t.y);
-            cv[2 * u + 1] = make_float2(t.z, t.w);
-          }
-        } else if (row_ok) {
+        for (int hc = 0; hc < 2; ++hc)
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int col = colh + i;
-            cv[i] = (col < p.N && !(p.lower && col > row)) ? dst[col] : make_float2(0.f, 0.f);
+          for (int it = 0; it < 16; ++it) {
+            const int rl = 2 * it + rl_lo, row = row0 + rl, col = colh + hc * 16 + cl;
+            cv[hc * 16 + it] = (row < p.M && col < p.N && !(p.lower && col > row)) ? base[(long long)row * ld + col]
+                                                                                   : make_float2(0.f, 0.f);
           }
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc) {
+#pragma unroll
+          for (int it = 0; it < 16; ++it) tb[(2 * it + rl_lo) * OZ_EPI_LD + cl] = cv[hc * 16 + it];
+          __syncwarp();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) cv[hc * 16 + c] = tb[lane * OZ_EPI_LD + c];
+          __syncwarp();
         }
       }
       for (int c = c0; c < c1; ++c) {
@@ -464,19 +484,22 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         if (++buf == 2) { buf = 0; tphase ^= 1; }
       }
       if (!ok) break;
-      {
-        if (vec) {
-          float4 *out = (float4 *)(dst + colh);
 #pragma unroll
-          for (int u = 0; u < 16; ++u) out[u] = make_float4(cv[2 * u].x, cv[2 * u].y, cv[2 * u + 1].x, cv[2 * u + 1].y);
-        } else if (row_ok) {
+      for (int hc = 0; hc < 2; ++hc) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int col = colh + i;
-            if (col < p.N && !(p.lower && col > row)) dst[col] = cv[i];
-          }
-        }
+        for (int c = 0; c < 16; ++c) tb[lane * OZ_EPI_LD + c] = cv[hc * 16 + c];
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < 16; ++it) cv[hc * 16 + it] = tb[(2 * it + rl_lo) * OZ_EPI_LD + cl];
+        __syncwarp();
       }
+#pragma unroll
+      for (int hc = 0; hc < 2; ++hc)
+#pragma unroll
+        for (int it = 0; it < 16; ++it) {
+          const int rl = 2 * it + rl_lo, row = row0 + rl, col = colh + hc * 16 + cl;
+          if (row < p.M && col < p.N && !(p.lower && col > row)) base[(long long)row * ld + col] = cv[hc * 16 + it];
+        }
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
@@ -711,13 +734,14 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
   p.ldc = ldc;
   p.partial = splits > 1 ? partial : nullptr;
   p.err = err;
-  const int grid = std::min(p.num_work, max_ctas > 0 ? std::min(max_ctas, sm_count()) : sm_count());
+  const int ctas = max_ctas > 0 ? std::min(max_ctas, sm_count()) : sm_count();
   // output entries: the whole M x N block, or its lower part (col <= row)
   const double mn = !lower ? (double)M * N
                            : (M >= N ? 0.5 * (double)N * (N + 1) + (double)(M - N) * N : 0.5 * (double)M * (M + 1));
   const double flops = 2.0 * mn * (double)chunks * OZ_CHUNK * 15.0;  // 15 slice products
-  GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, 16.0 * mn * chunks + (double)(M + N) * chunks * OZ_CHUNK * 2 * OZ_S, s,
-             ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
+  const double bytes = 16.0 * mn * chunks + (double)(M + N) * chunks * OZ_CHUNK * 2 * OZ_S;
+  const int grid = std::min(p.num_work, ctas);
+  GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, bytes, s, ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const long long total = (long long)M * N;
