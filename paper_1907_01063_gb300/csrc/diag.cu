@@ -106,25 +106,55 @@ trtri_batched_kernel(int n, const double *L, long long ldl, int first, int b, do
                    nullptr, 0, 0);
 }
 
+// 1/x and 1/sqrt(x) for normal positive x: the hardware's approximations
+// refined by two Newton-Raphson steps, y <- y (2 - x y) and
+// y <- y (3 - x y^2) / 2 (each step doubles the correct bits; the result is
+// within a few ulp).  FP64 instructions are scarce on this part, so this short
+// dependent chain is what the diagonal factorisation's serial part waits on.
+__device__ __forceinline__ double recip_nr(double x) {
+  if (!(x >= 2.2250738585072014e-308)) return 1.0 / x;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x >= 2.2250738585072014e-308)) return 1.0 / sqrt(x);
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double hx = 0.5 * x;
+  y = y * fma(-hx, y * y, 1.5);
+  return y * fma(-hx, y * y, 1.5);
+}
+
 // Cholesky factor of one nb x nb diagonal block in shared memory (the small-
 // block step of Section 3.3), blocked right-looking with panels of PF_PW
-// columns.  Per panel: warp 0 factors the PF_PW x PF_PW diagonal sub-block
-// column by column (pivot, one reciprocal, scaled column, rank-1 update);
-// one thread per row below solves that row against the sub-block and also
-// writes it, transposed, into a panel buffer; then every thread updates 4 x 4
-// tiles of the trailing lower triangle from the panel buffer (row and column
-// quadruples read as contiguous pairs, so the loads are conflict-free).  The
-// FP64 pipe of one SM bounds it: about nb^3/6 fused multiply-adds.  Writes L11
-// in place with the upper part of the block zeroed; the first failing pivot is
-// recorded in info (GPC_ERR_NOT_PD, or GPC_ERR_NAN for NaN/Inf) and the rest of
-// the block is written back unfinished.  No inverse is formed: the panel below
-// is solved by substitution (trsm_rows_kernel).
+// columns.  Per panel:
+//  1. the PF_PW x PF_PW diagonal sub-block by Schur-complement updates
+//     without square roots (a_ik -= a_ij a_kj / a_jj), one thread per
+//     element, one barrier per column; the thread that owns the next pivot
+//     forms its reciprocal right after its own update.  Column k is then
+//     scaled by 1/sqrt(a_kk) (L = L' D^{1/2}).
+//  2. one thread per row below solves that row against the sub-block,
+//     column by column with the later columns' updates independent, and
+//     writes it, transposed, into a panel buffer;
+//  3. every thread updates 4 x 4 tiles of the trailing lower triangle from
+//     the panel buffer (row and column quadruples read as contiguous pairs).
+// The FP64 pipe of one SM bounds step 3 (about nb^3/6 fused multiply-adds);
+// steps 1 and 2 are short dependent chains.  Writes L11 in place with the
+// upper part of the block zeroed; the first failing pivot is recorded in info
+// (GPC_ERR_NOT_PD, or GPC_ERR_NAN for NaN/Inf) and the rest of the block is
+// written back unfinished.  No inverse is formed: the panel below is solved
+// by substitution (trsm_rows_kernel).
 constexpr int PF_PW = 16;
+static_assert(PF_PW * PF_PW == DIAG_THREADS, "one thread per sub-block element");
 __global__ void __launch_bounds__(DIAG_THREADS)
 potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset) {
-  extern __shared__ double smem[];                       // nb x (nb + 1)
+  extern __shared__ double smem[];                            // nb x (nb + 1)
   __shared__ __align__(16) double pt[PF_PW][kMaxBlock + 4];  // panel rows below, transposed
-  __shared__ double rdiag[PF_PW];
+  __shared__ double rdiag[PF_PW], pinv[PF_PW];
   __shared__ int fail;
   const int ld = nb + 1;
   if (threadIdx.x == 0) fail = 0;
@@ -133,42 +163,41 @@ potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset)
     S(smem, ld, i, j) = (j <= i) ? A[(long long)i * lda + j] : 0.0;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int si = threadIdx.x / PF_PW, sk = threadIdx.x % PF_PW;  // sub-block element of this thread
   for (int p0 = 0; p0 < nb; p0 += PF_PW) {
     const int pw = min(PF_PW, nb - p0), m0 = p0 + pw;
-    // 1. diagonal sub-block, warp 0: lane l owns row jj + 1 + l of the sub-block
-    if (warp == 0) {
-      for (int j = 0; j < pw; ++j) {
-        const int jj = p0 + j;
-        const double pv = S(smem, ld, jj, jj);
-        if (!(pv > 0.0 && pv <= 1.79769313486231570e308)) {
-          if (lane == 0) {
-            fail = 1;
-            if (info && info[1] == 0) {
-              info[0] = pivot_offset + jj;
-              info[1] = (pv != pv || pv > 1.79769313486231570e308) ? GPC_ERR_NAN : GPC_ERR_NOT_PD;
-            }
-          }
-          break;
+    const bool mine = si < pw && sk <= si;
+    // 1. diagonal sub-block
+    auto pivot = [&](int j) {  // by the owner of (j, j), after its last update
+      const double pv = S(smem, ld, p0 + j, p0 + j);
+      if (!(pv > 0.0 && pv <= 1.79769313486231570e308)) {
+        fail = 1;
+        if (info && info[1] == 0) {
+          info[0] = pivot_offset + p0 + j;
+          info[1] = (pv != pv || pv > 1.79769313486231570e308) ? GPC_ERR_NAN : GPC_ERR_NOT_PD;
         }
-        const double d = sqrt(pv), r = 1.0 / d;
-        const int i = jj + 1 + lane;
-        double lij = 0.0;
-        if (i < m0) lij = S(smem, ld, i, jj) * r;
-        __syncwarp();
-        if (lane == 0) {
-          S(smem, ld, jj, jj) = d;
-          rdiag[j] = r;
-        }
-        if (i < m0) S(smem, ld, i, jj) = lij;
-        __syncwarp();
-        if (i < m0)
-          for (int k = jj + 1; k <= i; ++k) S(smem, ld, i, k) = fma(-lij, S(smem, ld, k, jj), S(smem, ld, i, k));
-        __syncwarp();
+      } else {
+        pinv[j] = recip_nr(pv);
       }
+    };
+    if (threadIdx.x == 0) pivot(0);
+    __syncthreads();
+    for (int j = 0; j < pw && !fail; ++j) {
+      if (mine && sk > j) {
+        const double t = S(smem, ld, p0 + si, p0 + j) * pinv[j];
+        S(smem, ld, p0 + si, p0 + sk) = fma(-t, S(smem, ld, p0 + sk, p0 + j), S(smem, ld, p0 + si, p0 + sk));
+        if (si == j + 1 && sk == j + 1) pivot(j + 1);
+      }
+      __syncthreads();
+    }
+    if (fail) break;
+    if (mine && si == sk) rdiag[sk] = rsqrt_nr(S(smem, ld, p0 + sk, p0 + sk));
+    __syncthreads();
+    if (mine) {
+      double &e = S(smem, ld, p0 + si, p0 + sk);
+      e *= rdiag[sk];  // on the diagonal: a_kk / sqrt(a_kk) = sqrt(a_kk)
     }
     __syncthreads();
-    if (fail) break;
     // 2. rows below the sub-block: x = a L_pp^{-T} by forward substitution
     for (int i = m0 + threadIdx.x; i < nb; i += blockDim.x) {
       double x[PF_PW];
@@ -177,10 +206,10 @@ potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset)
 #pragma unroll
       for (int j = 0; j < PF_PW; ++j) {
         if (j < pw) {
-          double v = x[j];
+          x[j] *= rdiag[j];
 #pragma unroll
-          for (int k = 0; k < j; ++k) v = fma(-x[k], S(smem, ld, p0 + j, p0 + k), v);
-          x[j] = v * rdiag[j];
+          for (int t = j + 1; t < PF_PW; ++t)
+            if (t < pw) x[t] = fma(-x[j], S(smem, ld, p0 + t, p0 + j), x[t]);
         }
       }
 #pragma unroll
