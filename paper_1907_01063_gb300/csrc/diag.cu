@@ -270,33 +270,46 @@ potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset)
 // a product with the inverse):
 //   mode 0: X <- X T^{-T}  (forward panel L21 = A21 L11^{-T}; columns ascending)
 //   mode 1: X <- X T^{-1}  (adjoint panel Cbar D^{-1}; columns descending)
-// One CTA per 32 rows, the rows in shared memory; T is read through L1.
-constexpr int TR_ROWS = 32;
+// One CTA per ROWS rows, the rows in shared memory; T is read through L1.
+// Thread (r, g) owns the columns k = g (mod 256 / ROWS) of row r; the owner of
+// the next column scales it right after its last update, so one barrier per
+// column suffices.  Fewer rows per CTA for short panels keep every SM busy.
+template <int ROWS>
 __global__ void __launch_bounds__(256)
 trsm_rows_kernel(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode) {
-  __shared__ double xs[TR_ROWS][kMaxBlock + 1];
+  constexpr int CG = 256 / ROWS;
+  __shared__ double xs[ROWS][kMaxBlock + 1];
   __shared__ double rdiag[kMaxBlock];
-  const int r0 = blockIdx.x * TR_ROWS, rows = min(TR_ROWS, m - r0);
-  for (int idx = threadIdx.x; idx < TR_ROWS * nb; idx += blockDim.x) {
+  const int r0 = blockIdx.x * ROWS, rows = min(ROWS, m - r0);
+  for (int idx = threadIdx.x; idx < ROWS * nb; idx += blockDim.x) {
     const int r = idx / nb, c = idx - r * nb;
     xs[r][c] = (r < rows) ? X[(long long)(r0 + r) * ldx + c] : 0.0;
   }
   for (int j = threadIdx.x; j < nb; j += blockDim.x) rdiag[j] = 1.0 / __ldg(&T[(long long)j * ldt + j]);
   __syncthreads();
-  const int r = threadIdx.x & (TR_ROWS - 1), cg = threadIdx.x >> 5;  // 8 column groups
+  const int r = threadIdx.x % ROWS, cg = threadIdx.x / ROWS;
+  const int jfirst = mode == 0 ? 0 : nb - 1;
+  if (cg == jfirst % CG) xs[r][jfirst] *= rdiag[jfirst];
+  __syncthreads();
   for (int step = 0; step < nb; ++step) {
     const int j = mode == 0 ? step : nb - 1 - step;
-    if (threadIdx.x < TR_ROWS) xs[r][j] *= rdiag[j];
-    __syncthreads();
     const double xj = xs[r][j];
     if (mode == 0) {
-      for (int k = j + 1 + cg; k < nb; k += 8) xs[r][k] = fma(-xj, __ldg(&T[(long long)k * ldt + j]), xs[r][k]);
+      int k = j + 1 + ((cg - (j + 1)) % CG + CG) % CG;
+      if (k == j + 1 && k < nb) {  // the next column: last update, then scale
+        xs[r][k] = fma(-xj, __ldg(&T[(long long)k * ldt + j]), xs[r][k]) * rdiag[k];
+        k += CG;
+      }
+      for (; k < nb; k += CG) xs[r][k] = fma(-xj, __ldg(&T[(long long)k * ldt + j]), xs[r][k]);
     } else {
-      for (int k = cg; k < j; k += 8) xs[r][k] = fma(-xj, __ldg(&T[(long long)j * ldt + k]), xs[r][k]);
+      const int kl = j - 1;
+      for (int k = cg; k < kl; k += CG) xs[r][k] = fma(-xj, __ldg(&T[(long long)j * ldt + k]), xs[r][k]);
+      if (kl >= 0 && kl % CG == cg)
+        xs[r][kl] = fma(-xj, __ldg(&T[(long long)j * ldt + kl]), xs[r][kl]) * rdiag[kl];
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < TR_ROWS * nb; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < ROWS * nb; idx += blockDim.x) {
     const int rr = idx / nb, c = idx - rr * nb;
     if (rr < rows) X[(long long)(r0 + rr) * ldx + c] = xs[rr][c];
   }
@@ -418,8 +431,18 @@ cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, 
                       cudaStream_t s) {
   if (m <= 0 || nb <= 0) return cudaSuccess;
   if (nb > kMaxBlock) return cudaErrorInvalidValue;
-  GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
-             trsm_rows_kernel<<<(m + TR_ROWS - 1) / TR_ROWS, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
+  // 32 rows per CTA when that still gives two CTAs per SM, else 16 or 8
+  const int sms = sm_count();
+  if ((m + 31) / 32 >= 2 * sms) {
+    GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
+               trsm_rows_kernel<32><<<(m + 31) / 32, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
+  } else if ((m + 15) / 16 >= sms) {
+    GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
+               trsm_rows_kernel<16><<<(m + 15) / 16, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
+  } else {
+    GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
+               trsm_rows_kernel<8><<<(m + 7) / 8, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
+  }
   return cudaGetLastError();
 }
 
