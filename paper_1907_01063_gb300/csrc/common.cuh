@@ -149,7 +149,7 @@ SliceBuf slice_view(void *base, int rows, int kchunks);
 cudaError_t split_operand(const double *src, long long rs, long long ks, int M, int K, int first,
                           const SliceBuf &out, cudaStream_t s, int chunk_offset = 0);
 size_t ozaki_partial_bytes(int M, int N, int splits);
-// C (double-float storage, ld in 8-byte elements) += alpha * A[a_row0 + i, a_k0 + k] B[b_row0 + j, b_k0 + k]
+// C (double-float storage, ld in 8-byte elements) += alpha * A[a_row0 + i, a_k0 + k] B[b_row0 + j, b_k0 + k], alpha = +1 or -1
 // over `chunks` K chunks; lower: only col <= row (M == N).  splits > 1 sums
 // K ranges through `partial` (ozaki_partial_bytes) in fixed order.
 // lower with M != N keeps the entries with (local) col <= row.  max_ctas > 0

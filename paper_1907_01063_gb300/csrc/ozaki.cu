@@ -230,31 +230,26 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   const float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
-__device__ __forceinline__ float2 df_add3(float2 c, float x, float y, float z) {
-  float s = c.x, e = c.y, t;
-  two_sum(s, x, s, t);
-  e = __fadd_rn(e, t);
-  two_sum(s, y, s, t);
-  e = __fadd_rn(e, t);
-  two_sum(s, z, s, t);
-  e = __fadd_rn(e, t);
+// c += (g2 + g3 + g4 + g5) for one chunk's four slice groups (decreasing
+// scale: each about 2^-8 of the one before): g2, g3 and g4 enter the high part
+// through exact two-sums, their errors and the rounded G56 group (whose own
+// rounding sits near 2^-48 of g2) are added to the low part, then the pair is
+// renormalised.  NEG subtracts instead (the negations fold into the adds).
+template <bool NEG>
+__device__ __forceinline__ float2 df_acc(float2 c, float g2, float g3, float g4, float g5) {
+  if (NEG) {
+    g2 = -g2;
+    g3 = -g3;
+    g4 = -g4;
+    g5 = -g5;
+  }
+  float s, e1, e2, e3;
+  two_sum(c.x, g2, s, e1);
+  two_sum(s, g3, s, e2);
+  two_sum(s, g4, s, e3);
+  const float e = __fadd_rn(__fadd_rn(__fadd_rn(c.y, g5), __fadd_rn(e1, e2)), e3);
   const float hi = __fadd_rn(s, e);
-  const float lo = __fsub_rn(e, __fsub_rn(hi, s));
-  return make_float2(hi, lo);
-}
-__device__ __forceinline__ float2 df_add4(float2 c, float x, float y, float z, float w) {
-  float s = c.x, e = c.y, t;
-  two_sum(s, x, s, t);
-  e = __fadd_rn(e, t);
-  two_sum(s, y, s, t);
-  e = __fadd_rn(e, t);
-  two_sum(s, z, s, t);
-  e = __fadd_rn(e, t);
-  two_sum(s, w, s, t);
-  e = __fadd_rn(e, t);
-  const float hi = __fadd_rn(s, e);
-  const float lo = __fsub_rn(e, __fsub_rn(hi, s));
-  return make_float2(hi, lo);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   float s, t;
@@ -287,6 +282,7 @@ __device__ __forceinline__ void work_coords(const OzParams &p, int w, int &tm, i
 }
 
 // ------------------------------------------------------------------ the GEMM
+template <bool NEG>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -474,9 +470,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           tmem_ld16(tacc + 3 * OZ_BN + cb * 16, g5);
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            cv[cb * 16 + i] = df_add4(cv[cb * 16 + i], p.alpha * g2[i], p.alpha * g3[i], p.alpha * g4[i],
-                                      p.alpha * g5[i]);
+          for (int i = 0; i < 16; ++i) cv[cb * 16 + i] = df_acc<NEG>(cv[cb * 16 + i], g2[i], g3[i], g4[i], g5[i]);
         }
         fence_before();
         __syncwarp();
@@ -700,12 +694,15 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
                        int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
                        int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas) {
   if (M <= 0 || N <= 0 || chunks <= 0) return cudaSuccess;
+  if (alpha != 1.0f && alpha != -1.0f) return cudaErrorInvalidValue;  // the epilogue applies a sign only
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, OZ_BM) || !make_map(&mb, B, OZ_BN)) return cudaErrorInvalidValue;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !g_oz_attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ozaki_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
     if (e != cudaSuccess) return e;
     g_oz_attr[dev] = true;
   }
@@ -741,7 +738,12 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
   const double flops = 2.0 * mn * (double)chunks * OZ_CHUNK * 15.0;  // 15 slice products
   const double bytes = 16.0 * mn * chunks + (double)(M + N) * chunks * OZ_CHUNK * 2 * OZ_S;
   const int grid = std::min(p.num_work, ctas);
-  GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, bytes, s, ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
+  if (alpha < 0.0f)
+    GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, bytes, s,
+               ozaki_gemm_kernel<true><<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
+  else
+    GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, bytes, s,
+               ozaki_gemm_kernel<false><<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const long long total = (long long)M * N;
