@@ -251,7 +251,8 @@ int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *
  * summed algorithmic flops and bytes (host pointers).
  * gpc_trace_timeline synchronises and copies up to max spans, in launch
  * order, into caller host arrays: class, kernel-name id, stream handle,
- * start (ms after the first traced launch began) and device duration (ms);
+ * start (ms after the first traced launch began), device duration (ms) and
+ * the launch's algorithmic flops;
  * *count receives the number of spans held (at most 2^21).  gpc_trace_name
  * writes the NUL-terminated kernel name of a name id into buf (truncated to
  * buf_bytes - 1 characters).  Not thread-safe; meant for benchmarks.
@@ -281,7 +282,7 @@ int gpc_fp64_peak(void *ws, size_t ws_bytes, double *gflops, gpc_stream_t stream
 int gpc_trace_enable(int on);
 int gpc_trace_summary(int cls, long long *launches, double *ms, double *flops, double *bytes);
 int gpc_trace_timeline(long long max, int *cls, int *name, unsigned long long *stream, float *start_ms,
-                       float *dur_ms, long long *count);
+                       float *dur_ms, double *flops, long long *count);
 int gpc_trace_name(int name, char *buf, size_t buf_bytes);
 
 #ifdef __cplusplus

@@ -73,7 +73,8 @@ _SIGNATURES = {
                            ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)], _c_int),
     "gpc_trace_timeline": ([ctypes.c_longlong, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                             ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_float),
-                            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_longlong)], _c_int),
+                            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_c_double),
+                            ctypes.POINTER(ctypes.c_longlong)], _c_int),
     "gpc_trace_name": ([_c_int, ctypes.c_char_p, _c_size], _c_int),
 }
 
@@ -233,16 +234,19 @@ def trace_enable(on: bool = True, timeline: bool = False):
 
 
 def trace_timeline() -> list:
-    """Recorded launches in order: class, kernel, stream, start and duration (ms)."""
+    """Recorded launches in order: class, kernel, stream, start and duration (ms), flops."""
     count = ctypes.c_longlong()
-    _check(capi.gpc_trace_timeline(0, None, None, None, None, None, ctypes.byref(count)), "gpc_trace_timeline")
+    _check(capi.gpc_trace_timeline(0, None, None, None, None, None, None, ctypes.byref(count)),
+           "gpc_trace_timeline")
     n = count.value
     cls = (ctypes.c_int * max(n, 1))()
     name = (ctypes.c_int * max(n, 1))()
     stream = (ctypes.c_ulonglong * max(n, 1))()
     start = (ctypes.c_float * max(n, 1))()
     dur = (ctypes.c_float * max(n, 1))()
-    _check(capi.gpc_trace_timeline(n, cls, name, stream, start, dur, ctypes.byref(count)), "gpc_trace_timeline")
+    flops = (ctypes.c_double * max(n, 1))()
+    _check(capi.gpc_trace_timeline(n, cls, name, stream, start, dur, flops, ctypes.byref(count)),
+           "gpc_trace_timeline")
     classes = {v: k for k, v in TRACE_CLASSES.items()}
     names = {}
     buf = ctypes.create_string_buffer(256)
@@ -252,7 +256,7 @@ def trace_timeline() -> list:
             _check(capi.gpc_trace_name(name[i], buf, 256), "gpc_trace_name")
             names[name[i]] = buf.value.decode()
         out.append({"class": classes.get(cls[i], str(cls[i])), "kernel": names[name[i]], "stream": stream[i],
-                    "start_ms": start[i], "dur_ms": dur[i]})
+                    "start_ms": start[i], "dur_ms": dur[i], "flops": flops[i]})
     return out
 
 

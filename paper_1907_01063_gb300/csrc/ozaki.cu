@@ -180,18 +180,22 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 //   a3 [b1 b2]       -> G4 G56         a3 b3 -> G56
 //   a4 b1, a4 b2, a5 b1                -> G56
 // The first MMA of a chunk (first == 0) overwrites all four accumulators.
-__device__ __forceinline__ void ozaki_kstep(uint32_t tacc, uint32_t ka, uint32_t kb, uint32_t first) {
+// da, db: descriptors of the first A and B plane of this K step; a plane
+// further is a fixed increment of the 14-bit address field (shared-memory
+// addresses stay below 2^18, so the field cannot carry into the next one).
+__device__ __forceinline__ void ozaki_kstep(uint32_t tacc, uint64_t da, uint64_t db, uint32_t first) {
   constexpr uint32_t n64 = idesc_n(64), n128 = idesc_n(128), n192 = idesc_n(192), n256 = idesc_n(256);
+  constexpr uint64_t pa = OZ_A_PLANE >> 4, pb = OZ_B_PLANE >> 4;
   const uint32_t g56 = tacc + 3 * OZ_BN;
-  mma_bf16(tacc, sdesc(ka), sdesc(kb), n256, first);
-  mma_bf16(g56, sdesc(ka), sdesc(kb + 4 * OZ_B_PLANE), n64, 1u);
-  mma_bf16(tacc + OZ_BN, sdesc(ka + OZ_A_PLANE), sdesc(kb), n192, 1u);
-  mma_bf16(g56, sdesc(ka + OZ_A_PLANE), sdesc(kb + 3 * OZ_B_PLANE), n64, 1u);
-  mma_bf16(tacc + 2 * OZ_BN, sdesc(ka + 2 * OZ_A_PLANE), sdesc(kb), n128, 1u);
-  mma_bf16(g56, sdesc(ka + 2 * OZ_A_PLANE), sdesc(kb + 2 * OZ_B_PLANE), n64, 1u);
-  mma_bf16(g56, sdesc(ka + 3 * OZ_A_PLANE), sdesc(kb), n64, 1u);
-  mma_bf16(g56, sdesc(ka + 3 * OZ_A_PLANE), sdesc(kb + OZ_B_PLANE), n64, 1u);
-  mma_bf16(g56, sdesc(ka + 4 * OZ_A_PLANE), sdesc(kb), n64, 1u);
+  mma_bf16(tacc, da, db, n256, first);
+  mma_bf16(g56, da, db + 4 * pb, n64, 1u);
+  mma_bf16(tacc + OZ_BN, da + pa, db, n192, 1u);
+  mma_bf16(g56, da + pa, db + 3 * pb, n64, 1u);
+  mma_bf16(tacc + 2 * OZ_BN, da + 2 * pa, db, n128, 1u);
+  mma_bf16(g56, da + 2 * pa, db + 2 * pb, n64, 1u);
+  mma_bf16(g56, da + 3 * pa, db, n64, 1u);
+  mma_bf16(g56, da + 3 * pa, db + pb, n64, 1u);
+  mma_bf16(g56, da + 4 * pa, db, n64, 1u);
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -379,11 +383,11 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           for (int h = 0; h < OZ_QPC && ok; ++h) {
             if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
             fence_after();
-            const uint32_t a0 = smem_u32(sA + stage * OZ_A_STAGE);
-            const uint32_t b0 = smem_u32(sB + stage * OZ_B_STAGE);
+            const uint64_t da = sdesc(smem_u32(sA + stage * OZ_A_STAGE));
+            const uint64_t db = sdesc(smem_u32(sB + stage * OZ_B_STAGE));
 #pragma unroll
-            for (int k = 0; k < OZ_BK / 16; ++k)
-              ozaki_kstep(tacc, a0 + k * 32, b0 + k * 32, (h == 0 && k == 0) ? 0u : 1u);
+            for (int k = 0; k < OZ_BK / 16; ++k)  // 16 BF16 = 32 bytes = 2 address units
+              ozaki_kstep(tacc, da + 2 * k, db + 2 * k, (h == 0 && k == 0) ? 0u : 1u);
             mma_commit(empty0 + 8 * stage);
             any = true;
             if (++stage == OZ_STAGES) { stage = 0; phase ^= 1; }

@@ -24,6 +24,7 @@ struct Span {
   int cls, name;
   unsigned long long stream;
   float start_ms, dur_ms;
+  double flops;
 };
 
 constexpr size_t kMaxSpans = 1u << 21;
@@ -86,7 +87,7 @@ void drain(TraceState &t, bool block) {
     if (t.timeline && r.e0 && t.spans.size() < kMaxSpans) {
       float start = 0.f;
       if (t.base) cudaEventElapsedTime(&start, t.base, r.e0);
-      t.spans.push_back(Span{r.cls, r.name, (unsigned long long)(uintptr_t)r.stream, start, ms});
+      t.spans.push_back(Span{r.cls, r.name, (unsigned long long)(uintptr_t)r.stream, start, ms, r.flops});
     }
     if (r.e0 && r.e0 != t.base) t.pool.push_back(r.e0);
     if (r.e1) t.pool.push_back(r.e1);
@@ -230,8 +231,8 @@ int gpc_trace_enable(int on) {
 }
 
 int gpc_trace_timeline(long long max, int *cls, int *name, unsigned long long *stream, float *start_ms,
-                       float *dur_ms, long long *count) {
-  if (!count || max < 0 || (max > 0 && (!cls || !name || !stream || !start_ms || !dur_ms)))
+                       float *dur_ms, double *flops, long long *count) {
+  if (!count || max < 0 || (max > 0 && (!cls || !name || !stream || !start_ms || !dur_ms || !flops)))
     return GPC_ERR_INVALID_ARG;
   TraceState &t = st();
   std::lock_guard<std::mutex> g(t.mu);
@@ -245,6 +246,7 @@ int gpc_trace_timeline(long long max, int *cls, int *name, unsigned long long *s
     stream[i] = sp.stream;
     start_ms[i] = sp.start_ms;
     dur_ms[i] = sp.dur_ms;
+    flops[i] = sp.flops;
   }
   return GPC_OK;
 }
