@@ -384,7 +384,6 @@ trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sy
 // Blocks are b rows from the top (the last may be shorter); Dinv_I is at
 // inv + I b^2 with leading dimension equal to the block size.  Same ticket
 // order, ready flags and bounded waits as trsv_kernel.
-constexpr int TIB = 128;
 __device__ __forceinline__ bool wait_flag(const int *flag, int &value) {
   const unsigned long long t0 = clock_ns();
   for (unsigned it = 0;; ++it) {
@@ -396,52 +395,56 @@ __device__ __forceinline__ bool wait_flag(const int *flag, int &value) {
 }
 
 // Latency matters more than bandwidth here: every block waits for the one
-// before it.  So the CTA loads its inverse block into shared memory at start,
-// and the slice of L it multiplies by the next ready block of x is loaded into
-// registers while the CTA waits for that block's flag; once the last flag it
-// needs arrives, only one register-resident product, a shuffle reduction and
-// the product with the shared-memory inverse stand between it and its own flag.
-// The abort word is double-buffered by step parity so that a CTA's thread 0
-// can record a failed wait while slower warps still read the previous step's.
-constexpr int TI_ROWS = TIB / 8;  // rows per warp in the forward solve
-constexpr int TI_KU = TIB / 32;   // columns per lane in the forward solve
-constexpr int TI_RT = TIB / 2;    // rows per thread in the transposed solve
+// before it, and on GB300 each dependent FP64 instruction costs about 64
+// cycles.  So the solve runs on sub-blocks of at most 64 rows (half a
+// factorisation block; the inverse of a diagonal sub-block is the matching
+// diagonal sub-block of the stored block inverse), with 256 threads as 64 rows
+// x 4 column quarters and no cross-lane FP64 reductions: each CTA loads its
+// sub-block inverse into shared memory at start, keeps the next L slice in
+// registers while it waits for the previous sub-block's flag, and after the
+// last flag only a 16-term product per thread, two four-way sums through
+// shared memory and the 16-term product with the inverse remain.  The abort
+// word is double-buffered by step parity so that a CTA's thread 0 can record a
+// failed wait while slower warps still read the previous step's.
+constexpr int TS = 64, TQ = 4, TW = TS / TQ;
 
-__global__ void __launch_bounds__(256, 1)
-trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b, double *x, int trans,
+__global__ void __launch_bounds__(256)
+trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b, int sb, double *x, int trans,
                 int *sync, int *info, const int *skip) {
   if (skip && *skip) return;
-  extern __shared__ double dinv_s[];  // nb x nb inverse of this CTA's diagonal block
+  __shared__ double dinv_s[TS][TS + 1];
   __shared__ int s_order, s_ab[2];
-  __shared__ double vbuf[TIB];
-  __shared__ double xs[TIB];
-  __shared__ double red[2][TIB];
-  const int nblk = (n + b - 1) / b;
+  __shared__ double vbuf[TS], xs[TS];
+  __shared__ double red[TQ][TS];
+  const int nsb = (n + sb - 1) / sb;
   if (threadIdx.x == 0) {
     s_order = atomicAdd(&sync[0], 1);
     s_ab[0] = s_ab[1] = 0;
   }
   __syncthreads();
   const int order = s_order;
-  const int blk = trans ? (nblk - 1 - order) : order;
-  const int i0 = blk * b, nb = min(b, n - i0);
-  const double *Dinv = inv + (size_t)blk * b * b;
-  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) dinv_s[idx] = __ldg(Dinv + idx);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sbk = trans ? (nsb - 1 - order) : order;
+  const int i0 = sbk * sb, nb = min(sb, n - i0);
+  {
+    const int B = i0 / b, off = i0 - B * b, nbB = min(b, n - B * b);
+    const double *Dinv = inv + (size_t)B * b * b + (size_t)off * nbB + off;  // leading dimension nbB
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+      const int rr = idx / nb, kk = idx - rr * nb;
+      dinv_s[rr][kk] = __ldg(Dinv + (size_t)rr * nbB + kk);
+    }
+  }
+  const int r = threadIdx.x % TS, q = threadIdx.x / TS;
   bool aborted = false;
+  double acc = 0.0, lv[TW];
 
   if (!trans) {
-    double acc[TI_ROWS], lv[TI_ROWS][TI_KU];
+    // lv[u] = L[i0 + r][c0 + q TW + u] for the next sub-block c
 #pragma unroll
-    for (int t = 0; t < TI_ROWS; ++t) {
-      acc[t] = 0.0;
-#pragma unroll
-      for (int u = 0; u < TI_KU; ++u) {
-        const int r = warp + 8 * t, k = lane + 32 * u;
-        lv[t][u] = (blk > 0 && r < nb && k < b) ? __ldg(L + (long long)(i0 + r) * ldl + k) : 0.0;
-      }
+    for (int u = 0; u < TW; ++u) {
+      const int k = q * TW + u;
+      lv[u] = (sbk > 0 && r < nb && k < sb) ? __ldg(L + (long long)(i0 + r) * ldl + k) : 0.0;
     }
-    for (int c = 0; c < blk; ++c) {
+    for (int c = 0; c < sbk; ++c) {
       if (threadIdx.x == 0) {
         int f;
         if (!wait_flag(&sync[1 + c], f) || f != 1) s_ab[c & 1] = 1;
@@ -452,67 +455,54 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
         aborted = true;
         break;
       }
-      const int c0 = c * b;  // c < blk: a full block
-      double xq[TI_KU];
+      const int c0 = c * sb;  // c < sbk: a full sub-block
+      double p[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int u = 0; u < TI_KU; ++u) xq[u] = (lane + 32 * u < b) ? __ldcg(&x[c0 + lane + 32 * u]) : 0.0;
-#pragma unroll
-      for (int t = 0; t < TI_ROWS; ++t)
-#pragma unroll
-        for (int u = 0; u < TI_KU; ++u) acc[t] = fma(lv[t][u], xq[u], acc[t]);
-      if (c + 1 < blk) {
-        const int c1 = c0 + b;
-#pragma unroll
-        for (int t = 0; t < TI_ROWS; ++t)
-#pragma unroll
-          for (int u = 0; u < TI_KU; ++u) {
-            const int r = warp + 8 * t, k = lane + 32 * u;
-            lv[t][u] = (r < nb && k < b) ? __ldg(L + (long long)(i0 + r) * ldl + c1 + k) : 0.0;
-          }
+      for (int u = 0; u < TW; ++u) {
+        const int k = q * TW + u;
+        const double xv = (k < sb) ? __ldcg(&x[c0 + k]) : 0.0;
+        p[u & 3] = fma(lv[u], xv, p[u & 3]);
       }
-    }
-    if (!aborted) {
+      acc += (p[0] + p[1]) + (p[2] + p[3]);
+      if (c + 1 < sbk) {
+        const int c1 = c0 + sb;
 #pragma unroll
-      for (int t = 0; t < TI_ROWS; ++t) {
-        double v = acc[t];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        const int r = warp + 8 * t;
-        if (lane == 0 && r < nb) vbuf[r] = x[i0 + r] - v;
-      }
-    }
-    __syncthreads();  // vbuf and dinv_s complete
-    if (!aborted) {
-#pragma unroll
-      for (int t = 0; t < TI_ROWS; ++t) {
-        const int r = warp + 8 * t;
-        if (r < nb) {
-          double v = 0.0;
-#pragma unroll
-          for (int u = 0; u < TI_KU; ++u) {
-            const int k = lane + 32 * u;
-            if (k <= r) v = fma(dinv_s[r * nb + k], vbuf[k], v);
-          }
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) {
-            x[i0 + r] = v;
-            __threadfence();
-          }
+        for (int u = 0; u < TW; ++u) {
+          const int k = q * TW + u;
+          lv[u] = (r < nb && k < sb) ? __ldg(L + (long long)(i0 + r) * ldl + c1 + k) : 0.0;
         }
       }
     }
-  } else {
-    const int i = threadIdx.x & (TIB - 1), rg = threadIdx.x >> 7;
-    double acc = 0.0, lv[TI_RT];
-    {
-      const int c0 = (nblk - 1) * b, cn = n - c0;
+    red[q][r] = acc;
+    __syncthreads();  // red and dinv_s complete
+    if (!aborted && q == 0 && r < nb) vbuf[r] = x[i0 + r] - ((red[0][r] + red[1][r]) + (red[2][r] + red[3][r]));
+    __syncthreads();
+    double p[4] = {0.0, 0.0, 0.0, 0.0};
+    if (!aborted && r < nb) {
 #pragma unroll
-      for (int m = 0; m < TI_RT; ++m) {
-        const int r = rg + 2 * m;
-        lv[m] = (order > 0 && i < nb && r < cn) ? __ldg(L + (long long)(c0 + r) * ldl + i0 + i) : 0.0;
+      for (int u = 0; u < TW; ++u) {
+        const int k = q * TW + u;
+        if (k <= r) p[u & 3] = fma(dinv_s[r][k], vbuf[k], p[u & 3]);
+      }
+    }
+    red[q][r] = (p[0] + p[1]) + (p[2] + p[3]);
+    __syncthreads();
+    if (!aborted && q == 0 && r < nb) {
+      x[i0 + r] = (red[0][r] + red[1][r]) + (red[2][r] + red[3][r]);
+      __threadfence();
+    }
+  } else {
+    // thread (i = r, row quarter q): lv[u] = L[c0 + q TW + u][i0 + i] for the next sub-block c below
+    {
+      const int c0 = (nsb - 1) * sb, cn = n - c0;
+#pragma unroll
+      for (int u = 0; u < TW; ++u) {
+        const int k = q * TW + u;
+        lv[u] = (order > 0 && r < nb && k < cn) ? __ldg(L + (long long)(c0 + k) * ldl + i0 + r) : 0.0;
       }
     }
     for (int step = 0; step < order; ++step) {
-      const int c = nblk - 1 - step;
+      const int c = nsb - 1 - step;
       if (threadIdx.x == 0) {
         int f;
         if (!wait_flag(&sync[1 + c], f) || f != 1) s_ab[step & 1] = 1;
@@ -523,31 +513,38 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
         aborted = true;
         break;
       }
-      const int c0 = c * b, cn = min(b, n - c0);
-      if (threadIdx.x < TIB) xs[threadIdx.x] = threadIdx.x < cn ? __ldcg(&x[c0 + threadIdx.x]) : 0.0;
+      const int c0 = c * sb, cn = min(sb, n - c0);
+      if (threadIdx.x < TS) xs[threadIdx.x] = threadIdx.x < cn ? __ldcg(&x[c0 + threadIdx.x]) : 0.0;
       __syncthreads();
+      double p[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int m = 0; m < TI_RT; ++m) acc = fma(lv[m], xs[rg + 2 * m], acc);
+      for (int u = 0; u < TW; ++u) p[u & 3] = fma(lv[u], xs[q * TW + u], p[u & 3]);
+      acc += (p[0] + p[1]) + (p[2] + p[3]);
       if (step + 1 < order) {
-        const int p0 = c0 - b;  // the next block up is a full block
+        const int p0 = c0 - sb;  // the next sub-block up is a full one
 #pragma unroll
-        for (int m = 0; m < TI_RT; ++m) {
-          const int r = rg + 2 * m;
-          lv[m] = (i < nb && r < b) ? __ldg(L + (long long)(p0 + r) * ldl + i0 + i) : 0.0;
+        for (int u = 0; u < TW; ++u) {
+          const int k = q * TW + u;
+          lv[u] = (r < nb && k < sb) ? __ldg(L + (long long)(p0 + k) * ldl + i0 + r) : 0.0;
         }
       }
     }
-    red[rg][i] = acc;
+    red[q][r] = acc;
     __syncthreads();  // red and dinv_s complete
-    if (!aborted && threadIdx.x < nb) vbuf[threadIdx.x] = x[i0 + threadIdx.x] - (red[0][threadIdx.x] + red[1][threadIdx.x]);
+    if (!aborted && q == 0 && r < nb) vbuf[r] = x[i0 + r] - ((red[0][r] + red[1][r]) + (red[2][r] + red[3][r]));
     __syncthreads();
-    double v = 0.0;
-    if (!aborted && i < nb)
-      for (int k = i + rg; k < nb; k += 2) v = fma(dinv_s[k * nb + i], vbuf[k], v);
-    red[rg][i] = v;
+    double p[4] = {0.0, 0.0, 0.0, 0.0};
+    if (!aborted && r < nb) {
+#pragma unroll
+      for (int u = 0; u < TW; ++u) {
+        const int k = q * TW + u;
+        if (k >= r && k < nb) p[u & 3] = fma(dinv_s[k][r], vbuf[k], p[u & 3]);
+      }
+    }
+    red[q][r] = (p[0] + p[1]) + (p[2] + p[3]);
     __syncthreads();
-    if (!aborted && threadIdx.x < nb) {
-      x[i0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+    if (!aborted && q == 0 && r < nb) {
+      x[i0 + r] = (red[0][r] + red[1][r]) + (red[2][r] + red[3][r]);
       __threadfence();
     }
   }
@@ -555,7 +552,7 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
   if (threadIdx.x == 0) {
     if (aborted && info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
     __threadfence();
-    atomicExch(&sync[1 + blk], aborted ? 2 : 1);
+    atomicExch(&sync[1 + sbk], aborted ? 2 : 1);
   }
 }
 
@@ -705,23 +702,15 @@ cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, vo
 cudaError_t trsv_inv(int n, const double *L, long long ldl, const double *inv, int b, double *x, int trans,
                      void *ws, int *info, cudaStream_t s, const int *skip) {
   if (n <= 0) return cudaSuccess;
-  if (b < 1 || b > TIB) return cudaErrorInvalidValue;
-  const int nblk = (n + b - 1) / b;
+  if (b < 1 || b > 2 * TS) return cudaErrorInvalidValue;
+  const int sb = b > TS ? (b + 1) / 2 : b;  // sub-blocks of at most 64 rows (b is even when > 64)
+  if (sb > TS || (b > TS && 2 * sb != b)) return cudaErrorInvalidValue;
+  const int nsb = (n + sb - 1) / sb;
   int *sync = (int *)ws;
-  cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nblk + 1) * sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nsb + 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  static bool attr_set[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    e = cudaFuncSetAttribute(trsv_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(TIB * TIB * sizeof(double)));
-    if (e != cudaSuccess) return e;
-    attr_set[dev] = true;
-  }
-  const size_t smem = (size_t)b * b * sizeof(double);
   GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n + 2.0 * n * b, 4.0 * (double)n * (n + 1) + 8.0 * n * b, s,
-             trsv_inv_kernel<<<nblk, 256, smem, s>>>(n, L, ldl, inv, b, x, trans ? 1 : 0, sync, info, skip));
+             trsv_inv_kernel<<<nsb, 256, 0, s>>>(n, L, ldl, inv, b, sb, x, trans ? 1 : 0, sync, info, skip));
   return cudaGetLastError();
 }
 
@@ -732,7 +721,9 @@ namespace {
 // 64-row block I: row segments K[i, 0..i] (i in I) and column segments
 // K[j, I] (j > first row of I) cover every stored entry that row block needs,
 // so each lower entry is read twice over the grid and nothing is atomic.
-// partial[block] = sum of r_i^2 over the block.
+// FP64 is throughput- and latency-bound here (n^2 fused multiply-adds, 64
+// cycles per dependent one), so every thread carries four independent partial
+// sums.  partial[block] = sum of r_i^2 over the block.
 constexpr int RB = 64;
 __global__ void __launch_bounds__(256)
 symv_residual_kernel(int n, const double *K, long long ldk, const double *y, const double *x, double *r,
@@ -746,18 +737,37 @@ symv_residual_kernel(int n, const double *K, long long ldk, const double *y, con
   for (int rr = warp; rr < rows; rr += 8) {
     const int i = i0 + rr;
     const double *row = K + (long long)i * ldk;
-    double acc = 0.0;
-    for (int j = lane; j <= i; j += 32) acc = fma(row[j], x[j], acc);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = lane;
+    for (; j + 96 <= i; j += 128) {
+      a0 = fma(row[j], x[j], a0);
+      a1 = fma(row[j + 32], x[j + 32], a1);
+      a2 = fma(row[j + 64], x[j + 64], a2);
+      a3 = fma(row[j + 96], x[j + 96], a3);
+    }
+    for (; j <= i; j += 32) a0 = fma(row[j], x[j], a0);
+    double acc = (a0 + a1) + (a2 + a3);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) part1[rr] = acc;
   }
+  // column segments: thread (c, g) takes rows j = g (mod 4) below the block's diagonal
   const int c = threadIdx.x & (RB - 1), jg = threadIdx.x >> 6;
-  double acc2 = 0.0;
+  double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
   if (c < rows) {
-    for (int j = i0 + 1 + jg; j < n; j += 4)
-      if (j > i0 + c) acc2 = fma(K[(long long)j * ldk + i0 + c], x[j], acc2);
+    const double *col = K + i0 + c;
+    const int jd = min(n, i0 + RB);  // rows inside the diagonal block need j > i0 + c
+    for (int j = i0 + 1 + jg; j < jd; j += 4)
+      if (j > i0 + c) b0 = fma(col[(long long)j * ldk], x[j], b0);
+    int j = jd + jg;
+    for (; j + 12 < n; j += 16) {
+      b0 = fma(col[(long long)j * ldk], x[j], b0);
+      b1 = fma(col[(long long)(j + 4) * ldk], x[j + 4], b1);
+      b2 = fma(col[(long long)(j + 8) * ldk], x[j + 8], b2);
+      b3 = fma(col[(long long)(j + 12) * ldk], x[j + 12], b3);
+    }
+    for (; j < n; j += 4) b0 = fma(col[(long long)j * ldk], x[j], b0);
   }
-  part2[jg][c] = acc2;
+  part2[jg][c] = (b0 + b1) + (b2 + b3);
   __syncthreads();
   double rr2 = 0.0;
   if (threadIdx.x < RB && threadIdx.x < rows) {
