@@ -30,7 +30,7 @@ se_cov_kernel(int n, int d, const double *X, long long ldx, double a2, double in
   for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
     const int r = idx / d, t = idx - r * d;
     xi[idx] = (i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0;
-    xj[idx] = (j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0;
+    xj[t * CT + r] = (j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0;  // dimension-major: no bank conflicts
   }
   __syncthreads();
   const int c = threadIdx.x & (CT - 1);
@@ -44,7 +44,7 @@ se_cov_kernel(int n, int d, const double *X, long long ldx, double a2, double in
     } else {
       double r2 = 0.0;
       for (int t = 0; t < d; ++t) {
-        const double df = xi[r * d + t] - xj[c * d + t];
+        const double df = xi[r * d + t] - xj[t * CT + c];
         r2 = fma(df, df, r2);
       }
       v = a2 * exp(-r2 * inv2r2);
@@ -58,10 +58,13 @@ se_cov_kernel(int n, int d, const double *X, long long ldx, double a2, double in
 // double-float arithmetic (FP32 pairs, about 2^-46 relative per entry; see
 // df.cuh) and one conversion to FP64 per entry.  Entries with
 // r^2 / (2 rho^2) > 80 (below 2^-115 alpha^2) take FP64's exp instead.
+// xi: the row's d coordinates (contiguous); xj: the column's, d apart by CT
+// (the tile's column coordinates are stored dimension-major so that the 32
+// lanes of a warp read 32 consecutive entries)
 __device__ __forceinline__ dfa::df se_r2_df(const dfa::df *xi, const dfa::df *xj, int d) {
   dfa::df r2 = {0.0f, 0.0f};
   for (int t = 0; t < d; ++t) {
-    const dfa::df df_ = dfa::add(xi[t], dfa::neg(xj[t]));
+    const dfa::df df_ = dfa::add(xi[t], dfa::neg(xj[t * CT]));
     r2 = dfa::add_same_sign(r2, dfa::mul(df_, df_));
   }
   return r2;
@@ -78,7 +81,7 @@ se_cov_df_kernel(int n, int d, const double *X, long long ldx, double a2, dfa::d
   for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
     const int r = idx / d, t = idx - r * d;
     xi[idx] = dfa::from_double((i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0);
-    xj[idx] = dfa::from_double((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
+    xj[t * CT + r] = dfa::from_double((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
   }
   __syncthreads();
   const int c = threadIdx.x & (CT - 1);
@@ -90,7 +93,7 @@ se_cov_df_kernel(int n, int d, const double *X, long long ldx, double a2, dfa::d
     if (i == j) {
       v = a2 + diagv;
     } else {
-      const dfa::df t = dfa::mul(se_r2_df(xi + r * d, xj + c * d, d), inv2r2);
+      const dfa::df t = dfa::mul(se_r2_df(xi + r * d, xj + c, d), inv2r2);
       if (t.hi <= 80.0f) {
         int k;
         const dfa::df m = dfa::exp_neg(t, k);
@@ -128,7 +131,7 @@ se_hyper_grad_kernel(int n, int d, const double *X, long long ldx, double alpha,
   for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
     const int r = idx / d, t = idx - r * d;
     xi[idx] = (i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0;
-    xj[idx] = (j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0;
+    xj[t * CT + r] = (j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0;  // dimension-major: no bank conflicts
   }
   __syncthreads();
   const double a2 = alpha * alpha, inv2r2 = 1.0 / (2.0 * rho * rho), inv_r3 = 1.0 / (rho * rho * rho);
@@ -140,7 +143,7 @@ se_hyper_grad_kernel(int n, int d, const double *X, long long ldx, double alpha,
     if (i >= n || j >= n || j > i) continue;
     double r2 = 0.0;
     for (int t = 0; t < d; ++t) {
-      const double df = xi[r * d + t] - xj[c * d + t];
+      const double df = xi[r * d + t] - xj[t * CT + c];
       r2 = fma(df, df, r2);
     }
     const double kf = a2 * exp(-r2 * inv2r2);
@@ -175,7 +178,7 @@ se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alp
   for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
     const int r = idx / d, t = idx - r * d;
     xi[idx] = dfa::from_double((i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0);
-    xj[idx] = dfa::from_double((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
+    xj[t * CT + r] = dfa::from_double((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
   }
   __syncthreads();
   const int c = threadIdx.x & (CT - 1);
@@ -191,7 +194,7 @@ se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alp
       gs = fma(kb, 2.0 * sigma, gs);
       continue;
     }
-    const dfa::df r2 = se_r2_df(xi + r * d, xj + c * d, d);
+    const dfa::df r2 = se_r2_df(xi + r * d, xj + c, d);
     const dfa::df t = dfa::mul(r2, inv2r2);
     if (t.hi <= 80.0f) {
       int k;
