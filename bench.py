@@ -241,16 +241,16 @@ def batched_workload(batch: int, d: int = 4, seed: int = 0, sigma: float = 0.1):
     return [int(v) for v in sizes], np.concatenate(Xs), np.concatenate(ys), hyp
 
 
-def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned):
+def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned, prec):
     import torch
     sizes, X, y, hyp = batched_workload(args.batch)
-    b = gp.Batch(sizes, device=dev)
+    b = gp.Batch(sizes, device=dev, precision=prec)
     Xd = torch.as_tensor(X, device=dev).contiguous()
     yd = torch.as_tensor(y, device=dev).contiguous()
     hd = torch.as_tensor(hyp, device=dev).contiguous()
     if not args.no_autotune:
         from paper_1907_01063_gb300 import autotune
-        tuned["batch_block"] = autotune.tune_batch_block(b, Xd, yd, hd)["best"]
+        tuned[f"batch_block_{prec}"] = autotune.tune_batch_block(b, Xd, yd, hd)["best"]
     nb = gp.get_tuning(gp.GPC_TUNE_BATCH_BLOCK)
     flops = sum(chol_flops(n) + adjoint_flops(n, nb) for n in sizes)
     # one persistent launch per step, captured once in a CUDA graph and replayed
@@ -271,13 +271,14 @@ def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned):
     barrier()
     t_ms = max_over_ranks(e0.elapsed_time(e1))
     info = b.info.cpu().numpy()
-    return {"workload": f"{args.batch} GPs, n_i ~ U{{64..1024}}, d=4, SE kernel, rho_i ~ U(0.2,2), sigma=0.1 (fp64)",
+    return {"workload": f"{args.batch} GPs, n_i ~ U{{64..1024}}, d=4, SE kernel, rho_i ~ U(0.2,2), sigma=0.1 ({prec})",
             "value": world * args.steps * flops / (t_ms / 1e3) / 1e9, "unit": "GFLOP/s",
             "gp_per_s": world * args.steps * args.batch / (t_ms / 1e3), "ms_per_step": t_ms / args.steps,
             "flops_per_step": flops, "sum_n": int(sum(sizes)), "max_n": int(max(sizes)),
             "cuda_graph": True, "kernels_per_step": 2, "block": nb,
             "all_ok": bool((info[:, 1] == 0).all()),
-            "value_checksum": float(b.value.double().sum().item())}
+            "value_checksum": float(b.value.double().sum().item()),
+            "_values": b.value.cpu().numpy()}
 
 
 def main():
@@ -407,7 +408,14 @@ def main():
 
     batched = None
     if not args.no_batched:
-        batched = run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned)
+        batched = {}
+        for bp in precisions:
+            batched[bp] = run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned, bp)
+        vals = {bp: r.pop("_values") for bp, r in batched.items()}
+        if "fp64" in vals and "mixed" in vals:
+            import numpy as np
+            batched["mixed"]["max_rel_value_diff_vs_fp64"] = float(
+                np.max(np.abs(vals["mixed"] - vals["fp64"]) / np.maximum(1.0, np.abs(vals["fp64"]))))
 
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}

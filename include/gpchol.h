@@ -228,9 +228,18 @@ int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes);
  *   hyp[3i..]  (alpha, rho, sigma) of GP i
  *   value[i], grad3[3i..3i+2], info[2i..2i+1]  outputs per GP (info as for
  *              gpc_chol; a GP whose factorisation fails gets NaN outputs)
- * nmax: host int, at most 4096; workspace from gpc_batched_workspace_size.
- * Only precision GPC_FP64 is accepted.  Results do not depend on the order in
- * which thread blocks take GPs.  No counterpart of the API itself is in the paper.
+ * nmax: host int, at most 4096; workspace from gpc_batched_workspace_size
+ * for the same precision (the mixed path needs more: an FP64 copy of each
+ * covariance and a residual vector).
+ * precision GPC_FP64: every step in FP64.  GPC_MIXED: the O(n^3) products
+ * (trailing updates of the factorisation and the adjoint's block products)
+ * run on the tensor cores as split-BF16 slice products with FP32 group sums
+ * folded into double-float accumulators (Section 3.3's blocked algorithms
+ * with the products of Section 3.2 replaced); the diagonal blocks, the
+ * solves and the log determinant stay FP64, and alpha is refined in FP64
+ * against the FP64 covariance (residual K alpha - y) until the residual
+ * stops shrinking.  Results do not depend on the order in which thread blocks
+ * take GPs.  No counterpart of the API itself is in the paper.
  */
 int gpc_batched_workspace_size(int batch, int nmax, int precision, size_t *bytes);
 int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *offK, const long long *rowX, int d,

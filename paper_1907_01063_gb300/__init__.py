@@ -417,10 +417,13 @@ class Batch:
 
     sizes: host sequence of n_i; the covariance/factor of GP i occupies
     n_i^2 doubles of K at offK[i]; its inputs are rows rowX[i] .. of X and y.
+    precision: "fp64" or "mixed"; the workspace is sized for it, and a batch
+    made for "fp64" cannot run the mixed path (its workspace is smaller).
     """
 
-    def __init__(self, sizes, device=None):
+    def __init__(self, sizes, device=None, precision="fp64"):
         device = device if device is not None else "cuda"
+        self.precision = precision
         self.sizes = [int(v) for v in sizes]
         self.batch = len(self.sizes)
         self.nmax = max(self.sizes) if self.sizes else 1
@@ -439,7 +442,8 @@ class Batch:
         self.grad3 = torch.empty(self.batch, 3, dtype=torch.float64, device=device)
         self.info = torch.empty(self.batch, 2, dtype=torch.int32, device=device)
         nbytes = ctypes.c_size_t()
-        _check(capi.gpc_batched_workspace_size(self.batch, self.nmax, GPC_FP64, ctypes.byref(nbytes)),
+        _check(capi.gpc_batched_workspace_size(self.batch, self.nmax, precision_code(precision),
+                                                 ctypes.byref(nbytes)),
                "gpc_batched_workspace_size")
         self.ws = torch.empty(nbytes.value, dtype=torch.uint8, device=device)
 
@@ -451,9 +455,11 @@ class Batch:
 
 
 def batched_gp_lml_grad(batch: Batch, X: torch.Tensor, y: torch.Tensor, hyp: torch.Tensor,
-                        precision="fp64"):
+                        precision=None):
     """Log marginal likelihood and (alpha, rho, sigma) gradient of every GP in
-    the batch in one launch; returns (value [batch], grad3 [batch, 3], info [batch, 2])."""
+    the batch in one launch; returns (value [batch], grad3 [batch, 3], info [batch, 2]).
+    precision defaults to the batch's own."""
+    precision = batch.precision if precision is None else precision
     if not (X.is_cuda and X.dtype == torch.float64 and X.dim() == 2 and X.is_contiguous()):
         raise ValueError("X must be a contiguous float64 CUDA matrix")
     if X.shape[0] != batch.total_rows or y.numel() != batch.total_rows:

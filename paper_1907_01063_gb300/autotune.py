@@ -7,7 +7,7 @@ runs apply them without timing again.
 
 Knobs:
   * batch_block: block size inside the batched per-GP pass (32 or 64), timed
-    on a batch of GPs with the caller's size mix.
+    on a batch of GPs with the caller's size mix, separately per precision.
   * fp64_block: block size of the FP64 blocked factorisation and adjoint
     (64, 96 or 128), timed on chol + adjoint at a stand-in order.
 The mixed path's block is fixed to its 128-wide slice chunk.
@@ -70,8 +70,8 @@ def _time(fn, reps: int = 2) -> float:
 
 
 def tune_batch_block(batch: "gp.Batch", X, y, hyp, force: bool = False) -> dict:
-    """Pick the batched block size for this batch's size mix; applies it."""
-    key = f"{_device_key()}/batch/{batch.batch}x{batch.nmax}/sum{batch.total_rows}"
+    """Pick the batched block size for this batch's size mix and precision; applies it."""
+    key = f"{_device_key()}/batch/{batch.precision}/{batch.batch}x{batch.nmax}/sum{batch.total_rows}"
     db = _load()
     if key in db and not force:
         gp.set_tuning(gp.GPC_TUNE_BATCH_BLOCK, db[key]["best"])
@@ -141,3 +141,5 @@ if __name__ == "__main__":
     y = torch.randn(rows, dtype=torch.float64, device="cuda")
     hyp = torch.tensor([[1.0, 1.0, 0.1]] * len(sizes), dtype=torch.float64)
     print(tune_batch_block(b, X, y, hyp, force=True))
+    bm = gp.Batch(sizes, precision="mixed")
+    print(tune_batch_block(bm, X, y, hyp, force=True))

@@ -288,8 +288,8 @@ int gpc_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, doub
 constexpr int kBatchMaxN = 4096;
 
 int gpc_batched_workspace_size(int batch, int nmax, int precision, size_t *bytes) {
-  if (!bytes || batch < 0 || nmax < 1 || nmax > kBatchMaxN || precision != GPC_FP64) return GPC_ERR_INVALID_ARG;
-  *bytes = batched_workspace_bytes(std::max(batch, 1), nmax);
+  if (!bytes || batch < 0 || nmax < 1 || nmax > kBatchMaxN || !valid_precision(precision)) return GPC_ERR_INVALID_ARG;
+  *bytes = batched_workspace_bytes(std::max(batch, 1), nmax, precision == GPC_MIXED);
   return GPC_OK;
 }
 
@@ -297,14 +297,15 @@ int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *
                             const double *X, const double *y, const double *hyp, int precision, double *Kws,
                             double *value, double *grad3, int *info, void *ws, size_t ws_bytes,
                             gpc_stream_t stream) {
-  if (batch < 0 || nmax < 1 || nmax > kBatchMaxN || d < 1 || d > kMaxDim || precision != GPC_FP64)
+  if (batch < 0 || nmax < 1 || nmax > kBatchMaxN || d < 1 || d > kMaxDim || !valid_precision(precision))
     return GPC_ERR_INVALID_ARG;
   if (batch == 0) return GPC_OK;
+  const bool mixed = precision == GPC_MIXED;
   if (!n || !offK || !rowX || !X || !y || !hyp || !Kws || !value || !grad3 || !info || !ws ||
-      ws_bytes < batched_workspace_bytes(batch, nmax))
+      ws_bytes < batched_workspace_bytes(batch, nmax, mixed))
     return GPC_ERR_INVALID_ARG;
-  return status_of(batched_gp_lml_grad(batch, n, offK, rowX, d, X, y, hyp, Kws, value, grad3, info, nmax, ws,
-                                       stream));
+  return status_of(batched_gp_lml_grad(batch, n, offK, rowX, d, X, y, hyp, Kws, value, grad3, info, nmax, mixed,
+                                       ws, stream));
 }
 
 int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes) {

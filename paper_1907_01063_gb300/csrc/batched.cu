@@ -19,6 +19,9 @@
 // Each GP's factor overwrites its covariance in the caller's Kws; Kbar and the
 // vectors live in a per-CTA slot of the workspace and are reused GP to GP.
 #include "common.cuh"
+#include "slices.cuh"
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
@@ -43,6 +46,9 @@ struct BatchParams {
   int *info;
 };
 
+constexpr int XK = 32;          // K step of the mixed product (one scale per row and step)
+constexpr int XLD = XK + 8;     // padded row of a BF16 slice tile (conflict-free fragment loads)
+
 struct Smem {
   double As[TM][TK + TP];
   double Bs[TM][TK + TP];
@@ -50,6 +56,16 @@ struct Smem {
   double v[MAXB];
   double red[8];
   int flag;
+};
+
+// Extra shared memory of the mixed products: the FP64 operand tiles of one
+// 32-wide K step and their BF16 slices.
+constexpr size_t kSmemXOffset = (sizeof(Smem) + 127) / 128 * 128;
+struct SmemX {
+  double Ax[TM][XK + 1];
+  double Bx[TM][XK + 1];
+  __nv_bfloat16 As[kSlices][TM][XLD];
+  __nv_bfloat16 Bs[kSlices][TM][XLD];
 };
 
 __device__ __forceinline__ void dmma(double (&c)[4], const double (&a)[8], const double (&b)[4]) {
@@ -144,6 +160,144 @@ __device__ void tile_gemm(const double *A, long long lda, const double *B, long 
   __syncthreads();
 }
 
+__device__ __forceinline__ void hmma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+// (hi, lo) += g2 + g3 + g4 + g5 (slice groups in decreasing scale): exact
+// two-sums for the three exact groups, the rounded last group into the low part
+__device__ __forceinline__ void df_acc4(float &hi, float &lo, float g2, float g3, float g4, float g5) {
+  float s, e1, e2, e3;
+  two_sum_f(hi, g2, s, e1);
+  two_sum_f(s, g3, s, e2);
+  two_sum_f(s, g4, s, e3);
+  const float e = __fadd_rn(__fadd_rn(__fadd_rn(lo, g5), __fadd_rn(e1, e2)), e3);
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// The mixed tile product: the same contract as tile_gemm, with the products
+// of each 32-wide K step taken as split-BF16 slices (slices.cuh; one scale per
+// operand row and step) on the warp-level BF16 tensor instruction with FP32
+// accumulation.  Per 16-wide K sub-step and 16 x 8 fragment the 15 slice
+// products with p + q <= 6 go to four FP32 groups (p + q = 2, 3, 4 exact:
+// integer sums below 2^21 in units of their scale; 5-6 rounded), which are
+// added into a double-float accumulator; the tile is converted to FP64 once,
+// when it is written.  No FP64 arithmetic is in the K loop.
+template <bool TA, bool TB>
+__device__ __noinline__ void tile_gemm_mixed(const double *A, long long lda, const double *B, long long ldb, double *C,
+                                long long ldc, int M, int N, int K, double alpha, double beta, bool lower, int m0,
+                                int n0, SmemX &sx) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, tg = lane & 3;
+  float hi[2][4][4], lo[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) hi[i][j][r] = lo[i][j][r] = 0.0f;
+  for (int k0 = 0; k0 < K; k0 += XK) {
+    __syncthreads();
+    // FP64 operand tiles, row-major [m][k] and [n][k]
+    for (int idx = t; idx < TM * XK; idx += BT) {
+      int r, k;
+      if (!TA) { r = idx / XK; k = idx - r * XK; } else { k = idx / TM; r = idx - k * TM; }
+      const int m = m0 + r, kk = k0 + k;
+      sx.Ax[r][k] = (m < M && kk < K) ? (TA ? A[(long long)kk * lda + m] : A[(long long)m * lda + kk]) : 0.0;
+    }
+    for (int idx = t; idx < TM * XK; idx += BT) {
+      int r, k;
+      if (TB) { r = idx / XK; k = idx - r * XK; } else { k = idx / TM; r = idx - k * TM; }
+      const int nn = n0 + r, kk = k0 + k;
+      sx.Bx[r][k] = (nn < N && kk < K) ? (TB ? B[(long long)nn * ldb + kk] : B[(long long)kk * ldb + nn]) : 0.0;
+    }
+    __syncthreads();
+    // slices: thread (row, half) splits 16 values of a row; the pair shares the row's exponent
+    {
+      const int r = t >> 1, h = t & 1;
+#pragma unroll
+      for (int op = 0; op < 2; ++op) {
+        const double *src = op == 0 ? &sx.Ax[r][16 * h] : &sx.Bx[r][16 * h];
+        int ex = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          ex = max(ex, slice_exponent((unsigned long long)__double_as_longlong(src[i])));
+        ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, 1));
+        __nv_bfloat16(*dst)[TM][XLD] = op == 0 ? sx.As : sx.Bs;
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) {
+          float v[kSlices];
+          split_value((unsigned long long)__double_as_longlong(src[i]), ex, v);
+#pragma unroll
+          for (int pp = 0; pp < kSlices; ++pp) dst[pp][r][16 * h + i] = __float2bfloat16_rn(v[pp]);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int kk = 0; kk < XK; kk += 16) {
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int ra = wm * 32 + mi * 16 + g;
+        uint32_t a[kSlices][4];
+#pragma unroll
+        for (int pp = 0; pp < kSlices; ++pp) {
+          a[pp][0] = *(const uint32_t *)&sx.As[pp][ra][kk + 2 * tg];
+          a[pp][1] = *(const uint32_t *)&sx.As[pp][ra + 8][kk + 2 * tg];
+          a[pp][2] = *(const uint32_t *)&sx.As[pp][ra][kk + 2 * tg + 8];
+          a[pp][3] = *(const uint32_t *)&sx.As[pp][ra + 8][kk + 2 * tg + 8];
+        }
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+          const int cb = wn * 32 + ni * 8 + g;
+          uint32_t b[kSlices][2];
+#pragma unroll
+          for (int pp = 0; pp < kSlices; ++pp) {
+            b[pp][0] = *(const uint32_t *)&sx.Bs[pp][cb][kk + 2 * tg];
+            b[pp][1] = *(const uint32_t *)&sx.Bs[pp][cb][kk + 2 * tg + 8];
+          }
+          float gr[4][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) gr[q][r] = 0.0f;
+          // slice pairs (p, q), 0-based, p + q <= 4: group min(p + q, 3)
+#pragma unroll
+          for (int pp = 0; pp < kSlices; ++pp)
+#pragma unroll
+            for (int qq = 0; qq < kSlices; ++qq)
+              if (pp + qq <= 4) hmma_bf16(gr[pp + qq < 3 ? pp + qq : 3], a[pp], b[qq]);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) df_acc4(hi[mi][ni][r], lo[mi][ni][r], gr[0][r], gr[1][r], gr[2][r], gr[3][r]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = m0 + wm * 32 + mi * 16 + g + ((r >> 1) << 3);
+        const int col = n0 + wn * 32 + ni * 8 + 2 * tg + (r & 1);
+        if (row >= M || col >= N || (lower && col > row)) continue;
+        double *dst = C + (long long)row * ldc + col;
+        const double v = alpha * ((double)hi[mi][ni][r] + (double)lo[mi][ni][r]);
+        *dst = (beta == 0.0) ? v : fma(beta, *dst, v);
+      }
+  __syncthreads();
+}
+
 template <bool TA, bool TB>
 __device__ void cta_gemm(const double *A, long long lda, const double *B, long long ldb, double *C, long long ldc,
                          int M, int N, int K, double alpha, double beta, bool lower, Smem &sm) {
@@ -152,6 +306,22 @@ __device__ void cta_gemm(const double *A, long long lda, const double *B, long l
       if (lower && n0 > m0 + TM - 1) break;
       tile_gemm<TA, TB>(A, lda, B, ldb, C, ldc, M, N, K, alpha, beta, lower, m0, n0, sm);
     }
+}
+
+// The O(n^3) products of a GP: split-BF16 tensor products when MIXED.
+template <bool MIXED, bool TA, bool TB>
+__device__ void cta_gemm_big(const double *A, long long lda, const double *B, long long ldb, double *C,
+                             long long ldc, int M, int N, int K, double alpha, double beta, bool lower, Smem &sm,
+                             SmemX *sx) {
+  if constexpr (!MIXED) {
+    cta_gemm<TA, TB>(A, lda, B, ldb, C, ldc, M, N, K, alpha, beta, lower, sm);
+  } else {
+    for (int m0 = 0; m0 < M; m0 += TM)
+      for (int n0 = 0; n0 < N; n0 += TM) {
+        if (lower && n0 > m0 + TM - 1) break;
+        tile_gemm_mixed<TA, TB>(A, lda, B, ldb, C, ldc, M, N, K, alpha, beta, lower, m0, n0, *sx);
+      }
+  }
 }
 
 __device__ double cta_sum(double v, Smem &sm) {
@@ -304,10 +474,41 @@ __device__ void cta_trsv(int n, const double *L, long long ldl, double *x, int t
   __syncthreads();
 }
 
+// r = y - K x for the symmetric K held in its lower triangle (ld n); returns
+// |r|^2 (all threads).  Four partial sums per thread keep FP64 latency hidden.
+__device__ double cta_residual(int n, const double *Kc, const double *y, const double *x, double *r, Smem &sm) {
+  double rr = 0.0;
+  for (int i = threadIdx.x; i < n; i += BT) {
+    const double *row = Kc + (long long)i * n;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = 0;
+    for (; j + 3 <= i; j += 4) {
+      a0 = fma(row[j], x[j], a0);
+      a1 = fma(row[j + 1], x[j + 1], a1);
+      a2 = fma(row[j + 2], x[j + 2], a2);
+      a3 = fma(row[j + 3], x[j + 3], a3);
+    }
+    for (; j <= i; ++j) a0 = fma(row[j], x[j], a0);
+    for (j = i + 1; j + 3 < n; j += 4) {
+      a0 = fma(Kc[(long long)j * n + i], x[j], a0);
+      a1 = fma(Kc[(long long)(j + 1) * n + i], x[j + 1], a1);
+      a2 = fma(Kc[(long long)(j + 2) * n + i], x[j + 2], a2);
+      a3 = fma(Kc[(long long)(j + 3) * n + i], x[j + 3], a3);
+    }
+    for (; j < n; ++j) a0 = fma(Kc[(long long)j * n + i], x[j], a0);
+    const double ri = y[i] - ((a0 + a1) + (a2 + a3));
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+  }
+  return cta_sum(rr, sm);
+}
+
+template <bool MIXED>
 __global__ void __launch_bounds__(BT)
 batched_gp_kernel(BatchParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+  SmemX *sx = MIXED ? reinterpret_cast<SmemX *>(smem_raw + kSmemXOffset) : nullptr;
   __shared__ int s_item;
   double *slot = p.slots + (size_t)blockIdx.x * p.slot_elems;
   const int nb = p.nb;
@@ -340,6 +541,8 @@ batched_gp_kernel(BatchParams p) {
     double *Mw = alpha + p.nmax;         // MAXB^2: sym(tril(D^T Dbar))
     double *Tw = Mw + MAXB * MAXB;       // MAXB^2: M D^{-1}
     double *Dinv = Tw + MAXB * MAXB;     // MAXB^2
+    double *Kc = Dinv + MAXB * MAXB;     // mixed: the covariance kept for refinement (nmax^2)
+    double *rv = Kc + (size_t)p.nmax * p.nmax;  // mixed: residual / correction (nmax)
     if (threadIdx.x == 0) {
       info[0] = -1;
       info[1] = GPC_OK;
@@ -362,6 +565,7 @@ batched_gp_kernel(BatchParams p) {
           v = dg;
         }
         L[idx] = v;
+        if (MIXED) Kc[idx] = v;
       }
     }
     __syncthreads();
@@ -374,7 +578,7 @@ batched_gp_kernel(BatchParams p) {
       if (!ok || m <= 0) continue;
       double *A21 = L + (long long)(k0 + bn) * ld + k0;
       cta_trsm(m, bn, A21, ld, A11, ld, 0, sm);
-      cta_gemm<false, true>(A21, ld, A21, ld, A21 + bn, ld, m, m, bn, -1.0, 1.0, true, sm);
+      cta_gemm_big<MIXED, false, true>(A21, ld, A21, ld, A21 + bn, ld, m, m, bn, -1.0, 1.0, true, sm, sx);
     }
     if (!ok) {
       if (threadIdx.x == 0) {
@@ -391,6 +595,29 @@ batched_gp_kernel(BatchParams p) {
     for (int i = threadIdx.x; i < n; i += BT) alpha[i] = z[i];
     __syncthreads();
     cta_trsv(n, L, ld, alpha, 1, nb, sm);
+    if constexpr (MIXED) {
+      // FP64 refinement against the kept covariance until |r| <= 1e-14 |y| or
+      // the residual stops halving (the FP64 floor); then z = L^T alpha
+      double yy = 0.0;
+      for (int i = threadIdx.x; i < n; i += BT) yy = fma(yg[i], yg[i], yy);
+      yy = cta_sum(yy, sm);
+      double prev = -1.0;
+      for (int it = 0; it < 8; ++it) {
+        const double rr = cta_residual(n, Kc, yg, alpha, rv, sm);
+        if (rr <= 1e-28 * yy || (prev >= 0.0 && rr > 0.25 * prev)) break;
+        prev = rr;
+        cta_trsv(n, L, ld, rv, 0, nb, sm);
+        cta_trsv(n, L, ld, rv, 1, nb, sm);
+        for (int i = threadIdx.x; i < n; i += BT) alpha[i] += rv[i];
+        __syncthreads();
+      }
+      for (int jc = threadIdx.x; jc < n; jc += BT) {
+        double acc = 0.0;
+        for (int i = jc; i < n; ++i) acc = fma(L[(long long)i * ld + jc], alpha[i], acc);
+        z[jc] = acc;
+      }
+      __syncthreads();
+    }
     double lsum = 0.0, q = 0.0;
     for (int i = threadIdx.x; i < n; i += BT) {
       lsum += log(L[(long long)i * ld + i]);
@@ -425,9 +652,10 @@ batched_gp_kernel(BatchParams p) {
         double *Cbar = Kb + (long long)k * ld + j;
         const double *C = L + (long long)k * ld + j;
         cta_trsm(m, bn, Cbar, ld, D, ld, 1, sm);
-        if (j > 0) cta_gemm<false, false>(Cbar, ld, L + (long long)j * ld, ld, Kb + (long long)k * ld, ld, m, j, bn,
-                                          -1.0, 1.0, false, sm);
-        cta_gemm<true, false>(Cbar, ld, C, ld, Dbar, ld, bn, bn, m, -1.0, 1.0, true, sm);
+        if (j > 0)
+          cta_gemm_big<MIXED, false, false>(Cbar, ld, L + (long long)j * ld, ld, Kb + (long long)k * ld, ld, m, j,
+                                            bn, -1.0, 1.0, false, sm, sx);
+        cta_gemm_big<MIXED, true, false>(Cbar, ld, C, ld, Dbar, ld, bn, bn, m, -1.0, 1.0, true, sm, sx);
       }
       // Dbar <- D^{-T} sym(tril(D^T Dbar)) D^{-1}
       cta_gemm<true, false>(D, ld, Dbar, ld, Mw, bn, bn, bn, bn, 1.0, 0.0, true, sm);
@@ -444,8 +672,8 @@ batched_gp_kernel(BatchParams p) {
       }
       __syncthreads();
       if (j > 0)
-        cta_gemm<true, false>(Dbar, ld, L + (long long)j * ld, ld, Kb + (long long)j * ld, ld, bn, j, n - j, -1.0,
-                              1.0, false, sm);
+        cta_gemm_big<MIXED, true, false>(Dbar, ld, L + (long long)j * ld, ld, Kb + (long long)j * ld, ld, bn, j,
+                                         n - j, -1.0, 1.0, false, sm, sx);
       for (int idx = threadIdx.x; idx < bn * bn; idx += BT) {
         const int r = idx / bn, c = idx - r * bn;
         double *q2 = Dbar + (long long)r * ld + c;
@@ -499,20 +727,28 @@ __global__ void order_kernel(int batch, const int *n, int *order) {
   }
 }
 
+size_t batch_slot_elems(int nmax, bool mixed) {
+  const size_t base = (size_t)nmax * nmax + 2 * (size_t)nmax + 3 * MAXB * MAXB;
+  return mixed ? base + (size_t)nmax * nmax + nmax : base;
+}
+size_t batched_smem_bytes(bool mixed) {
+  return mixed ? kSmemXOffset + sizeof(SmemX) : sizeof(Smem);
+}
+
 }  // namespace
 
-size_t batched_workspace_bytes(int batch, int nmax) {
-  const size_t slot = (size_t)nmax * nmax + 2 * (size_t)nmax + 3 * MAXB * MAXB;
+size_t batched_workspace_bytes(int batch, int nmax, bool mixed) {
+  const size_t slot = batch_slot_elems(nmax, mixed);
   return align_up((size_t)sm_count() * slot * sizeof(double), 256) + align_up((size_t)batch * sizeof(int), 256) + 256;
 }
 
 cudaError_t batched_gp_lml_grad(int batch, const int *n, const long long *offK, const long long *rowX, int d,
                                 const double *X, const double *y, const double *hyp, double *K, double *value,
-                                double *grad3, int *info, int nmax, void *ws, cudaStream_t s) {
+                                double *grad3, int *info, int nmax, bool mixed, void *ws, cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
   const int nb = std::min(std::max(tuning().batch_block, 16), MAXB);
   const int ctas = sm_count() * std::max(1, tuning().batch_ctas_per_sm);
-  const size_t slot = (size_t)nmax * nmax + 2 * (size_t)nmax + 3 * MAXB * MAXB;
+  const size_t slot = batch_slot_elems(nmax, mixed);
   char *p = (char *)ws;
   double *slots = (double *)p;
   p += align_up((size_t)sm_count() * slot * sizeof(double), 256);
@@ -547,11 +783,20 @@ cudaError_t batched_gp_lml_grad(int batch, const int *n, const long long *offK, 
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    e = cudaFuncSetAttribute(batched_gp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    e = cudaFuncSetAttribute(batched_gp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batched_smem_bytes(false));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(batched_gp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)batched_smem_bytes(true));
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  GPC_LAUNCH(GPC_TRACE_GEMM_F64, 0.0, 0.0, s, batched_gp_kernel<<<grid, BT, sizeof(Smem), s>>>(bp));
+  if (mixed)
+    GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, 0.0, 0.0, s,
+               batched_gp_kernel<true><<<grid, BT, batched_smem_bytes(true), s>>>(bp));
+  else
+    GPC_LAUNCH(GPC_TRACE_GEMM_F64, 0.0, 0.0, s,
+               batched_gp_kernel<false><<<grid, BT, batched_smem_bytes(false), s>>>(bp));
   return cudaGetLastError();
 }
 

@@ -164,10 +164,11 @@ cudaError_t from_df_rect(int m, int c, double *p, long long ld, cudaStream_t s);
 size_t mixed_workspace_bytes(int n);
 cudaError_t chol_mixed(int n, double *L, long long ldl, void *ws, int *info, cudaStream_t s);
 // Batched per-GP pass (batched.cu); rowX[i] = first row of GP i in X (d per row) and y.
-size_t batched_workspace_bytes(int batch, int nmax);
+// mixed: split-BF16 products for the O(n^3) work and FP64 refinement of alpha.
+size_t batched_workspace_bytes(int batch, int nmax, bool mixed);
 cudaError_t batched_gp_lml_grad(int batch, const int *n, const long long *offK, const long long *rowX, int d,
                                 const double *X, const double *y, const double *hyp, double *K, double *value,
-                                double *grad3, int *info, int nmax, void *ws, cudaStream_t s);
+                                double *grad3, int *info, int nmax, bool mixed, void *ws, cudaStream_t s);
 cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A, long long lda, void *ws,
                                int *err, cudaStream_t s);
 

@@ -45,6 +45,7 @@
 // wait is bounded in time; a timeout sets GPC_ERR_TIMEOUT in the error word,
 // drains the copies and MMAs already issued, frees TMEM and returns.
 #include "common.cuh"
+#include "slices.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -56,7 +57,7 @@
 namespace gpc {
 namespace {
 
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32, OZ_CHUNK = 128, OZ_S = 5, OZ_STAGES = 3;
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32, OZ_CHUNK = 128, OZ_S = kSlices, OZ_STAGES = 3;
 constexpr int OZ_QPC = OZ_CHUNK / OZ_BK;                 // stages per chunk
 constexpr int OZ_EPI_WARPS = 8;                         // two per TMEM lane quarter
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
@@ -532,43 +533,16 @@ split_kernel(const double *src, long long rs, long long ks, int M, int K, int fi
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       bits[i] = (unsigned long long)__double_as_longlong(tile[rr][lane * 4 + i]);
-      const int e = (int)((bits[i] >> 52) & 0x7FF);
-      ex = max(ex, (e == 0x7FF) ? 0 : e);
+      ex = max(ex, slice_exponent(bits[i]));
     }
     const int emax = __reduce_max_sync(0xffffffffu, ex);
     unsigned short out[OZ_S][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int e = (int)((bits[i] >> 52) & 0x7FF);
-      unsigned long long X = 0;
-      if (e != 0 && e != 0x7FF && emax != 0) {
-        const unsigned long long mant = (bits[i] & ((1ull << 52) - 1)) | (1ull << 52);
-        const int sh = 53 - 8 * OZ_S + (emax - e);  // >= 13
-        if (sh < 64) X = (mant + (1ull << (sh - 1))) >> sh;
-      }
-      const bool neg = (bits[i] >> 63) != 0;
-      // Balanced digits, least significant first: d in [-128, 127], carry up.
-      int dig[OZ_S];
+      float v[OZ_S];
+      split_value(bits[i], emax, v);
 #pragma unroll
-      for (int pp = OZ_S - 1; pp >= 1; --pp) {
-        int t = (int)(X & 255u);
-        X >>= 8;
-        if (t >= 128) {
-          t -= 256;
-          X += 1;
-        }
-        dig[pp] = t;
-      }
-      dig[0] = (int)X;  // in [0, 256]
-      // e_chunk = emax - 1023 + 1: slice p (0-based) carries 2^(e_chunk - 8 (p + 1))
-#pragma unroll
-      for (int pp = 0; pp < OZ_S; ++pp) {
-        const int fexp = (emax - 1023 + 1) - 8 * (pp + 1) + 127;  // FP32 biased exponent of the scale
-        float v = 0.0f;
-        if (dig[pp] != 0 && fexp >= 1 && fexp <= 254) v = (float)dig[pp] * __int_as_float(fexp << 23);
-        if (neg) v = -v;
-        out[pp][i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-      }
+      for (int pp = 0; pp < OZ_S; ++pp) out[pp][i] = __bfloat16_as_ushort(__float2bfloat16_rn(v[pp]));
     }
     const int r = r0 + rr;
 #pragma unroll

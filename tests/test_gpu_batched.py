@@ -22,8 +22,8 @@ def make_batch(sizes, d=4, seed=0, sigma=0.1):
     return Xs, ys, np.array(hyps)
 
 
-def run_batch(sizes, Xs, ys, hyps, block=None):
-    b = gp.Batch(sizes)
+def run_batch(sizes, Xs, ys, hyps, block=None, precision="fp64"):
+    b = gp.Batch(sizes, precision=precision)
     X = torch.as_tensor(np.concatenate(Xs), device="cuda").contiguous()
     y = torch.as_tensor(np.concatenate(ys), device="cuda").contiguous()
     old = gp.get_tuning(gp.GPC_TUNE_BATCH_BLOCK)
@@ -128,3 +128,94 @@ def test_batched_graph_replay_matches_direct_call():
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(b.value, v0) and torch.equal(b.grad3, g0)
+
+
+# ---------------------------------------------------------------- mixed path
+# Split-BF16 products with double-float accumulation and FP64 refinement of
+# alpha: the value and gradient stay within 1e-9 / 1e-7 (relative) of the
+# FP64 oracle on these conditioning levels (sigma = 0.1, so cond(K) is at most
+# about n / sigma^2 ~ 1e5).
+MIXED_VALUE_TOL, MIXED_GRAD_TOL = 1e-9, 1e-7
+
+
+@pytest.mark.parametrize("block", [32, 64])
+def test_batched_mixed_matches_oracle(block):
+    Xs, ys, hyps = make_batch(SIZES, seed=block + 1)
+    b, v, g, info = run_batch(SIZES, Xs, ys, hyps, block, precision="mixed")
+    assert np.all(info[:, 1] == gp.GPC_OK)
+    worst_v = worst_g = 0.0
+    for i, n in enumerate(SIZES):
+        ref = O.gp_lml_and_grad(Xs[i], ys[i], *hyps[i], 0.0)
+        ev = abs(v[i] - ref["value"]) / max(1.0, abs(ref["value"]))
+        eg = np.linalg.norm(g[i] - ref["grad"]) / np.linalg.norm(ref["grad"])
+        worst_v, worst_g = max(worst_v, ev), max(worst_g, eg)
+        assert ev <= MIXED_VALUE_TOL, (i, n, ev)
+        assert eg <= MIXED_GRAD_TOL, (i, n, eg)
+        if n in (65, 257):
+            L = b.factor(i).cpu().numpy()
+            assert np.linalg.norm(L - ref["L"]) <= 1e-9 * np.linalg.norm(ref["L"])
+            assert not np.any(np.triu(L, 1))
+    print(f"batched mixed block {block}: value {worst_v:.3e} grad {worst_g:.3e}")
+
+
+def test_batched_mixed_full_batch_against_fp64_and_oracle():
+    # the full batch workload (512 GPs, n ~ U{64..1024}, d = 4) through both
+    # precisions in the launch configuration the benchmark times; the oracle
+    # checks the smallest and the largest members
+    sizes = list(W.batch_sizes(512, 64, 1024, seed=0))
+    Xs, ys, hyps = make_batch(sizes, seed=0)
+    _, vf, gf, inf = run_batch(sizes, Xs, ys, hyps)
+    _, vm, gm, inm = run_batch(sizes, Xs, ys, hyps, precision="mixed")
+    assert np.all(inf[:, 1] == gp.GPC_OK) and np.all(inm[:, 1] == gp.GPC_OK)
+    ev = np.abs(vm - vf) / np.maximum(1.0, np.abs(vf))
+    eg = np.linalg.norm(gm - gf, axis=1) / np.linalg.norm(gf, axis=1)
+    print(f"batched mixed vs fp64 (512 GPs): value {ev.max():.3e} grad {eg.max():.3e}")
+    assert ev.max() <= MIXED_VALUE_TOL and eg.max() <= MIXED_GRAD_TOL
+    order = np.argsort(sizes)
+    for i in (order[0], order[-1]):
+        ref = O.gp_lml_and_grad(Xs[i], ys[i], *hyps[i], 0.0)
+        assert abs(vf[i] - ref["value"]) <= 1e-10 * max(1.0, abs(ref["value"]))
+        assert abs(vm[i] - ref["value"]) <= MIXED_VALUE_TOL * max(1.0, abs(ref["value"]))
+        assert np.linalg.norm(gm[i] - ref["grad"]) <= MIXED_GRAD_TOL * np.linalg.norm(ref["grad"])
+
+
+def test_batched_mixed_failure_is_isolated():
+    sizes = [40, 50, 60]
+    Xs, ys, hyps = make_batch(sizes, seed=9)
+    hyps[1, 2] = np.nan
+    _, v, g, info = run_batch(sizes, Xs, ys, hyps, precision="mixed")
+    assert info[1, 1] in (gp.GPC_ERR_NOT_PD, gp.GPC_ERR_NAN)
+    assert np.isnan(v[1])
+    for i in (0, 2):
+        ref = O.gp_lml_and_grad(Xs[i], ys[i], *hyps[i], 0.0)
+        assert info[i, 1] == gp.GPC_OK
+        assert abs(v[i] - ref["value"]) <= MIXED_VALUE_TOL * abs(ref["value"])
+
+
+def test_batched_mixed_graph_replay_is_deterministic():
+    sizes = [90, 17, 150, 64, 300]
+    Xs, ys, hyps = make_batch(sizes, seed=12)
+    b = gp.Batch(sizes, precision="mixed")
+    X = torch.as_tensor(np.concatenate(Xs), device="cuda").contiguous()
+    y = torch.as_tensor(np.concatenate(ys), device="cuda").contiguous()
+    hyp = torch.as_tensor(hyps, device="cuda").contiguous()
+    gp.batched_gp_lml_grad(b, X, y, hyp)
+    torch.cuda.synchronize()
+    v0, g0 = b.value.clone(), b.grad3.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gp.batched_gp_lml_grad(b, X, y, hyp)
+    b.value.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(b.value, v0) and torch.equal(b.grad3, g0)
+
+
+def test_batched_fp64_workspace_refuses_mixed_run():
+    sizes = [10, 20]
+    b = gp.Batch(sizes)
+    X = torch.zeros(30, 4, dtype=torch.float64, device="cuda")
+    y = torch.zeros(30, dtype=torch.float64, device="cuda")
+    with pytest.raises(gp.GpcholError):
+        gp.batched_gp_lml_grad(b, X, y, torch.ones(2, 3, dtype=torch.float64), precision="mixed")
