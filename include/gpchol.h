@@ -79,7 +79,8 @@ int gpc_workspace_size(int n, int precision, size_t *bytes);
  * Tuning knobs (host-side, process-wide; not thread-safe against concurrent
  * calls).  key: GPC_TUNE_BLOCK = block size b of the blocked factorisation and
  * adjoint (16..128, multiple of 16; default 128), GPC_TUNE_SLICES = number of
- * BF16 slices of the mixed path (3..8), GPC_TUNE_SPLITK_MIN = minimum K per
+ * BF16 slices of the mixed path (read-only: the split kernels group their
+ * products for 5 slices, so only 5 is accepted), GPC_TUNE_SPLITK_MIN = minimum K per
  * split of the split-K products.  Changing GPC_TUNE_BLOCK changes the
  * workspace size.  Returns GPC_ERR_INVALID_ARG for an unknown key or value.
  */

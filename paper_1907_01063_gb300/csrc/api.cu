@@ -109,10 +109,8 @@ int gpc_set_tuning(int key, int value) {
       if (value < 16 || value > kMaxBlock || value % 16) return GPC_ERR_INVALID_ARG;
       tuning().block = value;
       return GPC_OK;
-    case GPC_TUNE_SLICES:
-      if (value < 3 || value > 8) return GPC_ERR_INVALID_ARG;
-      tuning().slices = value;
-      return GPC_OK;
+    case GPC_TUNE_SLICES:  // fixed by the product grouping of the split kernels
+      return value == slices_count() ? GPC_OK : GPC_ERR_INVALID_ARG;
     case GPC_TUNE_SPLITK_MIN:
       if (value < 16 || value > (1 << 20)) return GPC_ERR_INVALID_ARG;
       tuning().splitk_min = value;
@@ -130,7 +128,7 @@ int gpc_get_tuning(int key, int *value) {
   if (!value) return GPC_ERR_INVALID_ARG;
   switch (key) {
     case GPC_TUNE_BLOCK: *value = tuning().block; return GPC_OK;
-    case GPC_TUNE_SLICES: *value = tuning().slices; return GPC_OK;
+    case GPC_TUNE_SLICES: *value = slices_count(); return GPC_OK;
     case GPC_TUNE_SPLITK_MIN: *value = tuning().splitk_min; return GPC_OK;
     case GPC_TUNE_BATCH_BLOCK: *value = tuning().batch_block; return GPC_OK;
     default: return GPC_ERR_INVALID_ARG;

@@ -14,7 +14,6 @@ namespace gpc {
 // ---------------------------------------------------------------- tuning
 struct Tuning {
   int block = 128;        // b: block size of the blocked factorisation / adjoint
-  int slices = 5;         // BF16 slices per FP64 operand on the mixed path
   int splitk_min = 32;    // minimum K per split of a split-K product
   int batch_block = 64;   // block size inside the batched per-GP pass (32 or 64)
   int batch_ctas_per_sm = 1;

@@ -57,6 +57,12 @@ def test_tuning_roundtrip_and_validation():
                 gp.set_tuning(gp.GPC_TUNE_BLOCK, bad)
         with pytest.raises(gp.GpcholError):
             gp.set_tuning(99, 1)
+        # the slice count is fixed by the split kernels: readable, settable only to itself
+        assert gp.get_tuning(gp.GPC_TUNE_SLICES) == 5
+        gp.set_tuning(gp.GPC_TUNE_SLICES, 5)
+        for bad in (3, 4, 6):
+            with pytest.raises(gp.GpcholError):
+                gp.set_tuning(gp.GPC_TUNE_SLICES, bad)
     finally:
         gp.set_tuning(gp.GPC_TUNE_BLOCK, old)
 
