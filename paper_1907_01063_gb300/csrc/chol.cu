@@ -152,6 +152,7 @@ cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, 
       p.B = Dbar; p.ldb = lda;
       p.C = w.m; p.ldc = nb;
       p.uplo = UPLO_LOWER_MIRROR;
+      p.kskip = KSKIP_ROWS;  // D^T upper triangular
       p.algo_flops = (double)nb * nb * nb / 3.0;  // triangular A and B, lower output
       TRY(gemm_f64(p, w.scratch, s));
       Gemm t;  // T = M D^{-1}
@@ -159,6 +160,7 @@ cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, 
       t.A = w.m; t.lda = nb;
       t.B = w.dinv; t.ldb = nb;
       t.C = w.t; t.ldc = nb;
+      t.kskip = KSKIP_COLS;  // D^{-1} lower triangular
       t.algo_flops = (double)nb * nb * (nb + 1);  // triangular B
       TRY(gemm_f64(t, w.scratch, s));
       Gemm d;  // Dbar = D^{-T} T, symmetric
@@ -167,6 +169,7 @@ cudaError_t chol_adjoint_fp64(int n, const double *L, long long ldl, double *A, 
       d.B = w.t; d.ldb = nb;
       d.C = Dbar; d.ldc = lda;
       d.uplo = UPLO_LOWER_MIRROR;
+      d.kskip = KSKIP_ROWS;  // D^{-T} upper triangular
       d.algo_flops = (double)nb * nb * nb / 3.0 * 2.0;  // triangular A, lower output
       TRY(gemm_f64(d, w.scratch, s));
     }

@@ -31,6 +31,7 @@ int sm_count();
 // neither computed nor touched); 2 lower, mirrored into the upper triangle.
 // beta == 0 never reads C.
 enum { UPLO_FULL = 0, UPLO_LOWER = 1, UPLO_LOWER_MIRROR = 2 };
+enum { KSKIP_NONE = 0, KSKIP_ROWS = 1, KSKIP_COLS = 2 };
 struct Gemm {
   int M = 0, N = 0, K = 0;
   double algo_flops = 0.0;  // algorithmic flops for the trace (0: 2MNK, or M(M+1)K lower)
@@ -43,6 +44,11 @@ struct Gemm {
   double *C = nullptr;
   long long ldc = 0;
   int uplo = UPLO_FULL;
+  // Known-zero K ranges of a triangular operand, skipped per output tile:
+  // KSKIP_ROWS when op(A)[i][k] = 0 for k < i (op(A) upper triangular), so
+  // the tile's rows from m0 need k >= m0; KSKIP_COLS when op(B)[k][j] = 0
+  // for k < j (op(B) lower triangular), so columns from n0 need k >= n0.
+  int kskip = KSKIP_NONE;
 };
 // Bytes of split-K scratch any gemm_f64 call may use (a fixed cap).
 size_t gemm_f64_scratch_bytes();
@@ -56,11 +62,13 @@ constexpr int kMaxBlock = 128;
 cudaError_t potrf_trtri_diag(int nb, double *A, long long lda, double *Winv, int *info,
                              int pivot_offset, cudaStream_t s);
 // Factor only (no inverse) of the nb x nb block at A, in place.
-cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_offset, cudaStream_t s);
+// df: the block is read in double-float storage (written back as FP64).
+cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_offset, cudaStream_t s,
+                       bool df = false);
 // In-place panel solve against the lower nb x nb block T: mode 0 X <- X T^{-T},
-// mode 1 X <- X T^{-1}.
+// mode 1 X <- X T^{-1}.  df: X is read in double-float storage (written back as FP64).
 cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode,
-                      cudaStream_t s);
+                      cudaStream_t s, bool df = false);
 // Inverse (lower, ld = nb) of the nb x nb lower block D.
 cudaError_t trtri_diag(int nb, const double *D, long long ldd, double *Dinv, cudaStream_t s);
 // Inverses of all diagonal blocks of L in one launch: block 0 = rows [0, first),
@@ -153,9 +161,12 @@ size_t ozaki_partial_bytes(int M, int N, int splits);
 // K ranges through `partial` (ozaki_partial_bytes) in fixed order.
 // lower with M != N keeps the entries with (local) col <= row.  max_ctas > 0
 // caps the persistent grid (leaves SMs free for work on another stream).
+// kdepth (multiple of 32, at most 128; 0 = 128): K entries of each chunk that
+// are multiplied -- the rest of the chunk must be zero slices.
 cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &B, int b_row0, int b_k0,
                        int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
-                       int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas = 0);
+                       int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas = 0,
+                       int kdepth = 0);
 // Lower triangle of src (FP64) -> dst in double-float storage (upper set to 0); src may == dst.
 cudaError_t to_df_lower(int n, const double *src, long long lds, double *dst, long long ldd, cudaStream_t s);
 // m x c block in double-float storage -> FP64, in place.

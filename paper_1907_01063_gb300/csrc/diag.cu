@@ -148,10 +148,19 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 // (GPC_ERR_NOT_PD, or GPC_ERR_NAN for NaN/Inf) and the rest of the block is
 // written back unfinished.  No inverse is formed: the panel below is solved
 // by substitution (trsm_rows_kernel).
+// An FP64 entry, or a double-float one (FP32 hi + lo in the same 8 bytes) when df.
+__device__ __forceinline__ double load_entry(const double *p, int df) {
+  if (df) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return (double)v.x + (double)v.y;
+  }
+  return *p;
+}
+
 constexpr int PF_PW = 16;
 static_assert(PF_PW * PF_PW == DIAG_THREADS, "one thread per sub-block element");
 __global__ void __launch_bounds__(DIAG_THREADS)
-potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset) {
+potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset, int df) {
   extern __shared__ double smem[];                            // nb x (nb + 1)
   __shared__ __align__(16) double pt[PF_PW][kMaxBlock + 4];  // panel rows below, transposed
   __shared__ double rdiag[PF_PW], pinv[PF_PW];
@@ -160,7 +169,7 @@ potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset)
   if (threadIdx.x == 0) fail = 0;
   for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
     const int i = idx / nb, j = idx - i * nb;
-    S(smem, ld, i, j) = (j <= i) ? A[(long long)i * lda + j] : 0.0;
+    S(smem, ld, i, j) = (j <= i) ? load_entry(A + (long long)i * lda + j, df) : 0.0;
   }
   __syncthreads();
   const int si = threadIdx.x / PF_PW, sk = threadIdx.x % PF_PW;  // sub-block element of this thread
@@ -276,14 +285,14 @@ potrf_diag_kernel(int nb, double *A, long long lda, int *info, int pivot_offset)
 // column suffices.  Fewer rows per CTA for short panels keep every SM busy.
 template <int ROWS>
 __global__ void __launch_bounds__(256)
-trsm_rows_kernel(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode) {
+trsm_rows_kernel(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode, int df) {
   constexpr int CG = 256 / ROWS;
   __shared__ double xs[ROWS][kMaxBlock + 1];
   __shared__ double rdiag[kMaxBlock];
   const int r0 = blockIdx.x * ROWS, rows = min(ROWS, m - r0);
   for (int idx = threadIdx.x; idx < ROWS * nb; idx += blockDim.x) {
     const int r = idx / nb, c = idx - r * nb;
-    xs[r][c] = (r < rows) ? X[(long long)(r0 + r) * ldx + c] : 0.0;
+    xs[r][c] = (r < rows) ? load_entry(X + (long long)(r0 + r) * ldx + c, df) : 0.0;
   }
   for (int j = threadIdx.x; j < nb; j += blockDim.x) rdiag[j] = 1.0 / __ldg(&T[(long long)j * ldt + j]);
   __syncthreads();
@@ -312,6 +321,64 @@ trsm_rows_kernel(int m, int nb, double *X, long long ldx, const double *T, long 
   for (int idx = threadIdx.x; idx < ROWS * nb; idx += blockDim.x) {
     const int rr = idx / nb, c = idx - rr * nb;
     if (rr < rows) X[(long long)(r0 + rr) * ldx + c] = xs[rr][c];
+  }
+}
+
+// The same panel solve with four threads per row and no block barriers, for
+// the block sizes the factorisations use (NB = 64 or 128).  Thread t of a row
+// holds columns k = 4c + t (c < NB / 4) in registers; at step j the owner of
+// column j (final by then) passes it to the row's other three threads with a
+// warp shuffle, every thread updates its columns still to be solved, and the
+// owner of the next column scales it.  Columns are dealt round-robin so the
+// shrinking work stays balanced; the loops are unrolled at compile time so the
+// row stays in registers.  The FP64 pipe, not synchronisation, bounds it.
+constexpr int TQ_THREADS = 64;  // 16 rows per CTA: enough CTAs that every SM gets an even share
+template <int NB, int MODE>
+__global__ void __launch_bounds__(TQ_THREADS)
+trsm_quad_kernel(int m, double *X, long long ldx, const double *T, long long ldt, int df) {
+  constexpr int C = NB / 4;
+  __shared__ double rdiag[NB];
+  for (int k = threadIdx.x; k < NB; k += blockDim.x) rdiag[k] = 1.0 / __ldg(&T[(long long)k * ldt + k]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, t = lane & 3, src0 = lane & ~3;
+  const int row = blockIdx.x * (TQ_THREADS / 4) + (threadIdx.x >> 2);
+  const bool live = row < m;
+  double *xr = X + (long long)(live ? row : 0) * ldx;
+  double x[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) x[c] = live ? load_entry(xr + 4 * c + t, df) : 0.0;
+  if (MODE == 0) {  // X <- X T^{-T}: columns ascending, x_k -= x_j T[k][j] for k > j
+    if (t == 0) x[0] *= rdiag[0];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const double xj = __shfl_sync(0xffffffffu, x[j >> 2], src0 | (j & 3));
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if (4 * c + 3 <= j) continue;  // every column of this group is already final
+        const int k = 4 * c + t;
+        const double tv = __ldg(&T[(long long)k * ldt + j]);
+        if (4 * c > j || k > j) x[c] = fma(-xj, tv, x[c]);
+      }
+      if (j + 1 < NB && t == ((j + 1) & 3)) x[(j + 1) >> 2] *= rdiag[j + 1];
+    }
+  } else {  // X <- X T^{-1}: columns descending, x_k -= x_j T[j][k] for k < j
+    if (t == ((NB - 1) & 3)) x[C - 1] *= rdiag[NB - 1];
+#pragma unroll
+    for (int j = NB - 1; j >= 0; --j) {
+      const double xj = __shfl_sync(0xffffffffu, x[j >> 2], src0 | (j & 3));
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if (4 * c >= j) continue;  // every column of this group is at or past j
+        const int k = 4 * c + t;
+        const double tv = __ldg(&T[(long long)j * ldt + k]);
+        if (4 * c + 3 < j || k < j) x[c] = fma(-xj, tv, x[c]);
+      }
+      if (j > 0 && t == ((j - 1) & 3)) x[(j - 1) >> 2] *= rdiag[j - 1];
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) xr[4 * c + t] = x[c];
   }
 }
 
@@ -409,7 +476,7 @@ cudaError_t trtri_batched(int n, const double *L, long long ldl, int first, int 
   return cudaGetLastError();
 }
 
-cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_offset, cudaStream_t s) {
+cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_offset, cudaStream_t s, bool df) {
   if (nb <= 0) return cudaSuccess;
   if (nb > kMaxBlock) return cudaErrorInvalidValue;
   static bool attr_set[64] = {};
@@ -423,25 +490,41 @@ cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_of
   }
   const size_t smem = (size_t)nb * (nb + 1) * sizeof(double);
   GPC_LAUNCH(GPC_TRACE_DIAG, (double)nb * nb * nb / 3.0, 16.0 * nb * nb, s,
-             potrf_diag_kernel<<<1, DIAG_THREADS, smem, s>>>(nb, A, lda, info, pivot_offset));
+             potrf_diag_kernel<<<1, DIAG_THREADS, smem, s>>>(nb, A, lda, info, pivot_offset, df ? 1 : 0));
   return cudaGetLastError();
 }
 
 cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool df) {
   if (m <= 0 || nb <= 0) return cudaSuccess;
   if (nb > kMaxBlock) return cudaErrorInvalidValue;
-  // 32 rows per CTA when that still gives two CTAs per SM, else 16 or 8
+  const double fl = (double)m * nb * nb, by = 16.0 * (double)m * nb + 4.0 * nb * nb;
+  const unsigned qgrid = (unsigned)((m + TQ_THREADS / 4 - 1) / (TQ_THREADS / 4));
+  if (nb == 64 || nb == 128) {
+    if (nb == 64 && mode == 0)
+      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, trsm_quad_kernel<64, 0><<<qgrid, TQ_THREADS, 0, s>>>(m, X, ldx, T, ldt, df));
+    else if (nb == 64)
+      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, trsm_quad_kernel<64, 1><<<qgrid, TQ_THREADS, 0, s>>>(m, X, ldx, T, ldt, df));
+    else if (mode == 0)
+      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, trsm_quad_kernel<128, 0><<<qgrid, TQ_THREADS, 0, s>>>(m, X, ldx, T, ldt, df));
+    else
+      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, trsm_quad_kernel<128, 1><<<qgrid, TQ_THREADS, 0, s>>>(m, X, ldx, T, ldt, df));
+    return cudaGetLastError();
+  }
+  // other block sizes: 32 rows per CTA when that still gives two CTAs per SM, else 16 or 8
   const int sms = sm_count();
   if ((m + 31) / 32 >= 2 * sms) {
     GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
-               trsm_rows_kernel<32><<<(m + 31) / 32, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
+               trsm_rows_kernel<32><<<(m + 31) / 32, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode,
+                                                                            df ? 1 : 0));
   } else if ((m + 15) / 16 >= sms) {
     GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
-               trsm_rows_kernel<16><<<(m + 15) / 16, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
+               trsm_rows_kernel<16><<<(m + 15) / 16, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode,
+                                                                            df ? 1 : 0));
   } else {
     GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
-               trsm_rows_kernel<8><<<(m + 7) / 8, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode));
+               trsm_rows_kernel<8><<<(m + 7) / 8, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode,
+                                                                            df ? 1 : 0));
   }
   return cudaGetLastError();
 }

@@ -20,6 +20,7 @@ namespace gpc {
 namespace {
 
 constexpr int MB = 128;  // block size of the mixed path (== slice chunk)
+constexpr int MH = 64;   // panel sub-block of the factorisation's FP64 steps
 constexpr size_t kPartialCap = size_t(40) << 20;
 
 #define TRY(x)                        \
@@ -101,17 +102,38 @@ cudaError_t chol_mixed(int n, double *L, long long ldl, void *ws, int *info, cud
   for (int k0 = 0; k0 < n; k0 += MB, ++step) {
     const int nb = std::min(MB, n - k0), m = n - k0 - nb;
     double *A11 = L + (long long)k0 * ldl + k0;
-    TRY(from_df_rect(n - k0, nb, A11, ldl, s));
-    TRY(potrf_diag(nb, A11, ldl, info, k0, s));
-    if (rest_pending) {
-      TRY(cudaStreamWaitEvent(s, aux->ev_rest, 0));
-      rest_pending = false;
+    void *sbuf = (char *)w.sc + (size_t)(step & 1) * slice_bytes(n, 1);
+    if (nb > MH) {
+      // Two 64-wide steps: factor and solve the left half, update the right
+      // half of the block column with it (split-BF16, K = 64), then factor and
+      // solve the right half.  The FP64 work of the block column halves.
+      const int hb = nb - MH, ma = n - k0 - MH;
+      double *Ab = A11 + (long long)MH * ldl + MH;  // right half's diagonal block
+      TRY(potrf_diag(MH, A11, ldl, info, k0, s, true));
+      if (rest_pending) {
+        TRY(cudaStreamWaitEvent(s, aux->ev_rest, 0));
+        rest_pending = false;
+      }
+      TRY(trsm_rows(ma, MH, A11 + (long long)MH * ldl, ldl, A11, ldl, 0, s, true));
+      SliceBuf Sh = slice_view(sbuf, ma, 1);
+      TRY(split_operand(A11 + (long long)MH * ldl, ldl, 1, ma, MH, MH, Sh, s));
+      TRY(ozaki_gemm(Sh, 0, 0, Sh, 0, 0, ma, hb, 1, true, -1.0f, (float2 *)Ab, ldl, 1, nullptr,
+                     info ? info + 1 : nullptr, s, 0, MH));
+      TRY(potrf_diag(hb, Ab, ldl, info, k0 + MH, s, true));
+      if (m <= 0) continue;
+      TRY(trsm_rows(m, hb, Ab + (long long)hb * ldl, ldl, Ab, ldl, 0, s, true));
+    } else {
+      TRY(potrf_diag(nb, A11, ldl, info, k0, s, true));
+      if (rest_pending) {
+        TRY(cudaStreamWaitEvent(s, aux->ev_rest, 0));
+        rest_pending = false;
+      }
+      if (m <= 0) continue;
+      TRY(trsm_rows(m, nb, A11 + (long long)nb * ldl, ldl, A11, ldl, 0, s, true));  // L21 = A21 L11^{-T} (FP64)
     }
-    if (m <= 0) continue;
     double *A21 = L + (long long)(k0 + nb) * ldl + k0;
-    TRY(trsm_rows(m, nb, A21, ldl, A11, ldl, 0, s));  // L21 = A21 L11^{-T} (FP64)
     // A22 -= L21 L21^T on split-BF16 slices, lower part, double-float storage
-    SliceBuf S = slice_view((char *)w.sc + (size_t)(step & 1) * slice_bytes(n, 1), m, 1);
+    SliceBuf S = slice_view(sbuf, m, 1);
     TRY(split_operand(A21, ldl, 1, m, nb, nb, S, s));
     const int nb2 = std::min(MB, m);
     float2 *T = (float2 *)(A21 + nb);
@@ -161,8 +183,24 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
     bool bbar_pending = false;
     if (m > 0) {
       double *Cbar = A + (long long)k * lda + j;
-      TRY(from_df_rect(m, nb, Cbar, lda, s));
-      TRY(trsm_rows(m, nb, Cbar, lda, D, ldl, 1, s));  // Cbar <- Cbar D^{-1} (FP64)
+      if (nb > MH) {
+        // Cbar <- Cbar D^{-1} as two 64-wide steps, right half first: with
+        // D = [Da 0; Dba Db], Xb = Cb Db^{-1}, then Ca -= Xb Dba (split-BF16,
+        // K = nb - 64) and Xa = Ca Da^{-1}.  The FP64 solves halve.
+        const int hb = nb - MH;
+        double *Cb = Cbar + MH;
+        const double *Dba = D + (long long)MH * ldl;
+        TRY(trsm_rows(m, hb, Cb, lda, Dba + MH, ldl, 1, s, true));
+        SliceBuf SX = slice_view((char *)w.sc + slice_bytes(n, 1), m, 1);
+        SliceBuf SD = slice_view(w.sdc, MH, 1);
+        TRY(split_operand(Cb, lda, 1, m, hb, hb, SX, s));
+        TRY(split_operand(Dba, 1, ldl, MH, hb, hb, SD, s));  // row c, K index t: Dba[t][c]
+        TRY(ozaki_gemm(SX, 0, 0, SD, 0, 0, m, MH, 1, false, -1.0f, (float2 *)Cbar, lda, 1, nullptr, err, s, 0,
+                       (hb + 31) / 32 * 32));
+        TRY(trsm_rows(m, MH, Cbar, lda, D, ldl, 1, s, true));
+      } else {
+        TRY(trsm_rows(m, nb, Cbar, lda, D, ldl, 1, s, true));  // Cbar <- Cbar D^{-1} (FP64)
+      }
       // Dbar -= Cbar^T C on slices, Dbar still in double-float storage: the
       // columns of Cbar (K = rows k..n) fill chunks 1.. of the block column's
       // slices; C^T is rows j..k of the L^T slices.
@@ -191,6 +229,7 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
       p.B = Dbar; p.ldb = lda;
       p.C = w.m; p.ldc = nb;
       p.uplo = UPLO_LOWER_MIRROR;
+      p.kskip = KSKIP_ROWS;  // D^T upper triangular
       p.algo_flops = (double)nb * nb * nb / 3.0;
       TRY(gemm_f64(p, w.scratch, s));
       Gemm t;  // T = M D^{-1}
@@ -198,6 +237,7 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
       t.A = w.m; t.lda = nb;
       t.B = dinv; t.ldb = nb;
       t.C = w.t; t.ldc = nb;
+      t.kskip = KSKIP_COLS;  // D^{-1} lower triangular
       t.algo_flops = (double)nb * nb * (nb + 1);
       TRY(gemm_f64(t, w.scratch, s));
       Gemm d;  // Dbar = D^{-T} T, symmetric
@@ -206,6 +246,7 @@ cudaError_t chol_adjoint_mixed(int n, const double *L, long long ldl, double *A,
       d.B = w.t; d.ldb = nb;
       d.C = Dbar; d.ldc = lda;
       d.uplo = UPLO_LOWER_MIRROR;
+      d.kskip = KSKIP_ROWS;  // D^{-T} upper triangular
       d.algo_flops = (double)nb * nb * nb / 3.0 * 2.0;
       TRY(gemm_f64(d, w.scratch, s));
     }

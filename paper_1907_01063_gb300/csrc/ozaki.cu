@@ -58,7 +58,6 @@ namespace gpc {
 namespace {
 
 constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32, OZ_CHUNK = 128, OZ_S = kSlices, OZ_STAGES = 3;
-constexpr int OZ_QPC = OZ_CHUNK / OZ_BK;                 // stages per chunk
 constexpr int OZ_EPI_WARPS = 8;                         // two per TMEM lane quarter
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_A_PLANE = OZ_BM * OZ_BK * 2;            // 8 KiB
@@ -75,7 +74,7 @@ constexpr int OZ_SMEM_BYTES = OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + OZ_EPI_WAR
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct OzParams {
-  int M, N, chunks;
+  int M, N, chunks, qpc;  // qpc: 32-wide K stages used per chunk (chunks shorter than 128)
   int a_row0, b_row0, a_k0, b_k0;
   int lower, splits, tiles_m, tiles_n, num_work;
   float alpha;
@@ -327,7 +326,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         int tm, tn, c0, c1;
         work_coords(p, w, tm, tn, c0, c1);
         for (int c = c0; c < c1 && ok; ++c) {
-          for (int h = 0; h < OZ_QPC; ++h) {
+          for (int h = 0; h < p.qpc; ++h) {
             if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
             mbar_expect_tx(full0 + 8 * stage, OZ_A_STAGE + OZ_B_STAGE);
             const int ka = p.a_k0 + c * OZ_CHUNK + h * OZ_BK;
@@ -367,7 +366,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           if (!mbar_wait(tempty0 + 8 * buf, tphase ^ 1, abort_flag)) { ok = false; break; }
           fence_after();
           const uint32_t tacc = tbase + (uint32_t)(buf * OZ_ACC_COLS);
-          for (int h = 0; h < OZ_QPC && ok; ++h) {
+          for (int h = 0; h < p.qpc && ok; ++h) {
             if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
             fence_after();
             const uint64_t da = sdesc(smem_u32(sA + stage * OZ_A_STAGE));
@@ -656,8 +655,10 @@ size_t ozaki_partial_bytes(int M, int N, int splits) {
 
 cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &B, int b_row0, int b_k0,
                        int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
-                       int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas) {
+                       int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas, int kdepth) {
   if (M <= 0 || N <= 0 || chunks <= 0) return cudaSuccess;
+  if (kdepth <= 0) kdepth = OZ_CHUNK;
+  if (kdepth > OZ_CHUNK || kdepth % OZ_BK) return cudaErrorInvalidValue;
   if (alpha != 1.0f && alpha != -1.0f) return cudaErrorInvalidValue;  // the epilogue applies a sign only
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, OZ_BM) || !make_map(&mb, B, OZ_BN)) return cudaErrorInvalidValue;
@@ -674,6 +675,7 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
   p.M = M;
   p.N = N;
   p.chunks = chunks;
+  p.qpc = kdepth / OZ_BK;
   p.a_row0 = a_row0;
   p.b_row0 = b_row0;
   p.a_k0 = a_k0;
@@ -699,8 +701,8 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
   // output entries: the whole M x N block, or its lower part (col <= row)
   const double mn = !lower ? (double)M * N
                            : (M >= N ? 0.5 * (double)N * (N + 1) + (double)(M - N) * N : 0.5 * (double)M * (M + 1));
-  const double flops = 2.0 * mn * (double)chunks * OZ_CHUNK * 15.0;  // 15 slice products
-  const double bytes = 16.0 * mn * chunks + (double)(M + N) * chunks * OZ_CHUNK * 2 * OZ_S;
+  const double flops = 2.0 * mn * (double)chunks * kdepth * 15.0;  // 15 slice products
+  const double bytes = 16.0 * mn * chunks + (double)(M + N) * chunks * kdepth * 2 * OZ_S;
   const int grid = std::min(p.num_work, ctas);
   if (alpha < 0.0f)
     GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, bytes, s,

@@ -49,7 +49,8 @@ extern "C" int gpc_test_ozaki_gemm(int M, int N, int K, const double *A, const d
   int splits = (int)std::max<long long>(1, std::min<long long>(chunks, (2LL * sm_count() + tiles - 1) / tiles));
   while (splits > 1 && ozaki_partial_bytes(M, N, splits) > kTestPartialCap) --splits;
   if (e == cudaSuccess)
-    e = ozaki_gemm(SA, 0, 0, SB, 0, 0, M, N, chunks, false, 1.0f, (float2 *)C, N, splits, partial, err, s);
+    e = ozaki_gemm(SA, 0, 0, SB, 0, 0, M, N, chunks, false, 1.0f, (float2 *)C, N, splits, partial, err, s, 0,
+                   chunks == 1 ? (K + 31) / 32 * 32 : 0);  // a single short chunk multiplies only its K range
   if (e == cudaSuccess) e = from_df_rect(M, N, C, N, s);
   return e == cudaSuccess ? GPC_OK : GPC_ERR_CUDA;
 }

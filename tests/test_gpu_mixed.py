@@ -44,8 +44,8 @@ def test_ozaki_exact_on_16_bit_operands(M, N, K):
     assert np.array_equal(C, exact.astype(np.float64) * 2.0 ** -32)
 
 
-@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (64, 64, 64), (128, 128, 128), (200, 130, 129),
-                                   (300, 257, 513), (128, 1000, 4096)])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (64, 64, 64), (129, 65, 33), (300, 200, 96), (128, 128, 128),
+                                   (200, 130, 129), (300, 257, 513), (128, 1000, 4096)])
 def test_ozaki_accuracy_random(M, N, K):
     g = np.random.default_rng(M + N + K)
     A = g.standard_normal((M, K))
