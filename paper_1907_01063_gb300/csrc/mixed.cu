@@ -106,22 +106,34 @@ cudaError_t chol_mixed(int n, double *L, long long ldl, void *ws, int *info, cud
     if (nb > MH) {
       // Two 64-wide steps: factor and solve the left half, update the right
       // half of the block column with it (split-BF16, K = 64), then factor and
-      // solve the right half.  The FP64 work of the block column halves.
-      const int hb = nb - MH, ma = n - k0 - MH;
-      double *Ab = A11 + (long long)MH * ldl + MH;  // right half's diagonal block
+      // solve the right half.  The FP64 work of the block column halves.  The
+      // diagonal block's share of this (both halves' factors and the 64 x 64
+      // update between them, a chain of small launches on a few SMs) runs
+      // first, while the previous step's trailing update may still hold the
+      // rest of the GPU; the panel rows below follow.
+      const int hb = nb - MH;
+      double *Aba = A11 + (long long)MH * ldl;  // right half's rows, left half's columns
+      double *Ab = Aba + MH;                    // right half's diagonal block
+      const size_t sb_small = slice_bytes(MH, 1);
+      SliceBuf Sba = slice_view((char *)sbuf + slice_bytes(n, 1) - sb_small, hb, 1);
       TRY(potrf_diag(MH, A11, ldl, info, k0, s, true));
+      TRY(trsm_rows(hb, MH, Aba, ldl, A11, ldl, 0, s, true));
+      TRY(split_operand(Aba, ldl, 1, hb, MH, MH, Sba, s));
+      TRY(ozaki_gemm(Sba, 0, 0, Sba, 0, 0, hb, hb, 1, true, -1.0f, (float2 *)Ab, ldl, 1, nullptr,
+                     info ? info + 1 : nullptr, s, 0, MH));
+      TRY(potrf_diag(hb, Ab, ldl, info, k0 + MH, s, true));
       if (rest_pending) {
         TRY(cudaStreamWaitEvent(s, aux->ev_rest, 0));
         rest_pending = false;
       }
-      TRY(trsm_rows(ma, MH, A11 + (long long)MH * ldl, ldl, A11, ldl, 0, s, true));
-      SliceBuf Sh = slice_view(sbuf, ma, 1);
-      TRY(split_operand(A11 + (long long)MH * ldl, ldl, 1, ma, MH, MH, Sh, s));
-      TRY(ozaki_gemm(Sh, 0, 0, Sh, 0, 0, ma, hb, 1, true, -1.0f, (float2 *)Ab, ldl, 1, nullptr,
-                     info ? info + 1 : nullptr, s, 0, MH));
-      TRY(potrf_diag(hb, Ab, ldl, info, k0 + MH, s, true));
       if (m <= 0) continue;
-      TRY(trsm_rows(m, hb, Ab + (long long)hb * ldl, ldl, Ab, ldl, 0, s, true));
+      double *Ca = A11 + (long long)nb * ldl;  // panel rows below the diagonal block, left half
+      TRY(trsm_rows(m, MH, Ca, ldl, A11, ldl, 0, s, true));
+      SliceBuf Sc = slice_view(sbuf, m, 1);
+      TRY(split_operand(Ca, ldl, 1, m, MH, MH, Sc, s));
+      TRY(ozaki_gemm(Sc, 0, 0, Sba, 0, 0, m, hb, 1, false, -1.0f, (float2 *)(Ca + MH), ldl, 1, nullptr,
+                     info ? info + 1 : nullptr, s, 0, MH));
+      TRY(trsm_rows(m, hb, Ca + MH, ldl, Ab, ldl, 0, s, true));
     } else {
       TRY(potrf_diag(nb, A11, ldl, info, k0, s, true));
       if (rest_pending) {
