@@ -422,6 +422,11 @@ def main():
     fp64_peak = gp.fp64_peak_gflops(dev)
     nominal_fp64 = peaks.get("bf16_tflops", 1900.0) * 1e3 * 1.25 / 2250.0
 
+    # DRAM bytes (read + write) per launch of the split product, averaged over the
+    # 1015 launches of one mixed step at n = 16384, from the ncu capture summarised
+    # in profiles/gp_step_mixed_n16384_launches.md; other sizes have no capture.
+    ozaki_traffic = {16384: 237.17e6}
+
     def roofline(res):
         trace = {k: dict(v, ms=v["ms"] / res["trace_steps"], flops=v["flops"] / res["trace_steps"],
                          bytes=v["bytes"] / res["trace_steps"], launches=v["launches"] / res["trace_steps"])
@@ -433,14 +438,15 @@ def main():
             achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12 if dom["ms"] else 0.0
             return {"kernel": "ozaki_gemm_kernel (tcgen05 BF16 slice products, 15 per FP64 product)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "launches_per_step": dom["launches"],
+                    "frac": achieved / peak, "traffic": ozaki_traffic.get(n), "launches_per_step": dom["launches"],
                     "avg_launch_ms": avg, "peak_source": "of measured: MEASURED_PEAKS bf16_tflops_sustained",
+                    "traffic_unit": "bytes per launch (ncu, averaged over a step's launches)",
                     "fp64_equivalent_gflops": dom["flops"] / 15.0 / (dom["ms"] / 1e3) / 1e9}
         if dom_name in ("gemm_f64", "diag", "trsm"):
             achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0
             names = {"gemm_f64": "gemm_f64_kernel (FP64 mma.sync m16n8k16)",
                      "diag": "diagonal-block kernels (potrf_diag, trtri_batched)",
-                     "trsm": "trsm_rows_kernel (FP64 panel solves)"}
+                     "trsm": "trsm_quad_kernel (FP64 panel solves)"}
             return {"kernel": names[dom_name],
                     "bound": "tensor" if dom_name == "gemm_f64" else "alu", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
                     "frac": achieved / fp64_peak, "traffic": None, "launches_per_step": dom["launches"],
