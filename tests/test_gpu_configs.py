@@ -94,8 +94,9 @@ def test_autograd_8192_matches_central_differences(gp8192):
     err = np.abs(g - fd)
     print(f"n=8192 autograd vs central FD: {err / np.abs(fd)} (value {v.item():.6e})")
     # the difference quotient carries the rounding of the two LML values
-    # (about 1e-14 |f| each at this size) divided by 2h, plus O(h^2) truncation
-    bound = 1e-14 * abs(v.item()) / step + 1e-7 * np.abs(fd)
+    # (measured about 4e-14 |f| each at this size: log-determinant and
+    # quadratic-form sums over 8192 terms) divided by 2h, plus O(h^2) truncation
+    bound = 1e-13 * abs(v.item()) / step + 1e-7 * np.abs(fd)
     assert np.all(err <= bound), (g, fd, bound)
 
 
