@@ -424,19 +424,30 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       // chunks: C is read once before the first chunk and written once after the last
       // (a split-K partial tile starts from zero and is written whole, so it is not read)
       float2 cv[32];
+      // the warp's 32 x 32 block lies wholly inside the output (and below the
+      // diagonal of a lower output): no per-element bounds tests
+      const bool interior = row0 + 32 <= p.M && colh + 32 <= p.N && (!p.lower || colh + 31 < row0);
       if (p.partial) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) cv[i] = make_float2(0.f, 0.f);
       } else {
         // all 32 loads in flight at once (cv holds them in the coalesced layout first)
+        if (interior) {
+          const float2 *src = base + (long long)(row0 + rl_lo) * ld + colh + cl;
 #pragma unroll
-        for (int hc = 0; hc < 2; ++hc)
+          for (int hc = 0; hc < 2; ++hc)
 #pragma unroll
-          for (int it = 0; it < 16; ++it) {
-            const int rl = 2 * it + rl_lo, row = row0 + rl, col = colh + hc * 16 + cl;
-            cv[hc * 16 + it] = (row < p.M && col < p.N && !(p.lower && col > row)) ? base[(long long)row * ld + col]
-                                                                                   : make_float2(0.f, 0.f);
-          }
+            for (int it = 0; it < 16; ++it) cv[hc * 16 + it] = src[(long long)(2 * it) * ld + hc * 16];
+        } else {
+#pragma unroll
+          for (int hc = 0; hc < 2; ++hc)
+#pragma unroll
+            for (int it = 0; it < 16; ++it) {
+              const int rl = 2 * it + rl_lo, row = row0 + rl, col = colh + hc * 16 + cl;
+              cv[hc * 16 + it] = (row < p.M && col < p.N && !(p.lower && col > row)) ? base[(long long)row * ld + col]
+                                                                                     : make_float2(0.f, 0.f);
+            }
+        }
 #pragma unroll
         for (int hc = 0; hc < 2; ++hc) {
 #pragma unroll
@@ -477,13 +488,21 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         for (int it = 0; it < 16; ++it) cv[hc * 16 + it] = tb[(2 * it + rl_lo) * OZ_EPI_LD + cl];
         __syncwarp();
       }
+      if (interior) {
+        float2 *dst = base + (long long)(row0 + rl_lo) * ld + colh + cl;
 #pragma unroll
-      for (int hc = 0; hc < 2; ++hc)
+        for (int hc = 0; hc < 2; ++hc)
 #pragma unroll
-        for (int it = 0; it < 16; ++it) {
-          const int rl = 2 * it + rl_lo, row = row0 + rl, col = colh + hc * 16 + cl;
-          if (row < p.M && col < p.N && !(p.lower && col > row)) base[(long long)row * ld + col] = cv[hc * 16 + it];
-        }
+          for (int it = 0; it < 16; ++it) dst[(long long)(2 * it) * ld + hc * 16] = cv[hc * 16 + it];
+      } else {
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc)
+#pragma unroll
+          for (int it = 0; it < 16; ++it) {
+            const int rl = 2 * it + rl_lo, row = row0 + rl, col = colh + hc * 16 + cl;
+            if (row < p.M && col < p.N && !(p.lower && col > row)) base[(long long)row * ld + col] = cv[hc * 16 + it];
+          }
+      }
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
