@@ -67,8 +67,9 @@ constexpr int OZ_B_STAGE = OZ_S * OZ_B_PLANE;            // 20 KiB
 constexpr int OZ_ACCS = 4;                               // G2, G3, G4, G56
 constexpr int OZ_ACC_COLS = OZ_ACCS * OZ_BN;             // one accumulator set
 constexpr int OZ_TMEM_COLS = 512;
-constexpr int OZ_EPI_LD = 17;                           // padded row of an epilogue transpose buffer (float2)
-constexpr int OZ_EPI_BUF = 32 * OZ_EPI_LD * 8;           // 32 rows x 16 columns of double-floats per warp
+constexpr int OZ_EPI_LD = 17;                           // padded row of an epilogue transpose buffer (float2, 8-byte path)
+constexpr int OZ_EPI_LD2 = 18;                          // the same for the 16-byte path (rows 16-byte aligned)
+constexpr int OZ_EPI_BUF = 32 * OZ_EPI_LD2 * 8;          // 32 rows x 16 columns of double-floats per warp
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + OZ_EPI_WARPS * OZ_EPI_BUF +
                               1024 /*barriers*/ + 1024 /*align*/;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
@@ -431,9 +432,39 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       // the warp's 32 x 32 block lies wholly inside the output (and below the
       // diagonal of a lower output): no per-element bounds tests
       const bool interior = row0 + 32 <= p.M && colh + 32 <= p.N && (!p.lower || colh + 31 < row0);
+      // ... and its rows are 16-byte aligned: pairs of double-floats per access,
+      // half the memory instructions
+      const bool vec = interior && (ld & 1) == 0 && ((uintptr_t)base & 15) == 0;
+      const int rq = lane >> 3, cp = lane & 7;  // 16-byte layout: 4 rows x 8 column pairs per access
       if (p.partial) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) cv[i] = make_float2(0.f, 0.f);
+      } else if (vec) {
+        const float2 *src = base + (long long)(row0 + rq) * ld + colh + 2 * cp;
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc)
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const float4 v = *reinterpret_cast<const float4 *>(src + (long long)(4 * it) * ld + hc * 16);
+            cv[hc * 16 + 2 * it] = make_float2(v.x, v.y);
+            cv[hc * 16 + 2 * it + 1] = make_float2(v.z, v.w);
+          }
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc) {
+#pragma unroll
+          for (int it = 0; it < 8; ++it)
+            *reinterpret_cast<float4 *>(&tb[(4 * it + rq) * OZ_EPI_LD2 + 2 * cp]) =
+                make_float4(cv[hc * 16 + 2 * it].x, cv[hc * 16 + 2 * it].y, cv[hc * 16 + 2 * it + 1].x,
+                            cv[hc * 16 + 2 * it + 1].y);
+          __syncwarp();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 v = *reinterpret_cast<const float4 *>(&tb[lane * OZ_EPI_LD2 + 2 * c]);
+            cv[hc * 16 + 2 * c] = make_float2(v.x, v.y);
+            cv[hc * 16 + 2 * c + 1] = make_float2(v.z, v.w);
+          }
+          __syncwarp();
+        }
       } else {
         // all 32 loads in flight at once (cv holds them in the coalesced layout first)
         if (interior) {
@@ -483,6 +514,24 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         if (++buf == 2) { buf = 0; tphase ^= 1; }
       }
       if (!ok) break;
+      if (vec) {
+        float2 *dst = base + (long long)(row0 + rq) * ld + colh + 2 * cp;
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<float4 *>(&tb[lane * OZ_EPI_LD2 + 2 * c]) =
+                make_float4(cv[hc * 16 + 2 * c].x, cv[hc * 16 + 2 * c].y, cv[hc * 16 + 2 * c + 1].x,
+                            cv[hc * 16 + 2 * c + 1].y);
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; ++it)
+            *reinterpret_cast<float4 *>(dst + (long long)(4 * it) * ld + hc * 16) =
+                *reinterpret_cast<const float4 *>(&tb[(4 * it + rq) * OZ_EPI_LD2 + 2 * cp]);
+          __syncwarp();
+        }
+        continue;
+      }
 #pragma unroll
       for (int hc = 0; hc < 2; ++hc) {
 #pragma unroll
