@@ -60,6 +60,7 @@ def parse_args():
     p.add_argument("--no-batched", action="store_true", help="skip the batched-GP workload")
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-graph", action="store_true", help="time direct launches instead of a CUDA graph replay")
     return p.parse_args()
 
 
@@ -105,12 +106,15 @@ def workload(n: int, d: int):
     return X, y, (alpha, rho, sigma), 0.0
 
 
-def describe(n, d, hyp, b, precision):
-    return {"workload": f"GP LML + gradient, SE kernel, n={n}, d={d}, cond~1e5 ({precision})",
-            "n": n, "d": d, "alpha": hyp[0], "rho": hyp[1], "sigma": round(hyp[2], 6),
-            "block": b, "precision": precision,
-            "l2": "inputs larger than L2 (K, L, Kbar are 8 n^2 bytes each)",
-            "parallelism": "replicas"}
+def describe(n, d, hyp, b, precision, cuda_graph=None):
+    out = {"workload": f"GP LML + gradient, SE kernel, n={n}, d={d}, cond~1e5 ({precision})",
+           "n": n, "d": d, "alpha": hyp[0], "rho": hyp[1], "sigma": round(hyp[2], 6),
+           "block": b, "precision": precision,
+           "l2": "inputs larger than L2 (K, L, Kbar are 8 n^2 bytes each)",
+           "parallelism": "replicas"}
+    if cuda_graph is not None:
+        out["timed"] = "one step captured in a CUDA graph, replayed per step" if cuda_graph else "direct launches"
+    return out
 
 
 # ---------------------------------------------------------------- clocks
@@ -342,17 +346,44 @@ def main():
             res = step(Xd, yd)
         barrier()
         gp.check_info(info, f"warm-up step ({prec})")
+        launches0 = gp.launch_count()
+        res = step(Xd, yd)
+        launches_per_step = gp.launch_count() - launches0
+        # One step captured once in a CUDA graph and replayed: the same kernels
+        # with the same arguments, without the per-launch gaps of ~4000 small
+        # launches (the library enqueues everything on the caller's stream and
+        # joins its auxiliary stream back with events, so it captures whole).
+        graph = None
+        if not args.no_graph:
+            try:
+                side = torch.cuda.Stream()
+                side.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(side):
+                    step(Xd, yd)
+                torch.cuda.current_stream().wait_stream(side)
+                torch.cuda.synchronize()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    res = step(Xd, yd)
+                graph.replay()
+                torch.cuda.synchronize()
+            except RuntimeError as exc:  # capture refused: time direct launches instead
+                print(f"bench: CUDA graph capture failed ({exc}); timing direct launches", file=sys.stderr)
+                graph = None
+                res = step(Xd, yd)
         clocks = ClockSampler(local)
         clocks.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        launches0 = gp.launch_count()
         barrier()
         ev0.record(stream)
         for _ in range(args.steps):
-            res = step(Xd, yd)
+            if graph is not None:
+                graph.replay()
+            else:
+                res = step(Xd, yd)
         ev1.record(stream)
         barrier()
-        launches = gp.launch_count() - launches0
+        launches = launches_per_step * args.steps
         t_ms = max_over_ranks(ev0.elapsed_time(ev1))
         # per-launch device times for the roofline: the same steps again with an
         # event pair around every launch (kept out of the region above because
@@ -373,6 +404,7 @@ def main():
         if st[1] not in (gp.GPC_OK, gp.GPC_ERR_NO_CONVERGENCE):
             gp.check_info(info, f"timed step ({prec})")
         out = {"prec": prec, "block": b, "step_flops": step_flops, "t_ms": t_ms, "launches": launches,
+               "cuda_graph": graph is not None,
                "trace": trace, "trace_steps": trace_steps, "traced_ms_per_step": traced_ms, "clocks": clk, "value": world * args.steps * step_flops / (t_ms / 1e3) / 1e9,
                "lml": res["value"].item(), "logdet": res["logdet"].item(), "grad": g3.tolist(),
                "refine_status": st[1]}
@@ -483,7 +515,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": head["t_ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x5+f64" if prec == "mixed" else "f64", "data": "synthetic",
-        "config": describe(n, d, hyp, head["block"], prec),
+        "config": describe(n, d, hyp, head["block"], prec, head["cuda_graph"]),
         "e2e": head["e2e"],
         "gpu_launches": head["launches"],
         "roofline": roofline(head),
