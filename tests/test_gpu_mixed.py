@@ -196,3 +196,45 @@ def test_gp_step_mixed_covariance_end_to_end():
     Kbar = gp.gp_lml_grad(res["L"], res["alpha"], 1.0, precision="mixed")
     g = gp.se_hyper_grad(dev(X), a, r, s, Kbar, precision="mixed").cpu().numpy()
     assert rel(g, ref["grad"]) <= 1e-7
+
+
+def test_gp_step_captures_in_a_cuda_graph():
+    # the whole step (covariance, mixed factorisation with the auxiliary
+    # stream's lookahead, refinement, adjoint, gradient) captures into one
+    # graph whose replay reproduces the direct launches bit for bit
+    n = 777
+    X, y, (a, r, s) = cond_problem(n)
+    Xd, yd = dev(X), dev(y)
+    K = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    L, Kbar = torch.empty_like(K), torch.empty_like(K)
+    ws = gp.workspace(n, "mixed", torch.device("cuda"))
+    hws = torch.empty(gp.se_hyper_grad_workspace_size(n), dtype=torch.uint8, device="cuda")
+    info = gp.new_info(torch.device("cuda"))
+    g3 = torch.empty(3, dtype=torch.float64, device="cuda")
+    val = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def step():
+        gp.se_cov(Xd, a, r, s, 0.0, out=K, precision="mixed")
+        res = gp.gp_lml(K, yd, "mixed", L=L, ws=ws, info=info, check=False)
+        gp.gp_lml_grad(L, res["alpha"], 1.0, "mixed", out=Kbar, ws=ws)
+        gp.se_hyper_grad(Xd, a, r, s, Kbar, ws=hws, out=g3, precision="mixed")
+        val.copy_(res["value"].reshape(1))
+
+    step()
+    torch.cuda.synchronize()
+    v0, g0, L0 = val.clone(), g3.clone(), L.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    val.zero_()
+    g3.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert info.tolist()[1] == gp.GPC_OK
+    assert torch.equal(val, v0) and torch.equal(g3, g0) and torch.equal(L, L0)
