@@ -193,6 +193,34 @@ def cpu_baseline(ns: int, d: int, hyp):
 
 
 # ---------------------------------------------------------------- distributed
+def make_sync(world, device):
+    """Barrier and max-over-ranks around the timed regions: NCCL between GPU
+    ranks in the benchmark, gloo between CPU ranks in the tests."""
+    import torch
+    import torch.distributed as dist
+
+    def barrier():
+        if device.type == "cuda":
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    return barrier, max_over_ranks
+
+
+def whole_job_rate(world, steps, units_per_step, t_ms):
+    """Units per second over all ranks: every rank processes its own copy of
+    the workload (replicas), and the slowest rank's time counts."""
+    return world * steps * units_per_step / (t_ms / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -276,8 +304,8 @@ def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned, pr
     t_ms = max_over_ranks(e0.elapsed_time(e1))
     info = b.info.cpu().numpy()
     return {"workload": f"{args.batch} GPs, n_i ~ U{{64..1024}}, d=4, SE kernel, rho_i ~ U(0.2,2), sigma=0.1 ({prec})",
-            "value": world * args.steps * flops / (t_ms / 1e3) / 1e9, "unit": "GFLOP/s",
-            "gp_per_s": world * args.steps * args.batch / (t_ms / 1e3), "ms_per_step": t_ms / args.steps,
+            "value": whole_job_rate(world, args.steps, flops, t_ms) / 1e9, "unit": "GFLOP/s",
+            "gp_per_s": whole_job_rate(world, args.steps, args.batch, t_ms), "ms_per_step": t_ms / args.steps,
             "flops_per_step": flops, "sum_n": int(sum(sizes)), "max_n": int(max(sizes)),
             "cuda_graph": True, "kernels_per_step": 2, "block": nb,
             "all_ok": bool((info[:, 1] == 0).all()),
@@ -319,17 +347,7 @@ def main():
     g3 = torch.empty(3, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+    barrier, max_over_ranks = make_sync(world, dev)
 
     def run(prec):
         b = gp.get_tuning(gp.GPC_TUNE_BLOCK) if prec == "fp64" else 128
@@ -405,7 +423,7 @@ def main():
             gp.check_info(info, f"timed step ({prec})")
         out = {"prec": prec, "block": b, "step_flops": step_flops, "t_ms": t_ms, "launches": launches,
                "cuda_graph": graph is not None,
-               "trace": trace, "trace_steps": trace_steps, "traced_ms_per_step": traced_ms, "clocks": clk, "value": world * args.steps * step_flops / (t_ms / 1e3) / 1e9,
+               "trace": trace, "trace_steps": trace_steps, "traced_ms_per_step": traced_ms, "clocks": clk, "value": whole_job_rate(world, args.steps, step_flops, t_ms) / 1e9,
                "lml": res["value"].item(), "logdet": res["logdet"].item(), "grad": g3.tolist(),
                "refine_status": st[1]}
         # end to end: pinned host inputs in, scalars out, every step
@@ -426,7 +444,7 @@ def main():
         e1.record(stream)
         barrier()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1))
-        out["e2e"] = {"value": world * e2e_steps * step_flops / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+        out["e2e"] = {"value": whole_job_rate(world, e2e_steps, step_flops, e2e_ms) / 1e9, "unit": "GFLOP/s",
                       "h2d_bytes_per_step": Xh.numel() * 8 + yh.numel() * 8, "d2h_bytes_per_step": 32,
                       "ms_per_step": e2e_ms / e2e_steps}
         return out
