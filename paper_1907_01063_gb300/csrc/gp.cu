@@ -439,6 +439,9 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
   const int r = threadIdx.x % TS, q = threadIdx.x / TS;
   bool aborted = false;
   double acc = 0.0, lv[TW];
+  // this sub-block's right-hand side, read now so that no global load is left
+  // on the chain after the last wait
+  const double rhs = (q == 0 && r < nb) ? x[i0 + r] : 0.0;
 
   if (!trans) {
     // lv[u] = L[i0 + r][c0 + q TW + u] for the next sub-block c
@@ -478,7 +481,7 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
     }
     red[q][r] = acc;
     __syncthreads();  // red and dinv_s complete
-    if (!aborted && q == 0 && r < nb) vbuf[r] = x[i0 + r] - ((red[0][r] + red[1][r]) + (red[2][r] + red[3][r]));
+    if (!aborted && q == 0 && r < nb) vbuf[r] = rhs - ((red[0][r] + red[1][r]) + (red[2][r] + red[3][r]));
     __syncthreads();
     double p[4] = {0.0, 0.0, 0.0, 0.0};
     if (!aborted && r < nb) {
@@ -534,7 +537,7 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
     }
     red[q][r] = acc;
     __syncthreads();  // red and dinv_s complete
-    if (!aborted && q == 0 && r < nb) vbuf[r] = x[i0 + r] - ((red[0][r] + red[1][r]) + (red[2][r] + red[3][r]));
+    if (!aborted && q == 0 && r < nb) vbuf[r] = rhs - ((red[0][r] + red[1][r]) + (red[2][r] + red[3][r]));
     __syncthreads();
     double p[4] = {0.0, 0.0, 0.0, 0.0};
     if (!aborted && r < nb) {
