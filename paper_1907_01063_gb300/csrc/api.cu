@@ -262,9 +262,8 @@ int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double
   ApiWs w = carve(ws, n, precision);
   double *z = w.vec;
   cudaError_t e = ltv(n, L, ldl, alpha, z, w.core, stream);
-  if (e == cudaSuccess) e = lml_lbar(n, L, ldl, alpha, z, gbar, Kbar, ldkb, stream);
+  if (e == cudaSuccess) e = lml_lbar(n, L, ldl, alpha, z, gbar, Kbar, ldkb, stream, precision == GPC_MIXED);
   if (precision == GPC_MIXED) {
-    if (e == cudaSuccess) e = to_df_lower(n, Kbar, ldkb, Kbar, ldkb, stream);
     if (e == cudaSuccess) e = chol_adjoint_mixed(n, L, ldl, Kbar, ldkb, w.core, w.flags, stream);
   } else {
     if (e == cudaSuccess) e = chol_adjoint_fp64(n, L, ldl, Kbar, ldkb, w.core, stream);

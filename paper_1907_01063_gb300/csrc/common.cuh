@@ -134,8 +134,9 @@ size_t ltv_workspace_bytes(int n);
 cudaError_t ltv(int n, const double *L, long long ldl, const double *v, double *z, void *ws,
                 cudaStream_t s);
 // Lbar = gbar (tril(alpha z^T) - diag(1/L_ii)), strict upper zero.
+// df: write L-bar in double-float storage (the mixed adjoint's input format).
 cudaError_t lml_lbar(int n, const double *L, long long ldl, const double *alpha,
-                     const double *z, double gbar, double *Lbar, long long ldlb, cudaStream_t s);
+                     const double *z, double gbar, double *Lbar, long long ldlb, cudaStream_t s, bool df = false);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

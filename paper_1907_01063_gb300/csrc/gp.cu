@@ -602,7 +602,7 @@ __global__ void ltv_reduce_kernel(int n, int chunks, const double *partial, doub
 }
 
 __global__ void lml_lbar_kernel(int n, const double *L, long long ldl, const double *alpha,
-                                const double *z, double gbar, double *Lbar, long long ldlb) {
+                                const double *z, double gbar, double *Lbar, long long ldlb, int df) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * n) return;
   const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
@@ -612,7 +612,12 @@ __global__ void lml_lbar_kernel(int n, const double *L, long long ldl, const dou
     if (i == j) v -= 1.0 / L[(long long)i * ldl + i];
     v *= gbar;
   }
-  Lbar[(long long)i * ldlb + j] = v;
+  if (df) {  // double-float storage (FP32 hi + lo in the 8 bytes), as the mixed adjoint takes it
+    const float h = __double2float_rn(v);
+    reinterpret_cast<float2 *>(Lbar)[(long long)i * ldlb + j] = make_float2(h, __double2float_rn(v - (double)h));
+  } else {
+    Lbar[(long long)i * ldlb + j] = v;
+  }
 }
 
 bool g_attr[64][4];
@@ -893,12 +898,12 @@ cudaError_t ltv(int n, const double *L, long long ldl, const double *v, double *
 }
 
 cudaError_t lml_lbar(int n, const double *L, long long ldl, const double *alpha, const double *z,
-                     double gbar, double *Lbar, long long ldlb, cudaStream_t s) {
+                     double gbar, double *Lbar, long long ldlb, cudaStream_t s, bool df) {
   if (n <= 0) return cudaSuccess;
   const long long total = (long long)n * n;
   GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (double)total, s,
              lml_lbar_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, L, ldl, alpha, z,
-                                                                             gbar, Lbar, ldlb));
+                                                                             gbar, Lbar, ldlb, df ? 1 : 0));
   return cudaGetLastError();
 }
 
