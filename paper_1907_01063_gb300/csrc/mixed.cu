@@ -3,14 +3,20 @@
 // Same block algorithms as the FP64 path (Section 3.3; see chol.cu), with the
 // O(n^3) products moved to split-BF16 tensor-core products (ozaki.cu):
 //   forward: the trailing update A22 -= L21 L21^T;
-//   adjoint: Bbar -= Cbar R and Rbar -= [Dbar; Cbar]^T [R; B].
-// The diagonal blocks, their inverses, the panel products with the inverses
-// and the Dbar update stay FP64.  Matrices that the split products update
-// (the trailing part of L, the not-yet-final part of Lbar) are held in
+//   adjoint: Bbar -= Cbar R, Dbar -= Cbar^T C and Rbar -= [Dbar; Cbar]^T [R; B].
+// The diagonal-block factors, their inverses, the panel solves and the Dbar
+// symbolic step stay FP64.  Matrices that the split products update (the
+// trailing part of L, the not-yet-final part of Lbar) are held in
 // double-float storage (FP32 hi + lo in each 8-byte element); each block
-// column is converted back to FP64 in place when it becomes current, so every
-// output is FP64 at the end.  The block size is fixed to the 128-wide chunk of
-// the split products so chunk boundaries line up with the sweep's blocks.
+// column is read as FP64 when it becomes current (the diagonal factor and the
+// panel solves convert it as they load it), so every output is FP64 at the
+// end.  The sweeps move by the 128-wide chunk of the split products so chunk
+// boundaries line up with the blocks; within a block column the FP64 steps
+// work on 64-wide halves (the blocked algorithm with b = 64 for its FP64
+// steps, the updates of two consecutive 64-steps merged into one K = 128
+// product), which halves the FP64 work of the panel solves and quarters that
+// of the diagonal factors -- the FP64 pipe, not the tensor cores, bounds the
+// critical path on this part.
 #include "common.cuh"
 
 #include <algorithm>
