@@ -73,7 +73,7 @@ def se_problem(n, d=3, seed=0, jitter=1e-6, rho=1.0, sigma=0.3):
     return X, O.se_cov(X, 1.0, rho, sigma, jitter)
 
 
-MIXED_SIZES = [1, 2, 17, 127, 128, 129, 200, 257, 300, 513]
+MIXED_SIZES = [1, 2, 17, 64, 65, 96, 127, 128, 129, 191, 200, 257, 300, 513]
 
 
 @pytest.mark.parametrize("n", MIXED_SIZES)
