@@ -282,3 +282,72 @@ void oracle_se_hyper_grad(int n, int d, const double *X, int ldx, double alpha, 
   grad3[1] = gr;
   grad3[2] = gs;
 }
+
+/*
+ * Lower-triangular inverse X = L^{-1} (Section 3.2, solving triangular
+ * systems, primitive function: the result the divide-and-conquer inverse
+ * reaches).  Written as its definition L X = I, solved one column at a time
+ * by forward substitution:
+ *   X_ij = 0 (i < j),  X_jj = 1 / L_jj,
+ *   X_ij = -(sum_{k=j}^{i-1} L_ik X_kj) / L_ii   (i > j, k ascending).
+ * Only the lower triangle of L is read; the strict upper triangle of X is set
+ * to zero.  X must not overlap L.
+ */
+void oracle_tri_inverse(int n, const double *L, int ldl, double *X, int ldx) {
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < j; ++i) AT(X, ldx, i, j) = 0.0;
+    AT(X, ldx, j, j) = 1.0 / AT(L, ldl, j, j);
+    for (int i = j + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += AT(L, ldl, i, k) * AT(X, ldx, k, j);
+      AT(X, ldx, i, j) = -s / AT(L, ldl, i, i);
+    }
+  }
+}
+
+/*
+ * C = L^{-1} B for lower-triangular L (n x n) and B (n x m): Section 3.2's
+ * general triangular solver (which the GPU reaches through the inverse and a
+ * product), written as forward substitution per column of B:
+ *   C_ij = (B_ij - sum_{k<i} L_ik C_kj) / L_ii   (k ascending).
+ * C may alias B.
+ */
+void oracle_tri_solve(int n, int m, const double *L, int ldl, const double *B, int ldb,
+                      double *C, int ldc) {
+  for (int j = 0; j < m; ++j) {
+    for (int i = 0; i < n; ++i) {
+      double s = AT(B, ldb, i, j);
+      for (int k = 0; k < i; ++k) s -= AT(L, ldl, i, k) * AT(C, ldc, k, j);
+      AT(C, ldc, i, j) = s / AT(L, ldl, i, i);
+    }
+  }
+}
+
+/*
+ * Reverse mode of C = L^{-1} B (Section 3.2, reverse mode function) for a
+ * scalar f with Cbar = df/dC.  From dC = L^{-1} (dB - dL C):
+ *   Bbar = L^{-T} Cbar                (back substitution per column)
+ *   Lbar_ij = -sum_t Bbar_it C_jt     (i >= j; strict upper set to zero)
+ * i.e. Lbar = -tril(Bbar C^T): the gradient with respect to the lower-triangle
+ * entries of L, the only ones the solve reads.  The paper prints the adjoint
+ * system with A rather than A^T; the transpose is what the differential
+ * gives (the two agree only for symmetric A).
+ */
+void oracle_tri_solve_adjoint(int n, int m, const double *L, int ldl, const double *C, int ldc,
+                              const double *Cbar, int ldcb, double *Bbar, int ldbb,
+                              double *Lbar, int ldlb) {
+  for (int j = 0; j < m; ++j) {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = AT(Cbar, ldcb, i, j);
+      for (int k = i + 1; k < n; ++k) s -= AT(L, ldl, k, i) * AT(Bbar, ldbb, k, j);
+      AT(Bbar, ldbb, i, j) = s / AT(L, ldl, i, i);
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      if (j <= i)
+        for (int t = 0; t < m; ++t) s -= AT(Bbar, ldbb, i, t) * AT(C, ldc, j, t);
+      AT(Lbar, ldlb, i, j) = s;
+    }
+}

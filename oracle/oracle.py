@@ -56,6 +56,12 @@ def _load():
         lib.oracle_lml_lbar.restype = None
         lib.oracle_se_hyper_grad.argtypes = [i, i, _D, i, d, d, d, _D, i, _D]
         lib.oracle_se_hyper_grad.restype = None
+        lib.oracle_tri_inverse.argtypes = [i, _D, i, _D, i]
+        lib.oracle_tri_inverse.restype = None
+        lib.oracle_tri_solve.argtypes = [i, i, _D, i, _D, i, _D, i]
+        lib.oracle_tri_solve.restype = None
+        lib.oracle_tri_solve_adjoint.argtypes = [i, i, _D, i, _D, i, _D, i, _D, i, _D, i]
+        lib.oracle_tri_solve_adjoint.restype = None
         _lib = lib
     return _lib
 
@@ -123,6 +129,49 @@ def trsv(L, x, trans: bool = False) -> np.ndarray:
     out = np.array(x, dtype=np.float64, copy=True)
     _load().oracle_trsv(L.shape[0], _p(L), L.shape[0], _p(out), 1 if trans else 0)
     return out
+
+
+def tri_inverse(L) -> np.ndarray:
+    """L^{-1} of a lower-triangular L, column by column from L X = I."""
+    L = _mat(L)
+    n = L.shape[0]
+    X = np.zeros_like(L)
+    _load().oracle_tri_inverse(n, _p(L), n, _p(X), n)
+    return X
+
+
+def _rect(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        a = a.reshape(-1, 1).copy()
+    if a.ndim != 2:
+        raise ValueError("expected a matrix or a vector")
+    return a
+
+
+def tri_solve(L, B) -> np.ndarray:
+    """C = L^{-1} B (L lower, B n x m) by forward substitution."""
+    L = _mat(L)
+    B = _rect(B)
+    n, m = B.shape
+    if n != L.shape[0]:
+        raise ValueError("shape mismatch")
+    C = np.zeros_like(B)
+    _load().oracle_tri_solve(n, m, _p(L), n, _p(B), m, _p(C), m)
+    return C
+
+
+def tri_solve_adjoint(L, C, Cbar):
+    """(Bbar, Lbar) of C = L^{-1} B given Cbar: L^{-T} Cbar and -tril(Bbar C^T)."""
+    L = _mat(L)
+    C, Cbar = _rect(C), _rect(Cbar)
+    n, m = C.shape
+    if Cbar.shape != C.shape or n != L.shape[0]:
+        raise ValueError("shape mismatch")
+    Bbar = np.zeros_like(C)
+    Lbar = np.zeros_like(L)
+    _load().oracle_tri_solve_adjoint(n, m, _p(L), n, _p(C), m, _p(Cbar), m, _p(Bbar), m, _p(Lbar), n)
+    return Bbar, Lbar
 
 
 def se_cov(X, alpha: float, rho: float, sigma: float, jitter: float = 0.0,

@@ -296,3 +296,107 @@ def test_hyper_grad_sigma_only_on_diagonal():
     Kbar = np.tril(np.ones((n, n)))
     g = O.se_hyper_grad(X, 1.0, 1.0, 0.25, Kbar)
     assert abs(g[2] - n * 2 * 0.25) < 1e-15
+
+
+# ---------------------------------------------------------------- triangular inverse and solve
+def rand_lower(n, seed, diag=2.0):
+    rng = np.random.default_rng(seed)
+    return np.tril(rng.standard_normal((n, n)) / math.sqrt(n)) + np.diag(diag + rng.random(n))
+
+
+def test_tri_inverse_bidiagonal_exact():
+    # unit lower bidiagonal with -1 below the diagonal: the inverse is the
+    # lower triangle of ones, and the inverse of that is the bidiagonal again
+    n = 9
+    E = np.eye(n) - np.eye(n, k=-1)
+    ones = np.tril(np.ones((n, n)))
+    assert np.array_equal(O.tri_inverse(E), ones)
+    assert np.array_equal(O.tri_inverse(ones), E)
+
+
+def test_tri_inverse_2x2_by_hand():
+    # [[a, 0], [c, b]]^{-1} = [[1/a, 0], [-c/(a b), 1/b]]
+    X = O.tri_inverse(np.array([[2.0, 0.0], [3.0, 4.0]]))
+    assert np.array_equal(X, np.array([[0.5, 0.0], [-0.375, 0.25]]))
+
+
+def test_tri_inverse_exact_rational():
+    # exact rational inverse of an integer lower-triangular matrix with unequal
+    # diagonal entries (sympy), brute force on a tiny case
+    sympy = pytest.importorskip("sympy")
+    rng = np.random.default_rng(3)
+    n = 6
+    L = np.tril(rng.integers(-4, 5, (n, n)).astype(float), -1) + np.diag([1.0, 2, 3, 5, 7, 11])
+    Xs = sympy.Matrix(L.astype(int).tolist()).inv()
+    ref = np.array(Xs.tolist(), dtype=float)
+    assert np.abs(O.tri_inverse(L) - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [1, 17, 130])
+def test_tri_inverse_matches_lapack(n):
+    L = rand_lower(n, seed=n)
+    ref, info = scipy.linalg.lapack.dtrtri(L, lower=1)
+    assert info == 0
+    assert rel_fro(O.tri_inverse(L), np.tril(ref)) <= 1e-14
+
+
+def test_tri_inverse_reads_lower_only():
+    L = rand_lower(12, seed=5)
+    J = L + np.triu(np.full((12, 12), 7.0), 1)
+    assert np.array_equal(O.tri_inverse(J), O.tri_inverse(L))
+    assert np.array_equal(np.triu(O.tri_inverse(J), 1), np.zeros((12, 12)))
+
+
+def test_tri_solve_first_differences_exact():
+    # L = lower ones: L^{-1} B takes first differences of the rows of B
+    n, m = 11, 4
+    rng = np.random.default_rng(0)
+    B = rng.integers(-50, 50, (n, m)).astype(float)
+    ref = B - np.vstack([np.zeros((1, m)), B[:-1]])
+    assert np.array_equal(O.tri_solve(np.tril(np.ones((n, n))), B), ref)
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (33, 5), (150, 17)])
+def test_tri_solve_matches_lapack(n, m):
+    L = rand_lower(n, seed=7)
+    B = np.random.default_rng(8).standard_normal((n, m))
+    ref = scipy.linalg.solve_triangular(L, B, lower=True)
+    assert rel_fro(O.tri_solve(L, B), ref) <= 1e-14
+
+
+def test_tri_solve_adjoint_1x1():
+    # c = b / l: bbar = cbar / l, lbar = -cbar b / l^2
+    Bb, Lb = O.tri_solve_adjoint([[4.0]], [[3.0 / 4.0]], [[2.0]])
+    assert Bb[0, 0] == 0.5 and Lb[0, 0] == -2.0 * 3.0 / 16.0
+
+
+@pytest.mark.parametrize("n,m", [(5, 3), (8, 1)])
+def test_tri_solve_adjoint_finite_differences(n, m):
+    # f(L, B) = sum(W * L^{-1} B): central differences in every lower entry of L
+    # and every entry of B, with LAPACK's solve for f
+    rng = np.random.default_rng(n + m)
+    L = rand_lower(n, seed=n)
+    B = rng.standard_normal((n, m))
+    Wt = rng.standard_normal((n, m))
+
+    def f(Lm, Bm):
+        return float(np.sum(Wt * scipy.linalg.solve_triangular(Lm, Bm, lower=True)))
+
+    C = O.tri_solve(L, B)
+    Bb, Lb = O.tri_solve_adjoint(L, C, Wt)
+    h = 1e-6
+    for i in range(n):
+        for j in range(i + 1):
+            Lp, Lm = L.copy(), L.copy()
+            Lp[i, j] += h
+            Lm[i, j] -= h
+            fd = (f(Lp, B) - f(Lm, B)) / (2 * h)
+            assert abs(Lb[i, j] - fd) <= 1e-7 * max(1.0, abs(fd)), (i, j)
+    for i in range(n):
+        for j in range(m):
+            Bp, Bm = B.copy(), B.copy()
+            Bp[i, j] += h
+            Bm[i, j] -= h
+            fd = (f(L, Bp) - f(L, Bm)) / (2 * h)
+            assert abs(Bb[i, j] - fd) <= 1e-7 * max(1.0, abs(fd)), (i, j)
+    assert np.array_equal(np.triu(Lb, 1), np.zeros((n, n)))

@@ -33,6 +33,15 @@ MUTANTS = {
     "hyper_rho_power": ("gr += kb * kf * r2 / (rho * rho * rho);",
                         "gr += kb * kf * r2 / (rho * rho);"),
     "hyper_alpha_factor": ("ga += kb * 2.0 * kf / alpha;", "ga += kb * kf / alpha;"),
+    "trinv_diag_index": ("AT(X, ldx, i, j) = -s / AT(L, ldl, i, i);",
+                         "AT(X, ldx, i, j) = -s / AT(L, ldl, j, j);"),
+    "trinv_dropped_term": ("for (int k = j; k < i; ++k) s += AT(L, ldl, i, k) * AT(X, ldx, k, j);",
+                           "for (int k = j + 1; k < i; ++k) s += AT(L, ldl, i, k) * AT(X, ldx, k, j);"),
+    "trsolve_sign": ("s -= AT(L, ldl, i, k) * AT(C, ldc, k, j);", "s += AT(L, ldl, i, k) * AT(C, ldc, k, j);"),
+    "trsolve_adj_untransposed": ("s -= AT(L, ldl, k, i) * AT(Bbar, ldbb, k, j);",
+                                 "s -= AT(L, ldl, i, k) * AT(Bbar, ldbb, k, j);"),
+    "trsolve_adj_lbar_transposed": ("s -= AT(Bbar, ldbb, i, t) * AT(C, ldc, j, t);",
+                                    "s -= AT(Bbar, ldbb, j, t) * AT(C, ldc, i, t);"),
 }
 
 
