@@ -61,6 +61,9 @@ def parse_args():
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="time direct launches instead of a CUDA graph replay")
+    p.add_argument("--no-tri", action="store_true", help="skip the triangular inverse / solve-adjoint leg")
+    p.add_argument("--tri-m", type=int, default=1024, help="right-hand-side columns of the solve-adjoint leg")
+    p.add_argument("--tri-reps", type=int, default=2)
     return p.parse_args()
 
 
@@ -456,6 +459,62 @@ def main():
 
     results = {p_: run(p_) for p_ in precisions}
 
+    def run_tri():
+        """Section 3.2 at the headline size: the lower-triangular inverse of the
+        step's Cholesky factor, and the reverse mode of C = L^{-1} B for an
+        n x m right-hand side (Bbar = L^{-T} Cbar, Lbar = -tril(Bbar C^T)) from
+        the kept inverse.  Inputs are resident and 2 GiB each (no L2 flush)."""
+        m, reps = args.tri_m, max(1, args.tri_reps)
+        prec0 = precisions[-1]
+        gp.se_cov(Xd, a, r, s, jitter, out=K, precision=prec0)
+        gp.chol(K, prec0, out=L, ws=ws, info=info)
+        Linv, Lbar = Kbar, K
+        g = torch.Generator(device="cpu")
+        g.manual_seed(5)
+        B = torch.randn(n, m, generator=g, dtype=torch.float64).to(dev)
+        Cbar = torch.randn(n, m, generator=g, dtype=torch.float64).to(dev)
+        C = torch.empty(n, m, dtype=torch.float64, device=dev)
+        Bbar = torch.empty_like(C)
+
+        def inverse():
+            gp.tri_inverse(L, out=Linv)
+
+        def adjoint():
+            gp.tri_solve_adjoint(Linv, C, Cbar, Bbar=Bbar, Lbar=Lbar)
+
+        gp.tri_solve(L, B, Linv=Linv, out=C)  # warm-up of the inverse, and C
+        adjoint()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def timed(fn):
+            l0 = gp.launch_count()
+            barrier()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            barrier()
+            return max_over_ranks(e0.elapsed_time(e1)) / reps, (gp.launch_count() - l0) // reps
+
+        inv_ms, inv_launches = timed(inverse)
+        adj_ms, adj_launches = timed(adjoint)
+        gp.trace_enable(True)
+        inverse()
+        torch.cuda.synchronize()
+        trace = gp.trace_summary()
+        gp.trace_enable(False)
+        gm = trace.get("gemm_f64", {})
+        inv_flops, adj_flops = n ** 3 / 3.0, 2.0 * n * n * m
+        return {"n": n, "m": m, "reps": reps, "factor_precision": prec0,
+                "inverse": {"ms": inv_ms, "gflops": inv_flops / (inv_ms / 1e3) / 1e9,
+                            "flops": inv_flops, "launches": inv_launches,
+                            "kernel_ms": {k: round(v["ms"], 3) for k, v in trace.items() if v["launches"]},
+                            "gemm_f64_gflops": (gm["flops"] / (gm["ms"] / 1e3) / 1e9) if gm.get("ms") else None},
+                "solve_adjoint": {"ms": adj_ms, "gflops": adj_flops / (adj_ms / 1e3) / 1e9,
+                                  "flops": adj_flops, "launches": adj_launches}}
+
+    tri = None if args.no_tri else run_tri()
+
     batched = None
     if not args.no_batched:
         batched = {}
@@ -545,6 +604,11 @@ def main():
     }
     if batched is not None:
         line["batched"] = batched
+    if tri is not None:
+        for leg in ("inverse", "solve_adjoint"):
+            tri[leg]["frac_of_fp64_peak"] = tri[leg]["gflops"] / fp64_peak
+        tri["peak_source"] = "of measured: FP64 DMMA m16n8k16 issue rate measured in this run (gpc_fp64_peak)"
+        line["tri"] = tri
     if tuned:
         line["tuned"] = tuned
     if "fp64" in results and "mixed" in results:

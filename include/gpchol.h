@@ -171,6 +171,57 @@ int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, si
 int gpc_trsv_noalloc(int n, const double *L, int ldl, double *x, int trans, gpc_stream_t stream);
 
 /*
+ * Lower-triangular inverse Linv = L^{-1} (Section 3.2, solving triangular
+ * systems, primitive function: the divide-and-conquer inverse with
+ * C3 = -C2 A3 C1, run bottom-up from the b x b diagonal blocks).
+ *  - L: n x n, row-major, leading dimension ldl >= n; only the lower triangle
+ *    (diagonal included) is read.  The diagonal must be non-zero; a zero or
+ *    non-finite diagonal entry is not detected and gives non-finite output.
+ *  - Linv: n x n output, ldi >= n; lower triangle = L^{-1}, strict upper
+ *    triangle = 0.  Linv == L (same ld) inverts in place; otherwise the two
+ *    must not overlap.  The strict upper triangle of Linv is scratch during
+ *    the call.
+ *  - FP64 throughout (FP64 tensor-core products); needs no workspace and
+ *    allocates nothing.  n == 0 returns GPC_OK without touching anything.
+ *  - Returns GPC_ERR_INVALID_ARG (nothing enqueued) for n < 0, a null pointer
+ *    or ld < n, or partially overlapping L and Linv; GPC_ERR_CUDA on a launch
+ *    error.
+ */
+int gpc_tri_inverse(int n, const double *L, int ldl, double *Linv, int ldi, gpc_stream_t stream);
+
+/*
+ * Triangular solve with a matrix right-hand side, C = L^{-1} B (Section 3.2,
+ * general solver: the inverse, then one product with it).
+ *  - L: n x n lower (ldl >= n; lower triangle read).  B: n x m (ldb >= m).
+ *  - Linv: n x n output (ldi >= n), written as by gpc_tri_inverse and kept for
+ *    gpc_tri_solve_adjoint; Linv == L (same ld) is allowed.
+ *  - C: n x m output (ldc >= m); must not overlap B, L or Linv.  B must not
+ *    overlap Linv.
+ *  - m == 0 computes only Linv.  FP64; no workspace.
+ *  - Errors as gpc_tri_inverse (plus m < 0, ldb or ldc < m, overlaps above).
+ */
+int gpc_tri_solve(int n, int m, const double *L, int ldl, const double *B, int ldb, double *Linv, int ldi,
+                  double *C, int ldc, gpc_stream_t stream);
+
+/*
+ * Reverse mode of C = L^{-1} B (Section 3.2, reverse mode function) for a
+ * scalar f with Cbar = df/dC:
+ *   Bbar = L^{-T} Cbar          (product with the kept inverse)
+ *   Lbar = -tril(Bbar C^T)      (the derivative with respect to the lower
+ *                                entries of L, the only ones the solve reads)
+ *  - Linv: n x n, ldi >= n, lower with a zero strict upper triangle (as
+ *    written by gpc_tri_inverse / gpc_tri_solve).  C, Cbar: n x m inputs.
+ *  - Bbar: n x m output (ldbb >= m); Lbar: n x n output (ldlb >= n), strict
+ *    upper triangle set to 0.  Both are overwritten, never read (a caller that
+ *    accumulates adjoints adds the results itself).
+ *  - Neither output may overlap any input or the other output.  FP64; no
+ *    workspace.  Errors as gpc_tri_solve.
+ */
+int gpc_tri_solve_adjoint(int n, int m, const double *Linv, int ldi, const double *C, int ldc,
+                          const double *Cbar, int ldcb, double *Bbar, int ldbb, double *Lbar, int ldlb,
+                          gpc_stream_t stream);
+
+/*
  * Gaussian-process log marginal likelihood of y ~ N(0, K):
  *   L = chol(K), z = L^{-1} y, alpha = L^{-T} z, logdet = 2 sum log L_ii,
  *   value = -1/2 y^T alpha - 1/2 logdet - (n/2) log(2 pi).

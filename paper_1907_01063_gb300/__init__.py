@@ -8,8 +8,8 @@ Two layers:
   * ``capi`` -- the C entry points with their C names (``capi.gpc_chol`` ...),
     taking raw integers for pointers and streams;
   * tensor functions with the same names minus the prefix (``chol``,
-    ``chol_adjoint``, ``gp_lml`` ...) and the autograd functions ``Chol`` and
-    ``GPLml``.
+    ``chol_adjoint``, ``gp_lml``, ``tri_solve`` ...) and the autograd
+    functions ``Chol``, ``GPLml`` and ``TriSolve``.
 There is no CPU fallback: without the compiled library every call raises.
 """
 from __future__ import annotations
@@ -54,6 +54,11 @@ _SIGNATURES = {
                           _c_vp, _c_size, _c_vp], _c_int),
     "gpc_trsv": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_size, _c_vp], _c_int),
     "gpc_trsv_noalloc": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp], _c_int),
+    "gpc_tri_inverse": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp], _c_int),
+    "gpc_tri_solve": ([_c_int, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp],
+                      _c_int),
+    "gpc_tri_solve_adjoint": ([_c_int, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int,
+                               _c_vp, _c_int, _c_vp], _c_int),
     "gpc_gp_lml": ([_c_int, _c_vp, _c_int, _c_vp, _c_vp, _c_int, _c_int, _c_vp, _c_vp, _c_vp,
                     _c_vp, _c_size, _c_vp, _c_vp], _c_int),
     "gpc_gp_lml_grad": ([_c_int, _c_vp, _c_int, _c_vp, _c_double, _c_vp, _c_int, _c_int, _c_vp,
@@ -332,6 +337,61 @@ def trsv(L: torch.Tensor, x: torch.Tensor, trans: bool = False,
     return x
 
 
+def _rect(t: torch.Tensor, n: int, name: str) -> tuple[int, int]:
+    """(m, ld) of an n x m row-major float64 CUDA matrix."""
+    if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 2 and t.shape[0] == n):
+        raise ValueError(f"{name} must be a float64 CUDA matrix with {n} rows")
+    m = int(t.shape[1])
+    if n > 0 and m > 0 and t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (stride(1) == 1)")
+    return m, (int(t.stride(0)) if n > 0 and m > 0 else max(m, 1))
+
+
+def tri_inverse(L: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """L^{-1} of the lower triangle of L (zero strict upper); out may be L itself."""
+    n = L.shape[0]
+    ldl = _square(L, "L")
+    X = out if out is not None else torch.empty_like(L)
+    ldx = _square(X, "Linv")
+    _check(capi.gpc_tri_inverse(n, _ptr(L), ldl, _ptr(X), ldx, _stream()), "gpc_tri_inverse")
+    return X
+
+
+def tri_solve(L: torch.Tensor, B: torch.Tensor, Linv: torch.Tensor | None = None,
+              out: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """(C, Linv) with C = L^{-1} B through the inverse, as one product."""
+    n = L.shape[0]
+    ldl = _square(L, "L")
+    m, ldb = _rect(B, n, "B")
+    X = Linv if Linv is not None else torch.empty_like(L)
+    ldx = _square(X, "Linv")
+    C = out if out is not None else torch.empty(n, m, dtype=torch.float64, device=B.device)
+    _, ldc = _rect(C, n, "C")
+    _check(capi.gpc_tri_solve(n, m, _ptr(L), ldl, _ptr(B), ldb, _ptr(X), ldx, _ptr(C), ldc, _stream()),
+           "gpc_tri_solve")
+    return C, X
+
+
+def tri_solve_adjoint(Linv: torch.Tensor, C: torch.Tensor, Cbar: torch.Tensor,
+                      Bbar: torch.Tensor | None = None,
+                      Lbar: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """(Bbar, Lbar) of C = L^{-1} B: L^{-T} Cbar and -tril(Bbar C^T)."""
+    n = Linv.shape[0]
+    ldx = _square(Linv, "Linv")
+    m, ldc = _rect(C, n, "C")
+    mb, ldcb = _rect(Cbar, n, "Cbar")
+    if mb != m:
+        raise ValueError("C and Cbar must have the same shape")
+    Bb = Bbar if Bbar is not None else torch.empty_like(C, memory_format=torch.contiguous_format)
+    _, ldbb = _rect(Bb, n, "Bbar")
+    Lb = Lbar if Lbar is not None else torch.empty_like(Linv)
+    ldlb = _square(Lb, "Lbar")
+    _check(capi.gpc_tri_solve_adjoint(n, m, _ptr(Linv), ldx, _ptr(C), ldc, _ptr(Cbar), ldcb, _ptr(Bb), ldbb,
+                                      _ptr(Lb), ldlb, _stream()),
+           "gpc_tri_solve_adjoint")
+    return Bb, Lb
+
+
 def gp_lml(K: torch.Tensor, y: torch.Tensor, precision="fp64", L: torch.Tensor | None = None,
            ws: torch.Tensor | None = None, info: torch.Tensor | None = None, check: bool = True):
     """Log marginal likelihood of y ~ N(0, K): returns dict(L, alpha, logdet, value).
@@ -522,6 +582,35 @@ class GPLml(torch.autograd.Function):
         Kbar = gp_lml_grad(L, alpha, 1.0, ctx.precision)
         g = se_hyper_grad(X, a, r, s, Kbar, precision=ctx.precision)
         return None, None, (g * gvalue).to(ctx.hyp_device), None, None
+
+
+class TriSolve(torch.autograd.Function):
+    """C = L^{-1} B with the lower triangle of L; backward gives
+    Bbar = L^{-T} Cbar and Lbar = -tril(Bbar C^T) from the kept inverse.
+    A 1-D B is treated as one column."""
+
+    @staticmethod
+    def forward(ctx, L, B):
+        vec = B.dim() == 1
+        Bm = B.detach().reshape(-1, 1) if vec else B.detach()
+        if Bm.shape[1] > 0 and Bm.stride(1) != 1:
+            Bm = Bm.contiguous()
+        C, X = tri_solve(L.detach(), Bm)
+        ctx.vec = vec
+        ctx.save_for_backward(X, C)
+        return C.reshape(-1) if vec else C
+
+    @staticmethod
+    def backward(ctx, Cbar):
+        X, C = ctx.saved_tensors
+        Cb = Cbar.reshape(-1, 1) if ctx.vec else Cbar
+        Bb, Lb = tri_solve_adjoint(X, C, Cb.contiguous())
+        return Lb, (Bb.reshape(-1) if ctx.vec else Bb)
+
+
+def mdivide_left_tri_low(L, B):
+    """Differentiable L^{-1} B for lower-triangular L (upper triangle ignored)."""
+    return TriSolve.apply(L, B)
 
 
 def gp_lml_value(X, y, hyp, jitter=0.0, precision="fp64"):

@@ -81,6 +81,20 @@ size_t mat_bytes(int n, int ld) { return n > 0 ? ((size_t)(n - 1) * ld + n) * si
 
 bool bad_square(int n, const void *p, int ld) { return n > 0 && (p == nullptr || ld < n); }
 
+size_t rect_bytes(int rows, int cols, int ld) {
+  return rows > 0 && cols > 0 ? ((size_t)(rows - 1) * ld + cols) * sizeof(double) : 0;
+}
+
+bool bad_rect(int rows, int cols, const void *p, int ld) {
+  return rows > 0 && cols > 0 && (p == nullptr || ld < cols);
+}
+
+// L and its inverse: the same buffer with the same ld, or disjoint.
+bool bad_inverse_pair(int n, const double *L, int ldl, const double *X, int ldx) {
+  if ((const void *)L == (const void *)X) return ldl != ldx;
+  return overlaps(L, mat_bytes(n, ldl), X, mat_bytes(n, ldx));
+}
+
 }  // namespace
 }  // namespace gpc
 
@@ -205,6 +219,47 @@ int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, si
   if (n == 0) return GPC_OK;
   if (bad_square(n, L, ldl) || !x || !ws || ws_bytes < trsv_workspace_bytes(n)) return GPC_ERR_INVALID_ARG;
   return status_of(trsv(n, L, ldl, x, trans, ws, nullptr, stream));
+}
+
+int gpc_tri_inverse(int n, const double *L, int ldl, double *Linv, int ldi, gpc_stream_t stream) {
+  if (n < 0) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (bad_square(n, L, ldl) || bad_square(n, Linv, ldi) || bad_inverse_pair(n, L, ldl, Linv, ldi))
+    return GPC_ERR_INVALID_ARG;
+  return status_of(tri_inverse(n, L, ldl, Linv, ldi, stream));
+}
+
+int gpc_tri_solve(int n, int m, const double *L, int ldl, const double *B, int ldb, double *Linv, int ldi,
+                  double *C, int ldc, gpc_stream_t stream) {
+  if (n < 0 || m < 0) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (bad_square(n, L, ldl) || bad_square(n, Linv, ldi) || bad_inverse_pair(n, L, ldl, Linv, ldi) ||
+      bad_rect(n, m, B, ldb) || bad_rect(n, m, C, ldc))
+    return GPC_ERR_INVALID_ARG;
+  if (m > 0) {
+    const size_t bb = rect_bytes(n, m, ldb), cb = rect_bytes(n, m, ldc);
+    if (overlaps(C, cb, B, bb) || overlaps(C, cb, L, mat_bytes(n, ldl)) || overlaps(C, cb, Linv, mat_bytes(n, ldi)) ||
+        overlaps(B, bb, Linv, mat_bytes(n, ldi)))
+      return GPC_ERR_INVALID_ARG;
+  }
+  return status_of(tri_solve(n, m, L, ldl, B, ldb, Linv, ldi, C, ldc, stream));
+}
+
+int gpc_tri_solve_adjoint(int n, int m, const double *Linv, int ldi, const double *C, int ldc,
+                          const double *Cbar, int ldcb, double *Bbar, int ldbb, double *Lbar, int ldlb,
+                          gpc_stream_t stream) {
+  if (n < 0 || m < 0) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (bad_square(n, Linv, ldi) || bad_square(n, Lbar, ldlb) || bad_rect(n, m, C, ldc) ||
+      bad_rect(n, m, Cbar, ldcb) || bad_rect(n, m, Bbar, ldbb))
+    return GPC_ERR_INVALID_ARG;
+  const size_t xb = mat_bytes(n, ldi), lb = mat_bytes(n, ldlb);
+  const size_t cb = rect_bytes(n, m, ldc), cbb = rect_bytes(n, m, ldcb), bbb = rect_bytes(n, m, ldbb);
+  if (overlaps(Lbar, lb, Linv, xb) || overlaps(Lbar, lb, C, cb) || overlaps(Lbar, lb, Cbar, cbb) ||
+      overlaps(Lbar, lb, Bbar, bbb) || overlaps(Bbar, bbb, Linv, xb) || overlaps(Bbar, bbb, C, cb) ||
+      overlaps(Bbar, bbb, Cbar, cbb))
+    return GPC_ERR_INVALID_ARG;
+  return status_of(tri_solve_adjoint(n, m, Linv, ldi, C, ldc, Cbar, ldcb, Bbar, ldbb, Lbar, ldlb, stream));
 }
 
 int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int ldl,

@@ -31,7 +31,7 @@ int sm_count();
 // neither computed nor touched); 2 lower, mirrored into the upper triangle.
 // beta == 0 never reads C.
 enum { UPLO_FULL = 0, UPLO_LOWER = 1, UPLO_LOWER_MIRROR = 2 };
-enum { KSKIP_NONE = 0, KSKIP_ROWS = 1, KSKIP_COLS = 2 };
+enum { KSKIP_NONE = 0, KSKIP_ROWS = 1, KSKIP_COLS = 2, KSKIP_ROWS_END = 3, KSKIP_COLS_END = 4 };
 struct Gemm {
   int M = 0, N = 0, K = 0;
   double algo_flops = 0.0;  // algorithmic flops for the trace (0: 2MNK, or M(M+1)K lower)
@@ -48,7 +48,17 @@ struct Gemm {
   // KSKIP_ROWS when op(A)[i][k] = 0 for k < i (op(A) upper triangular), so
   // the tile's rows from m0 need k >= m0; KSKIP_COLS when op(B)[k][j] = 0
   // for k < j (op(B) lower triangular), so columns from n0 need k >= n0.
+  // KSKIP_ROWS_END when op(A)[i][k] = 0 for k > i (op(A) lower triangular):
+  // rows below m0 + 64 need k < m0 + 64; KSKIP_COLS_END when op(B)[k][j] = 0
+  // for k > j (op(B) upper triangular): columns below n0 + 64 need k < n0 + 64.
+  // Entries of the diagonal 64 x 64 tile on the zero side are still read and
+  // must hold zeros.
   int kskip = KSKIP_NONE;
+  // batch > 1: grid.y runs over independent products of the same shape whose
+  // A, B and C start sA, sB and sC elements after the previous product's
+  // (never split over K).
+  int batch = 1;
+  long long sA = 0, sB = 0, sC = 0;
 };
 // Bytes of split-K scratch any gemm_f64 call may use (a fixed cap).
 size_t gemm_f64_scratch_bytes();
@@ -73,9 +83,10 @@ cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, 
 cudaError_t trtri_diag(int nb, const double *D, long long ldd, double *Dinv, cudaStream_t s);
 // Inverses of all diagonal blocks of L in one launch: block 0 = rows [0, first),
 // block ib >= 1 = [first + (ib-1) b, first + ib b); inverse ib at out + ib b^2
-// (leading dimension = block size).  n = total order.
+// (leading dimension = block size), or, when ldo != 0, at its diagonal
+// position of the n x n matrix out (leading dimension ldo; out may be L).
 cudaError_t trtri_batched(int n, const double *L, long long ldl, int first, int b, double *out,
-                          cudaStream_t s);
+                          cudaStream_t s, long long ldo = 0);
 
 // ---------------------------------------------------------------- elementwise helpers
 // dst(i,j) = src(i,j) for j <= i; strict upper of dst set to 0 (src may == dst).
@@ -91,6 +102,13 @@ cudaError_t lower_to_symmetric_half(int n, double *A, long long lda, cudaStream_
 cudaError_t reset_info(int *info, cudaStream_t s);
 
 // ---------------------------------------------------------------- drivers
+// Triangular inverse, solve and solve adjoint (trinv.cu); X is the inverse.
+cudaError_t tri_inverse(int n, const double *L, long long ldl, double *X, long long ldx, cudaStream_t s);
+cudaError_t tri_solve(int n, int m, const double *L, long long ldl, const double *B, long long ldb, double *X,
+                      long long ldx, double *C, long long ldc, cudaStream_t s);
+cudaError_t tri_solve_adjoint(int n, int m, const double *X, long long ldx, const double *C, long long ldc,
+                              const double *Cbar, long long ldcb, double *Bbar, long long ldbb, double *Lbar,
+                              long long ldlb, cudaStream_t s);
 size_t chol_workspace_bytes(int n, int precision);
 size_t adjoint_workspace_bytes(int n, int precision);
 size_t trsv_workspace_bytes(int n);

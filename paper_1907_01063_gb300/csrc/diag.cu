@@ -34,8 +34,8 @@ __device__ void invert_lower_smem(double *s, int ld, int nb) {
   }
 }
 
-__device__ void potrf_trtri_body(int nb, double *A, long long lda, double *Winv, int *info, int pivot_offset,
-                                 int factor) {
+__device__ void potrf_trtri_body(int nb, double *A, long long lda, double *Winv, long long ldw, int *info,
+                                 int pivot_offset, int factor) {
   extern __shared__ double smem[];
   const int ld = nb + 1;
   __shared__ int fail;
@@ -83,27 +83,31 @@ __device__ void potrf_trtri_body(int nb, double *A, long long lda, double *Winv,
   invert_lower_smem(smem, ld, nb);
   for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
     const int i = idx / nb, j = idx - i * nb;
-    Winv[idx] = (j <= i) ? S(smem, ld, i, j) : 0.0;
+    Winv[(long long)i * ldw + j] = (j <= i) ? S(smem, ld, i, j) : 0.0;
   }
 }
 
 __global__ void __launch_bounds__(DIAG_THREADS)
 potrf_trtri_kernel(int nb, double *A, long long lda, double *Winv, int *info, int pivot_offset,
                    int factor) {
-  potrf_trtri_body(nb, A, lda, Winv, info, pivot_offset, factor);
+  potrf_trtri_body(nb, A, lda, Winv, nb, info, pivot_offset, factor);
 }
 
 // All diagonal-block inverses of L at once, one CTA per block.  Block 0 is
-// rows [0, first), block ib >= 1 is [first + (ib - 1) b, first + ib b); the
-// inverse of block ib goes to out + ib * b * b with leading dimension equal to
-// its size.  (The per-block inverses of Section 3.2, computed as a batch.)
+// rows [0, first), block ib >= 1 is [first + (ib - 1) b, first + ib b).  With
+// ldo == 0 the inverse of block ib goes to out + ib * b * b with leading
+// dimension equal to its size; otherwise to its diagonal position in an
+// n x n matrix out with leading dimension ldo (out may be L itself: each block
+// is read into shared memory before its inverse is written).  (The per-block
+// inverses of Section 3.2, computed as a batch.)
 __global__ void __launch_bounds__(DIAG_THREADS)
-trtri_batched_kernel(int n, const double *L, long long ldl, int first, int b, double *out) {
+trtri_batched_kernel(int n, const double *L, long long ldl, int first, int b, double *out, long long ldo) {
   const int ib = blockIdx.x;
   const int j0 = (ib == 0) ? 0 : first + (ib - 1) * b;
   const int nb = (ib == 0) ? first : min(b, n - j0);
-  potrf_trtri_body(nb, const_cast<double *>(L) + (long long)j0 * ldl + j0, ldl, out + (size_t)ib * b * b,
-                   nullptr, 0, 0);
+  double *dst = ldo ? out + (long long)j0 * ldo + j0 : out + (size_t)ib * b * b;
+  potrf_trtri_body(nb, const_cast<double *>(L) + (long long)j0 * ldl + j0, ldl, dst, ldo ? ldo : nb, nullptr,
+                   0, 0);
 }
 
 // 1/x and 1/sqrt(x) for normal positive x: the hardware's approximations
@@ -457,7 +461,7 @@ cudaError_t trtri_diag(int nb, const double *D, long long ldd, double *Dinv, cud
 }
 
 cudaError_t trtri_batched(int n, const double *L, long long ldl, int first, int b, double *out,
-                          cudaStream_t s) {
+                          cudaStream_t s, long long ldo) {
   if (n <= 0) return cudaSuccess;
   if (b > kMaxBlock || first < 1 || first > b) return cudaErrorInvalidValue;
   static bool attr_set[64] = {};
@@ -472,7 +476,7 @@ cudaError_t trtri_batched(int n, const double *L, long long ldl, int first, int 
   const int nblk = 1 + (n - first + b - 1) / b;
   const size_t smem = (size_t)b * (b + 1) * sizeof(double);
   GPC_LAUNCH(GPC_TRACE_DIAG, (double)n * b * b / 3.0, 16.0 * (double)n * b, s,
-             trtri_batched_kernel<<<nblk, DIAG_THREADS, smem, s>>>(n, L, ldl, first, b, out));
+             trtri_batched_kernel<<<nblk, DIAG_THREADS, smem, s>>>(n, L, ldl, first, b, out, ldo));
   return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ struct Params {
   double *C;
   long long ldc;
   int uplo, tiles_n, kchunk, kskip;
+  long long sA, sB, sC;  // per-product offsets of a batch (grid.y)
   double *partial;  // non-null when grid.z > 1
 };
 
@@ -60,9 +61,10 @@ template <bool TA, bool TB>
 __device__ __forceinline__ void load_tiles(const Params &p, int m0, int n0, int k0, int kend,
                                            double (&ra)[8], double (&rb)[8]) {
   const int t = threadIdx.x;
+  const double *A = p.A + (long long)blockIdx.y * p.sA, *B = p.B + (long long)blockIdx.y * p.sB;
   if (!TA) {  // A[m][k]: 2 threads per row, 8 consecutive k each
     const int r = t >> 1, c0 = (t & 1) * 8, m = m0 + r;
-    const double *src = p.A + (long long)m * p.lda;
+    const double *src = A + (long long)m * p.lda;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = k0 + c0 + i;
@@ -70,7 +72,7 @@ __device__ __forceinline__ void load_tiles(const Params &p, int m0, int n0, int 
     }
   } else {  // A[k][m]: 8 threads per k-row, 8 consecutive m each
     const int kk = t >> 3, mm0 = (t & 7) * 8, k = k0 + kk;
-    const double *src = p.A + (long long)k * p.lda;
+    const double *src = A + (long long)k * p.lda;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int m = m0 + mm0 + i;
@@ -79,7 +81,7 @@ __device__ __forceinline__ void load_tiles(const Params &p, int m0, int n0, int 
   }
   if (!TB) {  // B[k][n]
     const int kk = t >> 3, nn0 = (t & 7) * 8, k = k0 + kk;
-    const double *src = p.B + (long long)k * p.ldb;
+    const double *src = B + (long long)k * p.ldb;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int n = n0 + nn0 + i;
@@ -87,7 +89,7 @@ __device__ __forceinline__ void load_tiles(const Params &p, int m0, int n0, int 
     }
   } else {  // B[n][k]
     const int r = t >> 1, c0 = (t & 1) * 8, n = n0 + r;
-    const double *src = p.B + (long long)n * p.ldb;
+    const double *src = B + (long long)n * p.ldb;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = k0 + c0 + i;
@@ -135,8 +137,9 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
   const int m0 = tm * BM, n0 = tn * BN;
   // a skipped leading K range is a multiple of BM = BN, so kbeg stays on a K step
   const int kfirst = p.kskip == KSKIP_ROWS ? m0 : (p.kskip == KSKIP_COLS ? n0 : 0);
+  const int klast = p.kskip == KSKIP_ROWS_END ? m0 + BM : (p.kskip == KSKIP_COLS_END ? n0 + BN : p.K);
   const int kbeg = max((int)blockIdx.z * p.kchunk, kfirst);
-  const int kend = min(p.K, (int)blockIdx.z * p.kchunk + p.kchunk);
+  const int kend = min(min(p.K, klast), (int)blockIdx.z * p.kchunk + p.kchunk);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wm = warp >> 1, wn = warp & 1;
@@ -203,10 +206,11 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
           continue;
         }
         if (p.uplo != UPLO_FULL && col > row) continue;
-        double *dst = p.C + (long long)row * p.ldc + col;
+        double *C = p.C + (long long)blockIdx.y * p.sC;
+        double *dst = C + (long long)row * p.ldc + col;
         const double out = (p.beta == 0.0) ? v : fma(p.beta, *dst, v);
         *dst = out;
-        if (p.uplo == UPLO_LOWER_MIRROR && col < row) p.C[(long long)col * p.ldc + row] = out;
+        if (p.uplo == UPLO_LOWER_MIRROR && col < row) C[(long long)col * p.ldc + row] = out;
       }
 }
 
@@ -229,8 +233,9 @@ __global__ void splitk_reduce_kernel(Params p, int splits) {
 size_t gemm_f64_scratch_bytes() { return kScratchCap; }
 
 cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.uplo != UPLO_FULL && g.M != g.N) return cudaErrorInvalidValue;
+  if (g.batch > 65535) return cudaErrorInvalidValue;
   Params p;
   p.M = g.M;
   p.N = g.N;
@@ -245,6 +250,9 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   p.ldc = g.ldc;
   p.uplo = g.uplo;
   p.kskip = g.kskip;
+  p.sA = g.sA;
+  p.sB = g.sB;
+  p.sC = g.sC;
   const int tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
   p.tiles_n = tn;
   const long long tiles = (g.uplo != UPLO_FULL) ? (long long)tm * (tm + 1) / 2 : (long long)tm * tn;
@@ -253,7 +261,7 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   int splits = 1;
   const long long target = 3LL * sm_count();  // three CTAs fit per SM
   const int kmin = std::max(tuning().splitk_min, BK);
-  if (scratch && tiles < target && p.K >= 2 * kmin) {
+  if (scratch && g.batch == 1 && tiles < target && p.K >= 2 * kmin) {
     long long want = (target + tiles - 1) / tiles;
     want = std::min<long long>(want, p.K / kmin);
     want = std::min<long long>(want, 64);
@@ -268,10 +276,11 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   p.kchunk = kchunk;
   p.partial = splits > 1 ? scratch : nullptr;
 
-  dim3 grid((unsigned)tiles, 1, (unsigned)splits);
+  dim3 grid((unsigned)tiles, (unsigned)g.batch, (unsigned)splits);
   const double mn = (g.uplo != UPLO_FULL) ? 0.5 * (double)g.M * (g.M + 1) : (double)g.M * g.N;
-  const double flops = g.algo_flops > 0.0 ? g.algo_flops : 2.0 * mn * (double)p.K;
-  const double bytes = 8.0 * ((double)g.M * p.K + (double)p.K * g.N + (g.beta != 0.0 ? 2.0 : 1.0) * mn);
+  const double flops = g.algo_flops > 0.0 ? g.algo_flops : 2.0 * mn * (double)p.K * g.batch;
+  const double bytes =
+      8.0 * g.batch * ((double)g.M * p.K + (double)p.K * g.N + (g.beta != 0.0 ? 2.0 : 1.0) * mn);
   GPC_LAUNCH(GPC_TRACE_GEMM_F64, flops, bytes, s, {
     if (!g.transA && !g.transB) gemm_f64_kernel<false, false><<<grid, THREADS, 0, s>>>(p);
     else if (!g.transA && g.transB) gemm_f64_kernel<false, true><<<grid, THREADS, 0, s>>>(p);

@@ -97,3 +97,29 @@ def test_argument_checks_return_before_any_launch():
     assert c.gpc_trsv(0, None, 0, None, 0, None, 0, None) == gp.GPC_OK
     assert c.gpc_se_cov(0, 1, None, 1, 1.0, 1.0, 0.1, 0.0, None, 0, 0, 0, None) == gp.GPC_OK
     assert c.gpc_se_cov(10, 2, fake, 2, 1.0, 1.0, 0.1, 0.0, fake, 10, 0, 7, None) == bad  # precision
+
+
+def test_triangular_argument_checks_return_before_any_launch():
+    c = gp.capi
+    bad = gp.GPC_ERR_INVALID_ARG
+    fake, far, farther = 0x1000, 0x100000, 0x200000  # never dereferenced
+    assert c.gpc_tri_inverse(-1, fake, 1, far, 1, None) == bad
+    assert c.gpc_tri_inverse(10, None, 10, far, 10, None) == bad
+    assert c.gpc_tri_inverse(10, fake, 9, far, 10, None) == bad
+    assert c.gpc_tri_inverse(10, fake, 10, fake + 8, 10, None) == bad  # partial overlap
+    assert c.gpc_tri_inverse(10, fake, 10, fake, 11, None) == bad  # in place, ld differs
+    assert c.gpc_tri_solve(10, -1, fake, 10, far, 3, farther, 10, 0x300000, 3, None) == bad
+    assert c.gpc_tri_solve(10, 3, fake, 10, far, 2, farther, 10, 0x300000, 3, None) == bad  # ldb < m
+    assert c.gpc_tri_solve(10, 3, fake, 10, far, 3, farther, 10, far, 3, None) == bad  # C == B
+    assert c.gpc_tri_solve(10, 3, fake, 10, far, 3, far, 10, 0x300000, 3, None) == bad  # B inside Linv
+    assert c.gpc_tri_solve(10, 3, fake, 10, None, 3, farther, 10, 0x300000, 3, None) == bad
+    assert c.gpc_tri_solve_adjoint(10, 3, fake, 10, far, 3, farther, 3, far, 3, 0x300000, 10,
+                                   None) == bad  # Bbar == C
+    assert c.gpc_tri_solve_adjoint(10, 3, fake, 10, far, 3, farther, 3, 0x300000, 3, fake, 10,
+                                   None) == bad  # Lbar == Linv
+    assert c.gpc_tri_solve_adjoint(10, 3, fake, 10, far, 3, farther, 3, 0x300000, 3, 0x400000, 9,
+                                   None) == bad  # ldlb < n
+    # zero-size calls need no device work
+    assert c.gpc_tri_inverse(0, None, 0, None, 0, None) == gp.GPC_OK
+    assert c.gpc_tri_solve(0, 5, None, 0, None, 0, None, 0, None, 0, None) == gp.GPC_OK
+    assert c.gpc_tri_solve_adjoint(0, 5, None, 0, None, 0, None, 0, None, 0, None, 0, None) == gp.GPC_OK
