@@ -513,7 +513,11 @@ def main():
                 "solve_adjoint": {"ms": adj_ms, "gflops": adj_flops / (adj_ms / 1e3) / 1e9,
                                   "flops": adj_flops, "launches": adj_launches}}
 
-    tri = None if args.no_tri else run_tri()
+    tri = None
+    if not args.no_tri:
+        torch.cuda.nvtx.range_push("tri")  # lets a profiler select this leg's launches
+        tri = run_tri()
+        torch.cuda.nvtx.range_pop()
 
     batched = None
     if not args.no_batched:
