@@ -351,3 +351,91 @@ void oracle_tri_solve_adjoint(int n, int m, const double *L, int ldl, const doub
       AT(Lbar, ldlb, i, j) = s;
     }
 }
+
+/*
+ * General matrix product C = A B (A: m x k, B: k x n, row-major; Section 3.1,
+ * primitive function), the plain triple loop with the sum over k ascending.
+ */
+void oracle_gemm(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                 double *C, int ldc) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int t = 0; t < k; ++t) s += AT(A, lda, i, t) * AT(B, ldb, t, j);
+      AT(C, ldc, i, j) = s;
+    }
+}
+
+/*
+ * Reverse mode of C = A B (Section 3.1, reverse mode function) for a scalar f
+ * with Cbar = df/dC:  Abar = Cbar B^T,  Bbar = A^T Cbar.
+ */
+void oracle_gemm_adjoint(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                         const double *Cbar, int ldcb, double *Abar, int ldab, double *Bbar, int ldbb) {
+  for (int i = 0; i < m; ++i)
+    for (int t = 0; t < k; ++t) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += AT(Cbar, ldcb, i, j) * AT(B, ldb, t, j);
+      AT(Abar, ldab, i, t) = s;
+    }
+  for (int t = 0; t < k; ++t)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += AT(A, lda, i, t) * AT(Cbar, ldcb, i, j);
+      AT(Bbar, ldbb, t, j) = s;
+    }
+}
+
+/*
+ * GLM log likelihood and its gradient (Section 3.4): the linear predictor
+ * eta_i = alpha + sum_j X_ij beta_j (j ascending), then per observation
+ *   family 0, normal-identity:  lp_i = -((y_i - eta_i)/sigma)^2 / 2 - log sigma - log(2 pi) / 2,
+ *                               d_i = (y_i - eta_i) / sigma^2
+ *   family 1, Bernoulli-logit:  lp_i = y_i eta_i - log(1 + exp(eta_i)),
+ *                               d_i = y_i - 1 / (1 + exp(-eta_i))
+ *   family 2, Poisson-log:      lp_i = y_i eta_i - exp(eta_i) - lgamma(y_i + 1),
+ *                               d_i = y_i - exp(eta_i)
+ * with d_i = d lp_i / d eta_i.  Outputs: lp = sum_i lp_i, dalpha = sum_i d_i,
+ * dbeta_j = sum_i X_ij d_i (i ascending), and for family 0
+ * dsigma = sum_i ((y_i - eta_i)^2 / sigma^3 - 1 / sigma) (else 0).
+ * log(1 + exp(eta)) is evaluated as max(eta, 0) + log1p(exp(-|eta|)), the
+ * same quantity without overflow.  Returns -1 if scratch cannot be allocated.
+ */
+int oracle_glm(int family, int n, int k, const double *X, int ldx, const double *y, double alpha,
+               const double *beta, double sigma, double *lp, double *dalpha, double *dbeta,
+               double *dsigma) {
+  double *d = (double *)malloc((size_t)n * sizeof(double) + 8);
+  if (!d) return -1;
+  double slp = 0.0, sda = 0.0, sds = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double eta = alpha;
+    for (int j = 0; j < k; ++j) eta += AT(X, ldx, i, j) * beta[j];
+    double li, di;
+    if (family == 0) {
+      double r = (y[i] - eta) / sigma;
+      li = -0.5 * r * r - log(sigma) - 0.5 * log(ORACLE_TWO_PI);
+      di = (y[i] - eta) / (sigma * sigma);
+      sds += (y[i] - eta) * (y[i] - eta) / (sigma * sigma * sigma) - 1.0 / sigma;
+    } else if (family == 1) {
+      double softplus = (eta > 0.0 ? eta : 0.0) + log1p(exp(-fabs(eta)));
+      li = y[i] * eta - softplus;
+      di = y[i] - 1.0 / (1.0 + exp(-eta));
+    } else {
+      li = y[i] * eta - exp(eta) - lgamma(y[i] + 1.0);
+      di = y[i] - exp(eta);
+    }
+    d[i] = di;
+    slp += li;
+    sda += di;
+  }
+  for (int j = 0; j < k; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += AT(X, ldx, i, j) * d[i];
+    dbeta[j] = s;
+  }
+  *lp = slp;
+  *dalpha = sda;
+  *dsigma = family == 0 ? sds : 0.0;
+  free(d);
+  return 0;
+}

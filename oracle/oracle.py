@@ -62,6 +62,12 @@ def _load():
         lib.oracle_tri_solve.restype = None
         lib.oracle_tri_solve_adjoint.argtypes = [i, i, _D, i, _D, i, _D, i, _D, i, _D, i]
         lib.oracle_tri_solve_adjoint.restype = None
+        lib.oracle_gemm.argtypes = [i, i, i, _D, i, _D, i, _D, i]
+        lib.oracle_gemm.restype = None
+        lib.oracle_gemm_adjoint.argtypes = [i, i, i, _D, i, _D, i, _D, i, _D, i, _D, i]
+        lib.oracle_gemm_adjoint.restype = None
+        lib.oracle_glm.argtypes = [i, i, i, _D, i, _D, d, _D, d, _D, _D, _D, _D]
+        lib.oracle_glm.restype = i
         _lib = lib
     return _lib
 
@@ -172,6 +178,49 @@ def tri_solve_adjoint(L, C, Cbar):
     Lbar = np.zeros_like(L)
     _load().oracle_tri_solve_adjoint(n, m, _p(L), n, _p(C), m, _p(Cbar), m, _p(Bbar), m, _p(Lbar), n)
     return Bbar, Lbar
+
+
+def gemm(A, B) -> np.ndarray:
+    """C = A B by the plain triple loop."""
+    A, B = _rect(A), _rect(B)
+    m, k = A.shape
+    if B.shape[0] != k:
+        raise ValueError("shape mismatch")
+    n = B.shape[1]
+    C = np.zeros((m, n))
+    _load().oracle_gemm(m, n, k, _p(A), k, _p(B), n, _p(C), n)
+    return C
+
+
+def gemm_adjoint(A, B, Cbar):
+    """(Abar, Bbar) = (Cbar B^T, A^T Cbar) for C = A B."""
+    A, B, Cbar = _rect(A), _rect(B), _rect(Cbar)
+    m, k = A.shape
+    n = B.shape[1]
+    if B.shape[0] != k or Cbar.shape != (m, n):
+        raise ValueError("shape mismatch")
+    Abar, Bbar = np.zeros((m, k)), np.zeros((k, n))
+    _load().oracle_gemm_adjoint(m, n, k, _p(A), k, _p(B), n, _p(Cbar), n, _p(Abar), k, _p(Bbar), n)
+    return Abar, Bbar
+
+
+GLM_FAMILIES = {"normal_id": 0, "bernoulli_logit": 1, "poisson_log": 2}
+
+
+def glm(family: str, X, y, alpha: float, beta, sigma: float = 1.0) -> dict:
+    """GLM log likelihood and gradient: dict(lp, dalpha, dbeta, dsigma)."""
+    X = _rect(X)
+    n, k = X.shape
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    if y.shape != (n,) or beta.shape != (k,):
+        raise ValueError("shape mismatch")
+    lp, da, ds = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    db = np.zeros(k)
+    if _load().oracle_glm(GLM_FAMILIES[family], n, k, _p(X), k, _p(y), float(alpha), _p(beta), float(sigma),
+                          ctypes.byref(lp), ctypes.byref(da), _p(db), ctypes.byref(ds)) != 0:
+        raise MemoryError("oracle scratch allocation failed")
+    return {"lp": lp.value, "dalpha": da.value, "dbeta": db, "dsigma": ds.value}
 
 
 def se_cov(X, alpha: float, rho: float, sigma: float, jitter: float = 0.0,

@@ -400,3 +400,107 @@ def test_tri_solve_adjoint_finite_differences(n, m):
             fd = (f(L, Bp) - f(L, Bm)) / (2 * h)
             assert abs(Bb[i, j] - fd) <= 1e-7 * max(1.0, abs(fd)), (i, j)
     assert np.array_equal(np.triu(Lb, 1), np.zeros((n, n)))
+
+
+# ---------------------------------------------------------------- GEMM and its reverse mode
+def test_gemm_exact_integers_and_numpy():
+    rng = np.random.default_rng(1)
+    A = rng.integers(-9, 10, (7, 5)).astype(float)
+    B = rng.integers(-9, 10, (5, 3)).astype(float)
+    assert np.array_equal(O.gemm(A, B), A @ B)  # small integers: every sum is exact
+    A, B = rng.standard_normal((33, 65)), rng.standard_normal((65, 17))
+    assert rel_fro(O.gemm(A, B), A @ B) <= 1e-15
+
+
+def test_gemm_adjoint_finite_differences():
+    # f(A, B) = sum(W * A B) is bilinear: central differences are exact up to rounding
+    rng = np.random.default_rng(2)
+    A, B, Wt = rng.standard_normal((4, 3)), rng.standard_normal((3, 5)), rng.standard_normal((4, 5))
+    Ab, Bb = O.gemm_adjoint(A, B, Wt)
+    h = 1e-3
+    for M, G in ((A, Ab), (B, Bb)):
+        for idx in np.ndindex(M.shape):
+            old = M[idx]
+            M[idx] = old + h
+            fp = float(np.sum(Wt * (A @ B)))
+            M[idx] = old - h
+            fm = float(np.sum(Wt * (A @ B)))
+            M[idx] = old
+            assert abs(G[idx] - (fp - fm) / (2 * h)) <= 1e-10 * max(1.0, abs(G[idx])), idx
+
+
+# ---------------------------------------------------------------- GLM likelihoods
+def glm_data(n=60, k=5, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, k))
+    beta = rng.standard_normal(k) / 2
+    return rng, X, beta, 0.3
+
+
+def test_glm_bernoulli_logit_matches_scipy():
+    import scipy.special as sp
+    rng, X, beta, alpha = glm_data()
+    eta = alpha + X @ beta
+    y = (rng.random(len(eta)) < sp.expit(eta)).astype(float)
+    r = O.glm("bernoulli_logit", X, y, alpha, beta)
+    assert abs(r["lp"] - scipy.stats.bernoulli.logpmf(y, sp.expit(eta)).sum()) <= 1e-12 * abs(r["lp"])
+    assert np.abs(r["dbeta"] - X.T @ (y - sp.expit(eta))).max() <= 1e-12
+    assert r["dsigma"] == 0.0
+
+
+def test_glm_bernoulli_zero_coefficients_closed_form():
+    # beta = 0, alpha = 0: every p_i = 1/2, lp = -n log 2, d_i = y_i - 1/2
+    rng, X, beta, _ = glm_data(n=40, k=3)
+    y = (rng.random(40) < 0.5).astype(float)
+    r = O.glm("bernoulli_logit", X, y, 0.0, np.zeros(3))
+    assert abs(r["lp"] + 40 * math.log(2.0)) <= 1e-13 * 40
+    assert abs(r["dalpha"] - float(np.sum(y - 0.5))) <= 1e-13
+    assert np.abs(r["dbeta"] - X.T @ (y - 0.5)).max() <= 1e-13
+
+
+def test_glm_bernoulli_extreme_eta_stays_finite():
+    # eta = +-800: softplus(eta) = max(eta, 0) + log1p(exp(-|eta|)) without overflow
+    X = np.array([[1.0], [-1.0], [1.0], [-1.0]])
+    y = np.array([1.0, 0.0, 0.0, 1.0])
+    r = O.glm("bernoulli_logit", X, y, 0.0, np.array([800.0]))
+    # the two well-predicted rows contribute ~0, the two mispredicted ones -800 each
+    assert abs(r["lp"] + 1600.0) <= 1e-9
+    assert r["dbeta"][0] == -2.0 and r["dalpha"] == 0.0
+
+
+def test_glm_poisson_and_normal_match_scipy():
+    rng, X, beta, alpha = glm_data(seed=3)
+    eta = alpha + X @ beta
+    yp = rng.poisson(np.exp(eta)).astype(float)
+    r = O.glm("poisson_log", X, yp, alpha, beta)
+    assert abs(r["lp"] - scipy.stats.poisson.logpmf(yp, np.exp(eta)).sum()) <= 1e-12 * abs(r["lp"])
+    assert np.abs(r["dbeta"] - X.T @ (yp - np.exp(eta))).max() <= 1e-11
+    sigma = 0.7
+    yn = eta + sigma * rng.standard_normal(len(eta))
+    r = O.glm("normal_id", X, yn, alpha, beta, sigma)
+    assert abs(r["lp"] - scipy.stats.norm.logpdf(yn, eta, sigma).sum()) <= 1e-12 * abs(r["lp"])
+
+
+@pytest.mark.parametrize("family", ["normal_id", "bernoulli_logit", "poisson_log"])
+def test_glm_gradient_finite_differences(family):
+    rng, X, beta, alpha = glm_data(n=30, k=4, seed=4)
+    eta = alpha + X @ beta
+    y = {"normal_id": eta + rng.standard_normal(30),
+         "bernoulli_logit": (rng.random(30) < 0.5).astype(float),
+         "poisson_log": rng.poisson(np.exp(eta)).astype(float)}[family]
+    sigma = 0.8
+    r = O.glm(family, X, y, alpha, beta, sigma)
+
+    def f(a, b, s):
+        return O.glm(family, X, y, a, b, s)["lp"]
+
+    h = 1e-6
+    assert abs(r["dalpha"] - (f(alpha + h, beta, sigma) - f(alpha - h, beta, sigma)) / (2 * h)) <= 1e-6
+    for j in range(4):
+        e = np.zeros(4)
+        e[j] = h
+        fd = (f(alpha, beta + e, sigma) - f(alpha, beta - e, sigma)) / (2 * h)
+        assert abs(r["dbeta"][j] - fd) <= 1e-6 * max(1.0, abs(fd)), j
+    if family == "normal_id":
+        fd = (f(alpha, beta, sigma + h) - f(alpha, beta, sigma - h)) / (2 * h)
+        assert abs(r["dsigma"] - fd) <= 1e-6 * max(1.0, abs(fd))

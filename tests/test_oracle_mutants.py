@@ -42,6 +42,17 @@ MUTANTS = {
                                  "s -= AT(L, ldl, i, k) * AT(Bbar, ldbb, k, j);"),
     "trsolve_adj_lbar_transposed": ("s -= AT(Bbar, ldbb, i, t) * AT(C, ldc, j, t);",
                                     "s -= AT(Bbar, ldbb, j, t) * AT(C, ldc, i, t);"),
+    "gemm_transposed_b": ("for (int t = 0; t < k; ++t) s += AT(A, lda, i, t) * AT(B, ldb, t, j);",
+                          "for (int t = 0; t < k; ++t) s += AT(A, lda, i, t) * AT(B, ldb, j, t);"),
+    "gemm_adj_untransposed": ("for (int j = 0; j < n; ++j) s += AT(Cbar, ldcb, i, j) * AT(B, ldb, t, j);",
+                              "for (int j = 0; j < n; ++j) s += AT(Cbar, ldcb, i, j) * AT(B, ldb, j, t);"),
+    "glm_logit_derivative_sign": ("di = y[i] - 1.0 / (1.0 + exp(-eta));", "di = y[i] - 1.0 / (1.0 + exp(eta));"),
+    "glm_softplus_branch": ("double softplus = (eta > 0.0 ? eta : 0.0) + log1p(exp(-fabs(eta)));",
+                            "double softplus = log1p(exp(-fabs(eta)));"),
+    "glm_dropped_alpha": ("double eta = alpha;", "double eta = 0.0;"),
+    "glm_poisson_lgamma": ("li = y[i] * eta - exp(eta) - lgamma(y[i] + 1.0);", "li = y[i] * eta - exp(eta);"),
+    "glm_normal_dsigma": ("sds += (y[i] - eta) * (y[i] - eta) / (sigma * sigma * sigma) - 1.0 / sigma;",
+                          "sds += (y[i] - eta) * (y[i] - eta) / (sigma * sigma) - 1.0 / sigma;"),
 }
 
 
