@@ -64,6 +64,9 @@ def parse_args():
     p.add_argument("--no-tri", action="store_true", help="skip the triangular inverse / solve-adjoint leg")
     p.add_argument("--tri-m", type=int, default=1024, help="right-hand-side columns of the solve-adjoint leg")
     p.add_argument("--tri-reps", type=int, default=2)
+    p.add_argument("--no-gemm-glm", action="store_true", help="skip the GEMM and GLM legs")
+    p.add_argument("--glm-n", type=int, default=1 << 20)
+    p.add_argument("--glm-k", type=int, default=512)
     return p.parse_args()
 
 
@@ -513,6 +516,79 @@ def main():
                 "solve_adjoint": {"ms": adj_ms, "gflops": adj_flops / (adj_ms / 1e3) / 1e9,
                                   "flops": adj_flops, "launches": adj_launches}}
 
+    def run_gemm_glm():
+        """Section 3.1 and 3.4 legs: FP64 GEMM C = A B and its reverse mode on
+        square 4096 matrices, a large-k product (128 x 128 output, k = 2^20,
+        split over k), and the fused Bernoulli-logit GLM likelihood with its
+        gradient on the logistic-regression toy data (one pass over X)."""
+        from paper_1907_01063_gb300 import workloads as W
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def timed(fn, reps):
+            fn()
+            l0 = gp.launch_count()
+            barrier()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            barrier()
+            return max_over_ranks(e0.elapsed_time(e1)) / reps, (gp.launch_count() - l0) // reps
+
+        g = torch.Generator(device=dev)
+        g.manual_seed(7)
+        gws = gp.gemm_workspace(dev)
+        out = {}
+        s_ = 4096
+        A = torch.randn(s_, s_, generator=g, dtype=torch.float64, device=dev)
+        B = torch.randn(s_, s_, generator=g, dtype=torch.float64, device=dev)
+        C = torch.empty_like(A)
+        ms, la = timed(lambda: gp.gemm(A, B, out=C, ws=gws), 3)
+        fl = 2.0 * s_ ** 3
+        out["gemm_4096"] = {"ms": ms, "gflops": fl / (ms / 1e3) / 1e9, "frac_of_fp64_peak": None, "launches": la}
+        ms, la = timed(lambda: gp.gemm_adjoint(A, B, C, ws=gws), 2)
+        out["gemm_adjoint_4096"] = {"ms": ms, "gflops": 2 * fl / (ms / 1e3) / 1e9, "launches": la}
+        del A, B, C
+        kk = 1 << 20
+        A = torch.randn(128, kk, generator=g, dtype=torch.float64, device=dev)
+        B = torch.randn(kk, 128, generator=g, dtype=torch.float64, device=dev)
+        C = torch.empty(128, 128, dtype=torch.float64, device=dev)
+        ms, la = timed(lambda: gp.gemm(A, B, out=C, ws=gws), 3)
+        out["gemm_128x128_k1M_splitk"] = {"ms": ms, "gflops": 2.0 * 128 * 128 * kk / (ms / 1e3) / 1e9, "launches": la}
+        del A, B, C
+        n_, k_ = args.glm_n, args.glm_k
+        X, y = W.glm_data(n_, k_, "bernoulli_logit", seed=0)
+        Xd, yd = torch.as_tensor(X, device=dev), torch.as_tensor(y, device=dev)
+        del X, y
+        beta = torch.zeros(k_, dtype=torch.float64, device=dev)
+        beta[0], beta[1] = 3.0, -2.0
+        gl_ws = gp.glm_workspace(k_, dev)
+        r = gp.glm("bernoulli_logit", Xd, yd, 1.0, beta)
+        ms, la = timed(lambda: gp.glm("bernoulli_logit", Xd, yd, 1.0, beta, ws=gl_ws), 20)
+        byts = 8.0 * (n_ * k_ + 2 * n_ + 2 * k_)
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        gp.trace_enable(True)
+        gp.glm("bernoulli_logit", Xd, yd, 1.0, beta)
+        torch.cuda.synchronize()
+        tr = gp.trace_summary()
+        gp.trace_enable(False)
+        kern_ms = tr["glm"]["ms"]
+        out["glm_bernoulli_logit"] = {
+            "n": n_, "k": k_, "ms": ms, "launches": la, "bytes": byts, "gbs": byts / (ms / 1e3) / 1e9,
+            "frac_of_hbm": byts / (ms / 1e3) / 1e9 / hbm, "glm_kernel_ms": kern_ms,
+            "glm_kernel_frac_of_hbm": byts / (kern_ms / 1e3) / 1e9 / hbm if kern_ms else None,
+            "lp": r["lp"].item(), "peak_source": "of measured: MEASURED_PEAKS hbm_gbs",
+            "l2": "X is 8 n k bytes, larger than L2"}
+        return out
+
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    extra = None
+    if not args.no_gemm_glm:
+        torch.cuda.nvtx.range_push("gemm_glm")
+        extra = run_gemm_glm()
+        torch.cuda.nvtx.range_pop()
+
     tri = None
     if not args.no_tri:
         torch.cuda.nvtx.range_push("tri")  # lets a profiler select this leg's launches
@@ -530,8 +606,6 @@ def main():
             batched["mixed"]["max_rel_value_diff_vs_fp64"] = float(
                 np.max(np.abs(vals["mixed"] - vals["fp64"]) / np.maximum(1.0, np.abs(vals["fp64"]))))
 
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     fp64_peak = gp.fp64_peak_gflops(dev)
     nominal_fp64 = peaks.get("bf16_tflops", 1900.0) * 1e3 * 1.25 / 2250.0
 
@@ -608,6 +682,10 @@ def main():
     }
     if batched is not None:
         line["batched"] = batched
+    if extra is not None:
+        for key in ("gemm_4096", "gemm_adjoint_4096", "gemm_128x128_k1M_splitk"):
+            extra[key]["frac_of_fp64_peak"] = extra[key]["gflops"] / fp64_peak
+        line["gemm_glm"] = extra
     if tri is not None:
         for leg in ("inverse", "solve_adjoint"):
             tri[leg]["frac_of_fp64_peak"] = tri[leg]["gflops"] / fp64_peak

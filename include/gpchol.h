@@ -222,6 +222,59 @@ int gpc_tri_solve_adjoint(int n, int m, const double *Linv, int ldi, const doubl
                           gpc_stream_t stream);
 
 /*
+ * General matrix product C = A B (Section 3.1, primitive function) on the FP64
+ * tensor path.  A: m x k (lda >= k), B: k x n (ldb >= n), C: m x n (ldc >= n),
+ * all row-major device arrays; C must not overlap A or B.  ws/ws_bytes: NULL/0,
+ * or at least gpc_gemm_workspace_size() bytes, which lets a product whose
+ * output is too small to fill the GPU split its k range over CTAs (the
+ * paper's large-k special case; partial products summed in a fixed order).
+ * k == 0 writes C = 0; m == 0 or n == 0 does nothing.  Errors:
+ * GPC_ERR_INVALID_ARG for negative sizes, null pointers, short leading
+ * dimensions, overlaps or a short non-null workspace (nothing enqueued);
+ * GPC_ERR_CUDA on a launch error.
+ */
+int gpc_gemm_workspace_size(size_t *bytes);
+int gpc_gemm(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+             void *ws, size_t ws_bytes, gpc_stream_t stream);
+
+/*
+ * Reverse mode of C = A B (Section 3.1, reverse mode function) for a scalar f
+ * with Cbar = df/dC (m x n, ldcb >= n):
+ *   Abar = Cbar B^T   (m x k, ldab >= k),    Bbar = A^T Cbar   (k x n, ldbb >= n).
+ * Both outputs are overwritten and must not overlap any input or each other.
+ * Workspace and errors as gpc_gemm.
+ */
+int gpc_gemm_adjoint(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                     const double *Cbar, int ldcb, double *Abar, int ldab, double *Bbar, int ldbb, void *ws,
+                     size_t ws_bytes, gpc_stream_t stream);
+
+/*
+ * Fused GLM log likelihood with its gradient (Section 3.4): for n
+ * observations with covariates X (n x k, row-major, ldx >= k) and targets y,
+ * eta_i = alpha + X_i . beta and, by family,
+ *   GPC_GLM_NORMAL_ID        y_i ~ Normal(eta_i, sigma)          (sigma > 0)
+ *   GPC_GLM_BERNOULLI_LOGIT  y_i ~ Bernoulli(1 / (1 + e^-eta_i)) (y_i in {0, 1})
+ *   GPC_GLM_POISSON_LOG      y_i ~ Poisson(e^eta_i)              (y_i = 0, 1, 2, ...)
+ * Writes lp = sum_i log p(y_i), dalpha = d lp / d alpha, dbeta (k) = d lp / d beta,
+ * and dsigma = d lp / d sigma (normal family; 0 otherwise); all four are
+ * device pointers.  alpha and sigma are host scalars; y and beta are device
+ * vectors.  One pass over X; results are bitwise reproducible.  The family's
+ * support of y is not checked.
+ *  - k <= GPC_GLM_MAX_K.  ws: at least gpc_glm_workspace_size(k) bytes.
+ *  - Errors: GPC_ERR_INVALID_ARG for an unknown family, n < 0, k < 0 or
+ *    k > GPC_GLM_MAX_K, sigma <= 0 (normal family), null pointers, ldx < k or
+ *    a short workspace (nothing enqueued); GPC_ERR_CUDA on a launch error.
+ */
+#define GPC_GLM_NORMAL_ID 0
+#define GPC_GLM_BERNOULLI_LOGIT 1
+#define GPC_GLM_POISSON_LOG 2
+#define GPC_GLM_MAX_K 12288
+int gpc_glm_workspace_size(int k, size_t *bytes);
+int gpc_glm(int family, long long n, int k, const double *X, long long ldx, const double *y, double alpha,
+            const double *beta, double sigma, double *lp, double *dalpha, double *dbeta, double *dsigma,
+            void *ws, size_t ws_bytes, gpc_stream_t stream);
+
+/*
  * Gaussian-process log marginal likelihood of y ~ N(0, K):
  *   L = chol(K), z = L^{-1} y, alpha = L^{-T} z, logdet = 2 sum log L_ii,
  *   value = -1/2 y^T alpha - 1/2 logdet - (n/2) log(2 pi).
@@ -327,7 +380,8 @@ int gpc_batched_gp_lml_grad(int batch, int nmax, const int *n, const long long *
 #define GPC_TRACE_GEMM_MIXED 6 /* split-BF16 tensor-core products */
 #define GPC_TRACE_SPLIT 7      /* FP64 -> BF16 slice splitting */
 #define GPC_TRACE_TRSM 8       /* FP64 panel solves against a diagonal block */
-#define GPC_TRACE_CLASSES 9
+#define GPC_TRACE_GLM 9        /* fused GLM likelihood and gradient */
+#define GPC_TRACE_CLASSES 10
 int gpc_launch_count(long long *count);
 
 /*

@@ -8,8 +8,8 @@ Two layers:
   * ``capi`` -- the C entry points with their C names (``capi.gpc_chol`` ...),
     taking raw integers for pointers and streams;
   * tensor functions with the same names minus the prefix (``chol``,
-    ``chol_adjoint``, ``gp_lml``, ``tri_solve`` ...) and the autograd
-    functions ``Chol``, ``GPLml`` and ``TriSolve``.
+    ``chol_adjoint``, ``gp_lml``, ``tri_solve``, ``gemm``, ``glm`` ...) and the
+    autograd functions ``Chol``, ``GPLml``, ``TriSolve``, ``MatMul`` and ``GLMLpmf``.
 There is no CPU fallback: without the compiled library every call raises.
 """
 from __future__ import annotations
@@ -55,6 +55,14 @@ _SIGNATURES = {
     "gpc_trsv": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_size, _c_vp], _c_int),
     "gpc_trsv_noalloc": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp], _c_int),
     "gpc_tri_inverse": ([_c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp], _c_int),
+    "gpc_gemm_workspace_size": ([ctypes.POINTER(_c_size)], _c_int),
+    "gpc_gemm": ([_c_int, _c_int, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_size, _c_vp],
+                 _c_int),
+    "gpc_gemm_adjoint": ([_c_int, _c_int, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int,
+                          _c_vp, _c_int, _c_vp, _c_size, _c_vp], _c_int),
+    "gpc_glm_workspace_size": ([_c_int, ctypes.POINTER(_c_size)], _c_int),
+    "gpc_glm": ([_c_int, ctypes.c_longlong, _c_int, _c_vp, ctypes.c_longlong, _c_vp, _c_double, _c_vp, _c_double,
+                 _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
     "gpc_tri_solve": ([_c_int, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp],
                       _c_int),
     "gpc_tri_solve_adjoint": ([_c_int, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int,
@@ -84,7 +92,9 @@ _SIGNATURES = {
 }
 
 TRACE_CLASSES = {"gemm_f64": 0, "diag": 1, "trsv": 2, "se_cov": 3, "hyper_grad": 4, "elementwise": 5,
-                 "gemm_mixed": 6, "split": 7, "trsm": 8}
+                 "gemm_mixed": 6, "split": 7, "trsm": 8, "glm": 9}
+GLM_FAMILIES = {"normal_id": 0, "bernoulli_logit": 1, "poisson_log": 2}
+GPC_GLM_MAX_K = 12288
 
 
 class GpcholError(RuntimeError):
@@ -392,6 +402,77 @@ def tri_solve_adjoint(Linv: torch.Tensor, C: torch.Tensor, Cbar: torch.Tensor,
     return Bb, Lb
 
 
+def gemm_workspace(device=None) -> torch.Tensor:
+    """Scratch that lets gemm / gemm_adjoint split long k ranges over CTAs."""
+    b = ctypes.c_size_t()
+    _check(capi.gpc_gemm_workspace_size(ctypes.byref(b)), "gpc_gemm_workspace_size")
+    return torch.empty(b.value, dtype=torch.uint8, device=device)
+
+
+def _rows(t: torch.Tensor, name: str) -> tuple[int, int, int]:
+    """(rows, cols, ld) of a row-major float64 CUDA matrix."""
+    if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 2):
+        raise ValueError(f"{name} must be a float64 CUDA matrix")
+    r, c = int(t.shape[0]), int(t.shape[1])
+    if r > 0 and c > 0 and t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (stride(1) == 1)")
+    return r, c, (int(t.stride(0)) if r > 0 and c > 0 else max(c, 1))
+
+
+def gemm(A: torch.Tensor, B: torch.Tensor, out: torch.Tensor | None = None,
+         ws: torch.Tensor | None = None) -> torch.Tensor:
+    """C = A B on the FP64 tensor path (ws: optional split-k scratch)."""
+    m, k, lda = _rows(A, "A")
+    k2, n, ldb = _rows(B, "B")
+    if k2 != k:
+        raise ValueError("inner dimensions differ")
+    C = out if out is not None else torch.empty(m, n, dtype=torch.float64, device=A.device)
+    _, _, ldc = _rows(C, "C")
+    _check(capi.gpc_gemm(m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, _ptr(ws),
+                         0 if ws is None else ws.numel(), _stream()), "gpc_gemm")
+    return C
+
+
+def gemm_adjoint(A: torch.Tensor, B: torch.Tensor, Cbar: torch.Tensor,
+                 ws: torch.Tensor | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """(Abar, Bbar) = (Cbar B^T, A^T Cbar) for C = A B."""
+    m, k, lda = _rows(A, "A")
+    _, n, ldb = _rows(B, "B")
+    _, _, ldcb = _rows(Cbar, "Cbar")
+    if tuple(Cbar.shape) != (m, n) or B.shape[0] != k:
+        raise ValueError("shape mismatch")
+    Abar = torch.empty(m, k, dtype=torch.float64, device=A.device)
+    Bbar = torch.empty(k, n, dtype=torch.float64, device=A.device)
+    _check(capi.gpc_gemm_adjoint(m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(Cbar), ldcb, _ptr(Abar), max(k, 1),
+                                 _ptr(Bbar), max(n, 1), _ptr(ws), 0 if ws is None else ws.numel(), _stream()),
+           "gpc_gemm_adjoint")
+    return Abar, Bbar
+
+
+def glm_workspace(k: int, device=None) -> torch.Tensor:
+    """Scratch for glm with k covariates (per-CTA partial gradient rows)."""
+    b = ctypes.c_size_t()
+    _check(capi.gpc_glm_workspace_size(int(k), ctypes.byref(b)), "gpc_glm_workspace_size")
+    return torch.empty(b.value, dtype=torch.uint8, device=device)
+
+
+def glm(family: str, X: torch.Tensor, y: torch.Tensor, alpha: float, beta: torch.Tensor, sigma: float = 1.0,
+        ws: torch.Tensor | None = None) -> dict:
+    """Fused GLM log likelihood and gradient: dict(lp, dalpha, dbeta, dsigma) of device tensors."""
+    n, k, ldx = _rows(X, "X")
+    _vector(y, n, "y")
+    _vector(beta, k, "beta")
+    dev = X.device
+    if ws is None:
+        ws = glm_workspace(k, dev)
+    out = torch.empty(3, dtype=torch.float64, device=dev)
+    dbeta = torch.empty(k, dtype=torch.float64, device=dev)
+    _check(capi.gpc_glm(GLM_FAMILIES[family], n, k, _ptr(X), ldx, _ptr(y), float(alpha), _ptr(beta), float(sigma),
+                        out.data_ptr(), out.data_ptr() + 8, _ptr(dbeta), out.data_ptr() + 16, _ptr(ws), ws.numel(),
+                        _stream()), "gpc_glm")
+    return {"lp": out[0], "dalpha": out[1], "dbeta": dbeta, "dsigma": out[2]}
+
+
 def gp_lml(K: torch.Tensor, y: torch.Tensor, precision="fp64", L: torch.Tensor | None = None,
            ws: torch.Tensor | None = None, info: torch.Tensor | None = None, check: bool = True):
     """Log marginal likelihood of y ~ N(0, K): returns dict(L, alpha, logdet, value).
@@ -611,6 +692,45 @@ class TriSolve(torch.autograd.Function):
 def mdivide_left_tri_low(L, B):
     """Differentiable L^{-1} B for lower-triangular L (upper triangle ignored)."""
     return TriSolve.apply(L, B)
+
+
+class MatMul(torch.autograd.Function):
+    """C = A B with the GEMM reverse mode (Abar = Cbar B^T, Bbar = A^T Cbar) as backward."""
+
+    @staticmethod
+    def forward(ctx, A, B):
+        A_, B_ = A.detach().contiguous(), B.detach().contiguous()
+        ctx.save_for_backward(A_, B_)
+        return gemm(A_, B_)
+
+    @staticmethod
+    def backward(ctx, Cbar):
+        A, B = ctx.saved_tensors
+        return gemm_adjoint(A, B, Cbar.contiguous())
+
+
+class GLMLpmf(torch.autograd.Function):
+    """GLM log likelihood of y given X, differentiable in alpha, beta and sigma
+    (the gradient comes from the same fused kernel as the value)."""
+
+    @staticmethod
+    def forward(ctx, X, y, alpha, beta, sigma, family):
+        r = glm(family, X.detach(), y.detach(), float(alpha), beta.detach().contiguous(), float(sigma))
+        ctx.save_for_backward(r["dalpha"].reshape(1), r["dbeta"], r["dsigma"].reshape(1))
+        ctx.devs = (alpha.device, sigma.device)
+        return r["lp"].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        da, db, ds = ctx.saved_tensors
+        return (None, None, (g * da[0]).to(ctx.devs[0]), g * db, (g * ds[0]).to(ctx.devs[1]), None)
+
+
+def glm_lpmf(family: str, X, y, alpha, beta, sigma=None):
+    """Differentiable GLM log likelihood; alpha and sigma are 0-d tensors (sigma only for normal_id)."""
+    if sigma is None:
+        sigma = torch.ones((), dtype=torch.float64)
+    return GLMLpmf.apply(X, y, alpha, beta, sigma, family)
 
 
 def gp_lml_value(X, y, hyp, jitter=0.0, precision="fp64"):

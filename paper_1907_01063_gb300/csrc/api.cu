@@ -221,6 +221,86 @@ int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, si
   return status_of(trsv(n, L, ldl, x, trans, ws, nullptr, stream));
 }
 
+int gpc_gemm_workspace_size(size_t *bytes) {
+  if (!bytes) return GPC_ERR_INVALID_ARG;
+  *bytes = gemm_f64_scratch_bytes();
+  return GPC_OK;
+}
+
+int gpc_gemm(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+             void *ws, size_t ws_bytes, gpc_stream_t stream) {
+  if (m < 0 || n < 0 || k < 0) return GPC_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return GPC_OK;
+  if (bad_rect(m, k, A, lda) || bad_rect(k, n, B, ldb) || bad_rect(m, n, C, ldc) ||
+      (ws && ws_bytes < gemm_f64_scratch_bytes()))
+    return GPC_ERR_INVALID_ARG;
+  const size_t cb = rect_bytes(m, n, ldc);
+  if (overlaps(C, cb, A, rect_bytes(m, k, lda)) || overlaps(C, cb, B, rect_bytes(k, n, ldb)) ||
+      (ws && overlaps(C, cb, ws, ws_bytes)))
+    return GPC_ERR_INVALID_ARG;
+  Gemm g;
+  g.M = m; g.N = n; g.K = k;
+  g.A = A; g.lda = lda;
+  g.B = B; g.ldb = ldb;
+  g.C = C; g.ldc = ldc;
+  return status_of(gemm_f64(g, (double *)ws, stream));
+}
+
+int gpc_gemm_adjoint(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                     const double *Cbar, int ldcb, double *Abar, int ldab, double *Bbar, int ldbb, void *ws,
+                     size_t ws_bytes, gpc_stream_t stream) {
+  if (m < 0 || n < 0 || k < 0) return GPC_ERR_INVALID_ARG;
+  if (bad_rect(m, k, A, lda) || bad_rect(k, n, B, ldb) || bad_rect(m, n, Cbar, ldcb) ||
+      bad_rect(m, k, Abar, ldab) || bad_rect(k, n, Bbar, ldbb) || (ws && ws_bytes < gemm_f64_scratch_bytes()))
+    return GPC_ERR_INVALID_ARG;
+  const size_t ab = rect_bytes(m, k, lda), bb = rect_bytes(k, n, ldb), cbb = rect_bytes(m, n, ldcb);
+  const size_t abb = rect_bytes(m, k, ldab), bbb = rect_bytes(k, n, ldbb);
+  const size_t wb = ws ? ws_bytes : 0;
+  if (overlaps(Abar, abb, A, ab) || overlaps(Abar, abb, B, bb) || overlaps(Abar, abb, Cbar, cbb) ||
+      overlaps(Abar, abb, Bbar, bbb) || overlaps(Bbar, bbb, A, ab) || overlaps(Bbar, bbb, B, bb) ||
+      overlaps(Bbar, bbb, Cbar, cbb) || overlaps(Abar, abb, ws, wb) || overlaps(Bbar, bbb, ws, wb))
+    return GPC_ERR_INVALID_ARG;
+  if (m > 0 && k > 0) {
+    Gemm a;  // Abar (m x k) = Cbar (m x n) B^T; B (k x n) is stored N x K
+    a.M = m; a.N = k; a.K = n;
+    a.A = Cbar; a.lda = ldcb;
+    a.transB = true; a.B = B; a.ldb = ldb;
+    a.C = Abar; a.ldc = ldab;
+    cudaError_t e = gemm_f64(a, (double *)ws, stream);
+    if (e != cudaSuccess) return status_of(e);
+  }
+  if (k > 0 && n > 0) {
+    Gemm b;  // Bbar (k x n) = A^T Cbar; A (m x k) is stored K x M
+    b.M = k; b.N = n; b.K = m;
+    b.transA = true; b.A = A; b.lda = lda;
+    b.B = Cbar; b.ldb = ldcb;
+    b.C = Bbar; b.ldc = ldbb;
+    cudaError_t e = gemm_f64(b, (double *)ws, stream);
+    if (e != cudaSuccess) return status_of(e);
+  }
+  return GPC_OK;
+}
+
+int gpc_glm_workspace_size(int k, size_t *bytes) {
+  if (!bytes || k < 0 || k > GPC_GLM_MAX_K) return GPC_ERR_INVALID_ARG;
+  *bytes = glm_workspace_bytes(k);
+  return GPC_OK;
+}
+
+int gpc_glm(int family, long long n, int k, const double *X, long long ldx, const double *y, double alpha,
+            const double *beta, double sigma, double *lp, double *dalpha, double *dbeta, double *dsigma,
+            void *ws, size_t ws_bytes, gpc_stream_t stream) {
+  if (family != GPC_GLM_NORMAL_ID && family != GPC_GLM_BERNOULLI_LOGIT && family != GPC_GLM_POISSON_LOG)
+    return GPC_ERR_INVALID_ARG;
+  if (n < 0 || k < 0 || k > GPC_GLM_MAX_K || !lp || !dalpha || !dsigma || !ws ||
+      ws_bytes < glm_workspace_bytes(k))
+    return GPC_ERR_INVALID_ARG;
+  if (family == GPC_GLM_NORMAL_ID && !(sigma > 0.0 && sigma <= 1.79769313486231570e308)) return GPC_ERR_INVALID_ARG;
+  if (!(alpha == alpha) || (k > 0 && (!beta || !dbeta)) || (n > 0 && (!y || (k > 0 && (!X || ldx < k)))))
+    return GPC_ERR_INVALID_ARG;
+  return status_of(glm(family, n, k, X, ldx, y, alpha, beta, sigma, lp, dalpha, dbeta, dsigma, ws, stream));
+}
+
 int gpc_tri_inverse(int n, const double *L, int ldl, double *Linv, int ldi, gpc_stream_t stream) {
   if (n < 0) return GPC_ERR_INVALID_ARG;
   if (n == 0) return GPC_OK;

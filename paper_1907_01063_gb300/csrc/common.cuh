@@ -102,6 +102,11 @@ cudaError_t lower_to_symmetric_half(int n, double *A, long long lda, cudaStream_
 cudaError_t reset_info(int *info, cudaStream_t s);
 
 // ---------------------------------------------------------------- drivers
+// Fused GLM likelihood and gradient (glm.cu).
+size_t glm_workspace_bytes(int k);
+cudaError_t glm(int family, long long n, int k, const double *X, long long ldx, const double *y, double alpha,
+                const double *beta, double sigma, double *lp, double *dalpha, double *dbeta, double *dsigma,
+                void *ws, cudaStream_t s);
 // Triangular inverse, solve and solve adjoint (trinv.cu); X is the inverse.
 cudaError_t tri_inverse(int n, const double *L, long long ldl, double *X, long long ldx, cudaStream_t s);
 cudaError_t tri_solve(int n, int m, const double *L, long long ldl, const double *B, long long ldb, double *X,

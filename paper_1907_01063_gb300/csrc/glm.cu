@@ -1,0 +1,192 @@
+// Fused GLM log likelihoods with their gradients (Section 3.4).
+//
+// For observations (x_i, y_i), i < n, the linear predictor is
+// eta_i = alpha + x_i . beta; each family gives lp_i and d_i = d lp_i / d eta_i:
+//   normal-identity  lp_i = -((y_i - eta_i)/sigma)^2/2 - log sigma - log(2 pi)/2,  d_i = (y_i - eta_i)/sigma^2
+//   Bernoulli-logit  lp_i = y_i eta_i - log(1 + e^eta_i),                          d_i = y_i - 1/(1 + e^-eta_i)
+//   Poisson-log      lp_i = y_i eta_i - e^eta_i - lgamma(y_i + 1),                  d_i = y_i - e^eta_i
+// and the outputs are lp = sum lp_i, dalpha = sum d_i, dbeta = X^T d and, for
+// the normal family, dsigma = sum ((y_i - eta_i)^2/sigma^3 - 1/sigma).
+//
+// As in the paper each likelihood is one kernel that produces the value and
+// the analytic gradient together; here the GEMV for dbeta is fused in as well,
+// so X (the only large operand) crosses HBM once.  A CTA walks blocks of R
+// rows: its warps first form eta_i for the block (one row per warp, lanes
+// strided over the row, a fixed-order shuffle reduction), then every thread
+// adds d_i x_ij for the columns it owns (j = thread, thread + 256, ...) over
+// the block's rows, re-reading the block from L1/L2.  The column sums stay in
+// shared memory for the CTA's whole share of rows and go out once as one
+// partial row; a second kernel adds the partial rows in CTA order.  Every sum
+// has a fixed order, so results are bitwise reproducible.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace gpc {
+namespace {
+
+constexpr int GT = 256;  // threads per CTA
+constexpr int kMaxRowsPerBlock = 64;
+
+struct GlmParams {
+  int family, k, R;
+  long long n, ldx;
+  const double *X, *y, *beta;
+  double alpha, inv_sigma, log_norm;  // log_norm = log(sigma) + log(2 pi)/2
+  double *part, *part_s;
+};
+
+__device__ __forceinline__ void glm_row(const GlmParams &p, double eta, double y, double &lp, double &d,
+                                        double &ds) {
+  if (p.family == GPC_GLM_NORMAL_ID) {
+    const double r = y - eta, z = r * p.inv_sigma;
+    lp = -0.5 * z * z - p.log_norm;
+    d = z * p.inv_sigma;
+    ds = (z * z - 1.0) * p.inv_sigma;
+  } else if (p.family == GPC_GLM_BERNOULLI_LOGIT) {
+    const double e = exp(-fabs(eta));  // log(1 + e^eta) = max(eta, 0) + log1p(e^-|eta|)
+    lp = y * eta - (fmax(eta, 0.0) + log1p(e));
+    d = y - (eta >= 0.0 ? 1.0 / (1.0 + e) : e / (1.0 + e));
+    ds = 0.0;
+  } else {
+    const double mu = exp(eta);
+    lp = y * eta - mu - lgamma(y + 1.0);
+    d = y - mu;
+    ds = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(GT) glm_kernel(GlmParams p) {
+  extern __shared__ double sm[];
+  double *acc = sm;             // k column sums; thread t owns j = t, t + GT, ...
+  double *bs = sm + p.k;        // beta
+  double *dblk = bs + p.k;      // d_i of the current block's rows
+  __shared__ double red[3][GT / 32];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int j = t; j < p.k; j += GT) {
+    acc[j] = 0.0;
+    bs[j] = p.beta[j];
+  }
+  __syncthreads();
+  double slp = 0.0, sda = 0.0, sds = 0.0;  // meaningful in lane 0 of each warp
+  const long long nblk = (p.n + p.R - 1) / p.R;
+  for (long long b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const long long i0 = b * p.R;
+    const int rows = (int)min((long long)p.R, p.n - i0);
+    for (int r = warp; r < rows; r += GT / 32) {
+      const double *x = p.X + (i0 + r) * p.ldx;
+      double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      int j = lane;
+      for (; j + 7 * 32 < p.k; j += 8 * 32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[u] = fma(x[j + 32 * u], bs[j + 32 * u], s[u]);
+      }
+      for (; j < p.k; j += 32) s[0] = fma(x[j], bs[j], s[0]);
+      double v = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        double lp, d, ds;
+        glm_row(p, v + p.alpha, p.y[i0 + r], lp, d, ds);
+        dblk[r] = d;
+        slp += lp;
+        sda += d;
+        sds += ds;
+      }
+    }
+    __syncthreads();
+    for (int j = t; j < p.k; j += GT) {
+      double a = acc[j];
+      const double *xc = p.X + i0 * p.ldx + j;
+      for (int r = 0; r < rows; ++r) a = fma(xc[(long long)r * p.ldx], dblk[r], a);
+      acc[j] = a;
+    }
+    __syncthreads();
+  }
+  for (int j = t; j < p.k; j += GT) p.part[(long long)blockIdx.x * p.k + j] = acc[j];
+  if (lane == 0) {
+    red[0][warp] = slp;
+    red[1][warp] = sda;
+    red[2][warp] = sds;
+  }
+  __syncthreads();
+  if (t < 3) {
+    double v = 0.0;
+    for (int w = 0; w < GT / 32; ++w) v += red[t][w];
+    p.part_s[3LL * blockIdx.x + t] = v;
+  }
+}
+
+// dbeta_j = sum over CTAs of the partial rows, and the three scalars, in CTA order.
+__global__ void glm_reduce_kernel(int k, int ctas, const double *part, const double *part_s, double *dbeta,
+                                  double *lp, double *dalpha, double *dsigma) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) {
+    double s = 0.0;
+    for (int c = 0; c < ctas; ++c) s += part[(long long)c * k + j];
+    dbeta[j] = s;
+  } else if (j < k + 3) {
+    const int q = j - k;
+    double s = 0.0;
+    for (int c = 0; c < ctas; ++c) s += part_s[3LL * c + q];
+    double *dst = q == 0 ? lp : (q == 1 ? dalpha : dsigma);
+    *dst = s;
+  }
+}
+
+int rows_per_block(int k) {
+  const int r = 16384 / std::max(k, 1);  // about 128 KiB of X per block, re-read from L1/L2
+  return std::max(8, std::min(kMaxRowsPerBlock, r / 8 * 8));
+}
+
+size_t smem_bytes(int k) { return (2 * (size_t)k + kMaxRowsPerBlock) * sizeof(double); }
+
+int max_ctas(int k) {
+  const size_t per = smem_bytes(k) + 1024;
+  const int by_smem = (int)std::max<size_t>(1, (size_t)(228 * 1024) / per);
+  return sm_count() * std::max(1, std::min(4, by_smem));
+}
+
+}  // namespace
+
+size_t glm_workspace_bytes(int k) {
+  const size_t ctas = (size_t)max_ctas(k);
+  return align_up(ctas * (size_t)std::max(k, 1) * sizeof(double), 256) + align_up(ctas * 3 * sizeof(double), 256);
+}
+
+cudaError_t glm(int family, long long n, int k, const double *X, long long ldx, const double *y, double alpha,
+                const double *beta, double sigma, double *lp, double *dalpha, double *dbeta, double *dsigma,
+                void *ws, cudaStream_t s) {
+  GlmParams p;
+  p.family = family;
+  p.n = n;
+  p.k = k;
+  p.R = rows_per_block(k);
+  p.ldx = ldx;
+  p.X = X;
+  p.y = y;
+  p.beta = beta;
+  p.alpha = alpha;
+  p.inv_sigma = family == GPC_GLM_NORMAL_ID ? 1.0 / sigma : 1.0;
+  p.log_norm = family == GPC_GLM_NORMAL_ID ? log(sigma) + 0.91893853320467274178 : 0.0;
+  const long long nblk = std::max<long long>(1, (n + p.R - 1) / p.R);
+  const int ctas = (int)std::min<long long>(nblk, max_ctas(k));
+  char *w = (char *)ws;
+  p.part = (double *)w;
+  p.part_s = (double *)(w + align_up((size_t)max_ctas(k) * (size_t)std::max(k, 1) * sizeof(double), 256));
+  const size_t smem = smem_bytes(k);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(glm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const double bytes = 8.0 * ((double)n * k + 2.0 * n + k);
+  GPC_LAUNCH(GPC_TRACE_GLM, 4.0 * (double)n * k, bytes, s, glm_kernel<<<ctas, GT, smem, s>>>(p));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  GPC_LAUNCH(GPC_TRACE_ELEM, (double)ctas * (k + 3), 8.0 * (double)ctas * (k + 3), s,
+             glm_reduce_kernel<<<(k + 3 + 255) / 256, 256, 0, s>>>(k, ctas, p.part, p.part_s, dbeta, lp, dalpha,
+                                                                    dsigma));
+  return cudaGetLastError();
+}
+
+}  // namespace gpc

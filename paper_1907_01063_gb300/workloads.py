@@ -97,3 +97,23 @@ def paper_gp_1d(n: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
     f = (f - f.mean()) / max(f.std(), 1e-300)
     y = f + math.sqrt(0.1) * torch.randn(n, generator=g, dtype=torch.float64).numpy()
     return x[:, None], y
+
+
+def glm_data(n: int, k: int, family: str = "bernoulli_logit", seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Toy GLM data after the logistic-regression experiment of Section 4.1:
+    X ~ N(0, 1) (n x k, k >= 2), latent mu_i = 3 X_i1 - 2 X_i2 + 1 (the other
+    columns are noise); y_i ~ Bernoulli(1 / (1 + e^-mu_i)).  The Poisson-log
+    and normal-identity variants use the same X with y_i ~ Poisson(e^(mu_i / 4))
+    and y_i ~ N(mu_i, 1)."""
+    g = _gen(seed)
+    X = torch.randn(n, k, generator=g, dtype=torch.float64).numpy()
+    mu = 3.0 * X[:, 0] - 2.0 * X[:, 1] + 1.0 if k >= 2 else np.ones(n)
+    u = torch.rand(n, generator=g, dtype=torch.float64).numpy()
+    if family == "bernoulli_logit":
+        y = (u < 1.0 / (1.0 + np.exp(-mu))).astype(np.float64)
+    elif family == "poisson_log":
+        y = torch.poisson(torch.as_tensor(np.exp(mu / 4.0)), generator=g).numpy().astype(np.float64)
+    else:
+        y = mu + torch.randn(n, generator=g, dtype=torch.float64).numpy()
+    return X, y
+

@@ -123,3 +123,37 @@ def test_triangular_argument_checks_return_before_any_launch():
     assert c.gpc_tri_inverse(0, None, 0, None, 0, None) == gp.GPC_OK
     assert c.gpc_tri_solve(0, 5, None, 0, None, 0, None, 0, None, 0, None) == gp.GPC_OK
     assert c.gpc_tri_solve_adjoint(0, 5, None, 0, None, 0, None, 0, None, 0, None, 0, None) == gp.GPC_OK
+
+
+def test_gemm_and_glm_argument_checks_return_before_any_launch():
+    c = gp.capi
+    bad = gp.GPC_ERR_INVALID_ARG
+    fake, far, farther = 0x1000, 0x100000, 0x200000  # never dereferenced
+    size = ctypes.c_size_t()
+    assert c.gpc_gemm_workspace_size(ctypes.byref(size)) == gp.GPC_OK and size.value > 0
+    assert c.gpc_gemm(-1, 2, 2, fake, 2, far, 2, farther, 2, None, 0, None) == bad
+    assert c.gpc_gemm(4, 3, 2, fake, 1, far, 3, farther, 3, None, 0, None) == bad  # lda < k
+    assert c.gpc_gemm(4, 3, 2, fake, 2, far, 3, fake, 3, None, 0, None) == bad  # C overlaps A
+    assert c.gpc_gemm(4, 3, 2, fake, 2, far, 3, farther, 3, 0x300000, 16, None) == bad  # short workspace
+    assert c.gpc_gemm(4, 3, 2, None, 2, far, 3, farther, 3, None, 0, None) == bad
+    assert c.gpc_gemm(0, 3, 2, None, 2, None, 3, None, 3, None, 0, None) == gp.GPC_OK
+    assert c.gpc_gemm_adjoint(4, 3, 2, fake, 2, far, 3, farther, 3, fake, 2, 0x300000, 3, None, 0,
+                              None) == bad  # Abar == A
+    assert c.gpc_gemm_adjoint(4, 3, 2, fake, 2, far, 3, farther, 3, 0x300000, 2, 0x300000, 3, None, 0,
+                              None) == bad  # Abar overlaps Bbar
+    assert c.gpc_glm_workspace_size(-1, ctypes.byref(size)) == bad
+    assert c.gpc_glm_workspace_size(gp.GPC_GLM_MAX_K + 1 if hasattr(gp, "GPC_GLM_MAX_K") else 12289,
+                                    ctypes.byref(size)) == bad
+    assert c.gpc_glm_workspace_size(100, ctypes.byref(size)) == gp.GPC_OK
+    ws = size.value
+    out = 0x400000
+    assert c.gpc_glm(7, 10, 3, fake, 3, far, 0.0, farther, 1.0, out, out + 8, out + 32, out + 16, 0x500000, ws,
+                     None) == bad  # family
+    assert c.gpc_glm(0, 10, 3, fake, 3, far, 0.0, farther, 0.0, out, out + 8, out + 32, out + 16, 0x500000, ws,
+                     None) == bad  # sigma <= 0 for the normal family
+    assert c.gpc_glm(1, 10, 3, fake, 2, far, 0.0, farther, 1.0, out, out + 8, out + 32, out + 16, 0x500000, ws,
+                     None) == bad  # ldx < k
+    assert c.gpc_glm(1, 10, 3, fake, 3, far, 0.0, farther, 1.0, out, out + 8, out + 32, out + 16, 0x500000, 8,
+                     None) == bad  # short workspace
+    assert c.gpc_glm(1, 10, 3, fake, 3, None, 0.0, farther, 1.0, out, out + 8, out + 32, out + 16, 0x500000, ws,
+                     None) == bad  # no y
