@@ -11,10 +11,14 @@
 // As in the paper each likelihood is one kernel that produces the value and
 // the analytic gradient together; here the GEMV for dbeta is fused in as well,
 // so X (the only large operand) crosses HBM once.  A CTA walks blocks of R
-// rows: its warps first form eta_i for the block (one row per warp, lanes
-// strided over the row, a fixed-order shuffle reduction), then every thread
-// adds d_i x_ij for the columns it owns (j = thread, thread + 256, ...) over
-// the block's rows, re-reading the block from L1/L2.  The column sums stay in
+// rows: its warps first form eta_i for the block (four rows per warp, lanes
+// strided over the columns, a fixed-order shuffle reduction), then one thread
+// per row evaluates the family's terms, then every thread adds d_i x_ij for
+// the columns it owns (j = thread, thread + 256, ...) over the block's rows,
+// re-reading the block from L1/L2.  FP64 work (two multiply-adds per element
+// of X) rather than HBM bounds this on GB300, so every FP64 instruction
+// carries 32 active lanes: the per-row exp/log1p run one row per thread, not
+// on one lane of a warp.  The column sums stay in
 // shared memory for the CTA's whole share of rows and go out once as one
 // partial row; a second kernel adds the partial rows in CTA order.  Every sum
 // has a fixed order, so results are bitwise reproducible.
@@ -58,9 +62,10 @@ __device__ __forceinline__ void glm_row(const GlmParams &p, double eta, double y
 
 __global__ void __launch_bounds__(GT) glm_kernel(GlmParams p) {
   extern __shared__ double sm[];
-  double *acc = sm;             // k column sums; thread t owns j = t, t + GT, ...
-  double *bs = sm + p.k;        // beta
-  double *dblk = bs + p.k;      // d_i of the current block's rows
+  double *acc = sm;                      // k column sums; thread t owns j = t, t + GT, ...
+  double *bs = sm + p.k;                 // beta
+  double *eta_s = bs + p.k;              // eta of the current block's rows
+  double *dblk = eta_s + kMaxRowsPerBlock;  // d_i of the current block's rows
   __shared__ double red[3][GT / 32];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   for (int j = t; j < p.k; j += GT) {
@@ -68,42 +73,74 @@ __global__ void __launch_bounds__(GT) glm_kernel(GlmParams p) {
     bs[j] = p.beta[j];
   }
   __syncthreads();
-  double slp = 0.0, sda = 0.0, sds = 0.0;  // meaningful in lane 0 of each warp
+  double slp = 0.0, sda = 0.0, sds = 0.0;  // per thread (threads below R)
   const long long nblk = (p.n + p.R - 1) / p.R;
   for (long long b = blockIdx.x; b < nblk; b += gridDim.x) {
     const long long i0 = b * p.R;
     const int rows = (int)min((long long)p.R, p.n - i0);
-    for (int r = warp; r < rows; r += GT / 32) {
-      const double *x = p.X + (i0 + r) * p.ldx;
-      double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-      int j = lane;
-      for (; j + 7 * 32 < p.k; j += 8 * 32) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s[u] = fma(x[j + 32 * u], bs[j + 32 * u], s[u]);
+    // eta for four rows per warp: four independent FMA chains per lane, then a
+    // transposed butterfly that leaves row 2 bit4 + bit3 of the lane index in
+    // every lane (6 adds for the four rows).  Missing rows of a short last
+    // group re-read the group's first row and are not stored.
+    for (int g = warp; 4 * g < rows; g += GT / 32) {
+      const int r0 = 4 * g, nr = min(4, rows - r0);
+      const double *x0 = p.X + (i0 + r0) * p.ldx;
+      const double *x1 = nr > 1 ? x0 + p.ldx : x0;
+      const double *x2 = nr > 2 ? x0 + 2 * p.ldx : x0;
+      const double *x3 = nr > 3 ? x0 + 3 * p.ldx : x0;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 2
+      for (int j = lane; j < p.k; j += 32) {
+        const double bj = bs[j];
+        s0 = fma(x0[j], bj, s0);
+        s1 = fma(x1[j], bj, s1);
+        s2 = fma(x2[j], bj, s2);
+        s3 = fma(x3[j], bj, s3);
       }
-      for (; j < p.k; j += 32) s[0] = fma(x[j], bs[j], s[0]);
-      double v = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) {
-        double lp, d, ds;
-        glm_row(p, v + p.alpha, p.y[i0 + r], lp, d, ds);
-        dblk[r] = d;
-        slp += lp;
-        sda += d;
-        sds += ds;
-      }
+      const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+      double k0 = h16 ? s2 : s0, k1 = h16 ? s3 : s1;
+      k0 += __shfl_xor_sync(0xffffffffu, h16 ? s0 : s2, 16);
+      k1 += __shfl_xor_sync(0xffffffffu, h16 ? s1 : s3, 16);
+      double v = h8 ? k1 : k0;
+      v += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      const int row = ((lane >> 4) << 1) | ((lane >> 3) & 1);
+      if ((lane & 7) == 0 && row < nr) eta_s[r0 + row] = v + p.alpha;
     }
     __syncthreads();
+    // the family's terms, one row per thread
+    if (t < rows) {
+      double lp, d, ds;
+      glm_row(p, eta_s[t], p.y[i0 + t], lp, d, ds);
+      dblk[t] = d;
+      slp += lp;
+      sda += d;
+      sds += ds;
+    }
+    __syncthreads();
+    // dbeta: column-owned sums over the block's rows (two chains), X from L1/L2
     for (int j = t; j < p.k; j += GT) {
-      double a = acc[j];
       const double *xc = p.X + i0 * p.ldx + j;
-      for (int r = 0; r < rows; ++r) a = fma(xc[(long long)r * p.ldx], dblk[r], a);
-      acc[j] = a;
+      double a0 = 0.0, a1 = 0.0;
+      int r = 0;
+      for (; r + 1 < rows; r += 2) {
+        a0 = fma(xc[(long long)r * p.ldx], dblk[r], a0);
+        a1 = fma(xc[(long long)(r + 1) * p.ldx], dblk[r + 1], a1);
+      }
+      if (r < rows) a0 = fma(xc[(long long)r * p.ldx], dblk[r], a0);
+      acc[j] += a0 + a1;
     }
     __syncthreads();
   }
   for (int j = t; j < p.k; j += GT) p.part[(long long)blockIdx.x * p.k + j] = acc[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    slp += __shfl_down_sync(0xffffffffu, slp, o);
+    sda += __shfl_down_sync(0xffffffffu, sda, o);
+    sds += __shfl_down_sync(0xffffffffu, sds, o);
+  }
   if (lane == 0) {
     red[0][warp] = slp;
     red[1][warp] = sda;
@@ -139,7 +176,7 @@ int rows_per_block(int k) {
   return std::max(8, std::min(kMaxRowsPerBlock, r / 8 * 8));
 }
 
-size_t smem_bytes(int k) { return (2 * (size_t)k + kMaxRowsPerBlock) * sizeof(double); }
+size_t smem_bytes(int k) { return (2 * (size_t)k + 2 * kMaxRowsPerBlock) * sizeof(double); }
 
 int max_ctas(int k) {
   const size_t per = smem_bytes(k) + 1024;
