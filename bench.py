@@ -685,6 +685,13 @@ def main():
     if extra is not None:
         for key in ("gemm_4096", "gemm_adjoint_4096", "gemm_128x128_k1M_splitk"):
             extra[key]["frac_of_fp64_peak"] = extra[key]["gflops"] / fp64_peak
+        gl = extra["glm_bernoulli_logit"]
+        if gl["glm_kernel_ms"]:
+            # two FP64 multiply-adds per element of X (eta, then X^T d): on GB300 the
+            # FP64 pipe, not HBM, bounds the kernel
+            gl["fp64_gflops"] = 4.0 * gl["n"] * gl["k"] / (gl["glm_kernel_ms"] / 1e3) / 1e9
+            gl["frac_of_fp64_peak"] = gl["fp64_gflops"] / fp64_peak
+            gl["bound"] = "alu (FP64)"
         line["gemm_glm"] = extra
     if tri is not None:
         for leg in ("inverse", "solve_adjoint"):
