@@ -5,6 +5,9 @@ fastest; results are cached per device name and workload shape in a JSON
 file (``GPCHOL_TUNE_CACHE``, default ``~/.cache/gpchol/tune.json``) so later
 runs apply them without timing again.
 
+Offline (``tune_*``: dedicated timing runs, cached) and online
+(``OnlineTuner``: the caller's own repeated calls are the timing runs).
+
 Knobs:
   * batch_block: block size inside the batched per-GP pass (32 or 64), timed
     on a batch of GPs with the caller's size mix, separately per precision.
@@ -116,6 +119,107 @@ def tune_fp64_block(n: int = 4096, force: bool = False) -> dict:
     db[key] = rec
     _store(db)
     return rec
+
+
+class _EventTimer:
+    """CUDA-event pairs on the current stream; read back only when asked."""
+
+    def start(self):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        return (e0, e1)
+
+    def stop(self, token):
+        token[1].record()
+
+    def elapsed_ms(self, token) -> float:
+        token[1].synchronize()
+        return token[0].elapsed_time(token[1])
+
+
+class OnlineTuner:
+    """Online tuning across repeated calls (Section 5): an MCMC or optimisation
+    loop calls the same primitive with the same input sizes every iteration, so
+    the calls themselves serve as the timing runs.
+
+    For each key (the caller's description of the call and its sizes) the
+    first ``len(candidates) * reps`` calls run with the candidate values of
+    ``knob`` in turn, each bracketed by a timer pair on the caller's stream
+    (no synchronisation while exploring).  At the next call the times are read
+    back once, the candidate with the smallest mean is kept (ties: the earlier
+    candidate), and every later call of that key runs with it untimed.  The
+    knob is set before each call and restored right after it is enqueued (the
+    library reads it at enqueue time), so other code sees no change.
+
+    ``setter``/``getter`` default to ``gp.set_tuning``/``gp.get_tuning`` and
+    ``timer`` to CUDA events; tests pass fakes.  A knob that changes workspace
+    sizes (the FP64 block does) needs ``fn`` to size its own workspace.
+    """
+
+    def __init__(self, knob: int, candidates, reps: int = 1, timer=None, setter=None, getter=None):
+        if not candidates or reps < 1:
+            raise ValueError("need at least one candidate and one repetition")
+        self.knob = knob
+        self.candidates = list(candidates)
+        self.reps = int(reps)
+        self._timer = timer if timer is not None else _EventTimer()
+        self._set = setter if setter is not None else gp.set_tuning
+        self._get = getter if getter is not None else gp.get_tuning
+        self._state = {}  # key -> {"samples": [(candidate index, token)], "best": value or None, "ms": {}}
+
+    def _schedule(self, i: int) -> int:
+        return i // self.reps
+
+    def _decide(self, st: dict):
+        sums, counts = {}, {}
+        for ci, tok in st["samples"]:
+            ms = self._timer.elapsed_ms(tok)
+            sums[ci] = sums.get(ci, 0.0) + ms
+            counts[ci] = counts.get(ci, 0) + 1
+        means = {ci: sums[ci] / counts[ci] for ci in sums}
+        best = min(sorted(means), key=lambda ci: means[ci])
+        st["best"] = self.candidates[best]
+        st["ms"] = {self.candidates[ci]: m for ci, m in means.items()}
+        st["samples"] = []
+
+    def __call__(self, key, fn):
+        st = self._state.setdefault(key, {"samples": [], "best": None, "ms": {}, "calls": 0})
+        explore = len(self.candidates) * self.reps
+        if st["best"] is None and st["calls"] >= explore:
+            self._decide(st)
+        old = self._get(self.knob)
+        if st["best"] is not None:
+            value, tok = st["best"], None
+        else:
+            ci = self._schedule(st["calls"])
+            value = self.candidates[ci]
+        try:
+            self._set(self.knob, value)
+            if st["best"] is None:
+                tok = self._timer.start()
+                out = fn()
+                self._timer.stop(tok)
+                st["samples"].append((ci, tok))
+            else:
+                out = fn()
+        finally:
+            self._set(self.knob, old)
+        st["calls"] += 1
+        return out
+
+    def best(self, key):
+        """The value chosen for key (None while still exploring)."""
+        st = self._state.get(key)
+        if st is None:
+            return None
+        if st["best"] is None and st["calls"] >= len(self.candidates) * self.reps:
+            self._decide(st)
+        return st["best"]
+
+    def times(self, key) -> dict:
+        """Mean milliseconds per candidate for key, once decided."""
+        self.best(key)
+        return dict(self._state.get(key, {}).get("ms", {}))
 
 
 def apply_cached() -> dict:
