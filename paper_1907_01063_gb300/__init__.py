@@ -15,7 +15,6 @@ There is no CPU fallback: without the compiled library every call raises.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import torch

@@ -5,7 +5,6 @@ stated bar for jittered SE matrices with condition number <= 1e6), and the
 same relative bound on scalars.  Sizes span several 64-wide GEMM tiles and
 128-wide factorisation blocks with ragged tails.
 """
-import math
 
 import numpy as np
 import pytest

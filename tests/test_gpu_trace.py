@@ -1,5 +1,4 @@
 """Launch trace and timeline (measurement support) through the C ABI."""
-import numpy as np
 import pytest
 import torch
 
