@@ -263,25 +263,40 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def batched_workload(batch: int, d: int = 4, seed: int = 0, sigma: float = 0.1):
-    """512 GPs with n_i ~ U{64..1024}, X ~ N(0, 1) in d = 4, rho_i ~ U(0.2, 2),
-    alpha = 1, sigma = 0.1; targets from an approximate GP draw."""
+def batched_sizes(batch: int, seed: int = 0) -> list[int]:
+    from paper_1907_01063_gb300 import workloads as W
+    return [int(v) for v in W.batch_sizes(batch, 64, 1024, seed=seed)]
+
+
+def batched_workload(batch: int, d: int = 4, seed: int = 0, sigma: float = 0.1, indices=None):
+    """A batch of GPs with n_i ~ U{64..1024}, X ~ N(0, 1) in d = 4, rho_i ~ U(0.2, 2),
+    alpha = 1, sigma = 0.1; targets from an approximate GP draw.  Every GP has its
+    own seeds, so ``indices`` (a rank's share) generates just those GPs."""
     from paper_1907_01063_gb300 import workloads as W
     import numpy as np
-    sizes = W.batch_sizes(batch, 64, 1024, seed=seed)
-    rho = W.batch_lengthscales(batch, 0.2, 2.0, seed=seed + 1)
+    sizes_all = batched_sizes(batch, seed)
+    rho_all = W.batch_lengthscales(batch, 0.2, 2.0, seed=seed + 1)
+    idx = list(range(batch)) if indices is None else list(indices)
     Xs, ys = [], []
-    for i, n in enumerate(sizes):
-        X = W.gp_inputs(int(n), d, seed=1000 + i)
+    for i in idx:
+        X = W.gp_inputs(sizes_all[i], d, seed=1000 + i)
         Xs.append(X)
-        ys.append(W.gp_targets(X, 1.0, float(rho[i]), sigma, seed=2000 + i, features=256))
-    hyp = np.stack([np.ones(batch), rho, np.full(batch, sigma)], axis=1)
-    return [int(v) for v in sizes], np.concatenate(Xs), np.concatenate(ys), hyp
+        ys.append(W.gp_targets(X, 1.0, float(rho_all[i]), sigma, seed=2000 + i, features=256))
+    hyp = np.stack([np.ones(len(idx)), rho_all[idx], np.full(len(idx), sigma)], axis=1)
+    return [sizes_all[i] for i in idx], np.concatenate(Xs), np.concatenate(ys), hyp
 
 
-def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned, prec):
+def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, rank, tuned, prec):
+    """The batched workload, sharded: with N ranks the job is N x batch GPs, dealt
+    to the ranks by cost (shard.partition_by_cost), so each rank has about one
+    batch of work (weak scaling); per-GP results are gathered once after the
+    timed region.  With one rank the shard is the whole batch."""
     import torch
-    sizes, X, y, hyp = batched_workload(args.batch)
+    from paper_1907_01063_gb300 import shard
+    total = args.batch * world
+    sizes_all = batched_sizes(total)
+    mine = shard.partition_by_cost(sizes_all, world)[rank]
+    sizes, X, y, hyp = batched_workload(total, indices=mine)
     b = gp.Batch(sizes, device=dev, precision=prec)
     Xd = torch.as_tensor(X, device=dev).contiguous()
     yd = torch.as_tensor(y, device=dev).contiguous()
@@ -290,7 +305,7 @@ def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned, pr
         from paper_1907_01063_gb300 import autotune
         tuned[f"batch_block_{prec}"] = autotune.tune_batch_block(b, Xd, yd, hd)["best"]
     nb = gp.get_tuning(gp.GPC_TUNE_BATCH_BLOCK)
-    flops = sum(chol_flops(n) + adjoint_flops(n, nb) for n in sizes)
+    flops_all = sum(chol_flops(n) + adjoint_flops(n, nb) for n in sizes_all)
     # one persistent launch per step, captured once in a CUDA graph and replayed
     gp.batched_gp_lml_grad(b, Xd, yd, hd)
     torch.cuda.synchronize()
@@ -300,7 +315,6 @@ def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned, pr
     for _ in range(args.warmup):
         graph.replay()
     barrier()
-    launches0 = gp.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -308,15 +322,20 @@ def run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned, pr
     e1.record(stream)
     barrier()
     t_ms = max_over_ranks(e0.elapsed_time(e1))
-    info = b.info.cpu().numpy()
-    return {"workload": f"{args.batch} GPs, n_i ~ U{{64..1024}}, d=4, SE kernel, rho_i ~ U(0.2,2), sigma=0.1 ({prec})",
-            "value": whole_job_rate(world, args.steps, flops, t_ms) / 1e9, "unit": "GFLOP/s",
-            "gp_per_s": whole_job_rate(world, args.steps, args.batch, t_ms), "ms_per_step": t_ms / args.steps,
-            "flops_per_step": flops, "sum_n": int(sum(sizes)), "max_n": int(max(sizes)),
-            "cuda_graph": True, "kernels_per_step": 2, "block": nb,
-            "all_ok": bool((info[:, 1] == 0).all()),
-            "value_checksum": float(b.value.double().sum().item()),
-            "_values": b.value.cpu().numpy()}
+    values, _ = shard.gather_results(mine, b.value, b.grad3, total, world, device=dev)
+    info_ok = torch.tensor([float((b.info[:, 1] == 0).all().item())], dtype=torch.float64, device=dev)
+    all_ok = max_over_ranks(-info_ok.item()) <= -1.0  # every rank's GPs finished
+    rate = args.steps / (t_ms / 1e3)
+    return {"workload": f"{total} GPs ({args.batch} per GPU, dealt by n^3), n_i ~ U{{64..1024}}, d=4, SE kernel, "
+                        f"rho_i ~ U(0.2,2), sigma=0.1 ({prec})",
+            "value": rate * flops_all / 1e9, "unit": "GFLOP/s",
+            "gp_per_s": rate * total, "ms_per_step": t_ms / args.steps,
+            "flops_per_step": flops_all, "gps": total, "gps_this_rank": len(mine),
+            "sum_n": int(sum(sizes_all)), "max_n": int(max(sizes_all)),
+            "cuda_graph": True, "kernels_per_step": 2, "block": nb, "sharding": "by n^3, no collective in the step",
+            "all_ok": bool(all_ok),
+            "value_checksum": float(values.double().sum().item()),
+            "_values": values.cpu().numpy()}
 
 
 def main():
@@ -599,7 +618,7 @@ def main():
     if not args.no_batched:
         batched = {}
         for bp in precisions:
-            batched[bp] = run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, tuned, bp)
+            batched[bp] = run_batched(args, gp, dev, stream, barrier, max_over_ranks, world, rank, tuned, bp)
         vals = {bp: r.pop("_values") for bp, r in batched.items()}
         if "fp64" in vals and "mixed" in vals:
             import numpy as np

@@ -219,3 +219,24 @@ def test_batched_fp64_workspace_refuses_mixed_run():
     y = torch.zeros(30, dtype=torch.float64, device="cuda")
     with pytest.raises(gp.GpcholError):
         gp.batched_gp_lml_grad(b, X, y, torch.ones(2, 3, dtype=torch.float64), precision="mixed")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sharded_batch_matches_whole_batch(precision):
+    """The GPs of a batch run as three shards dealt by cost (one launch each,
+    one after another on this GPU) give the whole batch's results."""
+    from paper_1907_01063_gb300 import shard
+    sizes = [int(v) for v in W.batch_sizes(24, 16, 300, seed=5)]
+    Xs, ys, hyps = make_batch(sizes, seed=7)
+    _, v0, g0, info0 = run_batch(sizes, Xs, ys, hyps, precision=precision)
+    assert np.all(info0[:, 1] == gp.GPC_OK)
+    v, g = np.full(len(sizes), np.nan), np.full((len(sizes), 3), np.nan)
+    for part in shard.partition_by_cost(sizes, 3):
+        _, vp, gp_, info = run_batch([sizes[i] for i in part], [Xs[i] for i in part], [ys[i] for i in part],
+                                     hyps[part], precision=precision)
+        assert np.all(info[:, 1] == gp.GPC_OK)
+        vv, gg = shard.gather_results(part, vp, gp_, len(sizes), 1)
+        keep = ~np.isnan(vv.numpy())
+        v[keep], g[keep] = vv.numpy()[keep], gg.numpy()[keep]
+    assert np.all(np.abs(v - v0) <= 1e-13 * np.maximum(1.0, np.abs(v0)))
+    assert np.all(np.abs(g - g0) <= 1e-11 * np.maximum(1.0, np.abs(g0)))
