@@ -111,3 +111,19 @@ def test_gather_with_one_rank_needs_no_process_group():
     v, g = shard.gather_results([2, 0], [5.0, 7.0], [[1, 2, 3], [4, 5, 6]], 3, 1)
     assert v[0].item() == 7.0 and v[2].item() == 5.0 and torch.isnan(v[1])
     assert g[2].tolist() == [1.0, 2.0, 3.0]
+
+
+def test_bench_batched_workload_by_index_equals_slicing_the_whole():
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    total = 10
+    sizes, X, y, hyp = bench.batched_workload(total)
+    assert sizes == bench.batched_sizes(total)
+    for world in (2, 3):
+        for rank, part in enumerate(shard.partition_by_cost(sizes, world)):
+            s, Xs, ys, hs = bench.batched_workload(total, indices=part)
+            s2, X2, y2, h2 = shard.take(part, sizes, X, y, hyp)
+            assert s == s2
+            assert np.array_equal(Xs, X2) and np.array_equal(ys, y2) and np.array_equal(hs, h2)
