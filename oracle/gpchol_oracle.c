@@ -387,6 +387,25 @@ void oracle_gemm_adjoint(int m, int n, int k, const double *A, int lda, const do
 }
 
 /*
+ * Digamma psi(x) for x > 0 (needed by the negative-binomial GLM's dphi):
+ * the recurrence psi(x) = psi(x + 1) - 1/x (Abramowitz and Stegun 6.3.5)
+ * moves x to 12 or above, then the asymptotic series (A&S 6.3.18)
+ *   psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)
+ * is summed through the x^-12 term (B_2 .. B_12 = 1/6, -1/30, 1/42, -1/30,
+ * 5/66, -691/2730); the first omitted term is below 4e-16 at x = 12.
+ */
+static double oracle_digamma(double x) {
+  double acc = 0.0;
+  while (x < 12.0) {
+    acc -= 1.0 / x;
+    x += 1.0;
+  }
+  double r = 1.0 / (x * x);
+  double series = r * (1.0 / 12.0 - r * (1.0 / 120.0 - r * (1.0 / 252.0 - r * (1.0 / 240.0 - r * (1.0 / 132.0 - r * (691.0 / 32760.0))))));
+  return acc + log(x) - 0.5 / x - series;
+}
+
+/*
  * GLM log likelihood and its gradient (Section 3.4): the linear predictor
  * eta_i = alpha + sum_j X_ij beta_j (j ascending), then per observation
  *   family 0, normal-identity:  lp_i = -((y_i - eta_i)/sigma)^2 / 2 - log sigma - log(2 pi) / 2,
@@ -395,9 +414,15 @@ void oracle_gemm_adjoint(int m, int n, int k, const double *A, int lda, const do
  *                               d_i = y_i - 1 / (1 + exp(-eta_i))
  *   family 2, Poisson-log:      lp_i = y_i eta_i - exp(eta_i) - lgamma(y_i + 1),
  *                               d_i = y_i - exp(eta_i)
+ *   family 3, negative-binomial-log (mean mu_i = exp(eta_i), dispersion phi = sigma):
+ *     lp_i = lgamma(y_i + phi) - lgamma(y_i + 1) - lgamma(phi)
+ *            + phi (log phi - log(mu_i + phi)) + y_i (eta_i - log(mu_i + phi)),
+ *     d_i = y_i - (y_i + phi) mu_i / (mu_i + phi),
+ *     dphi_i = psi(y_i + phi) - psi(phi) + log phi - log(mu_i + phi) + 1 - (y_i + phi)/(mu_i + phi)
  * with d_i = d lp_i / d eta_i.  Outputs: lp = sum_i lp_i, dalpha = sum_i d_i,
  * dbeta_j = sum_i X_ij d_i (i ascending), and for family 0
- * dsigma = sum_i ((y_i - eta_i)^2 / sigma^3 - 1 / sigma) (else 0).
+ * dsigma = sum_i ((y_i - eta_i)^2 / sigma^3 - 1 / sigma), for family 3
+ * dsigma = sum_i dphi_i (else 0).
  * log(1 + exp(eta)) is evaluated as max(eta, 0) + log1p(exp(-|eta|)), the
  * same quantity without overflow.  Returns -1 if scratch cannot be allocated.
  */
@@ -420,9 +445,14 @@ int oracle_glm(int family, int n, int k, const double *X, int ldx, const double 
       double softplus = (eta > 0.0 ? eta : 0.0) + log1p(exp(-fabs(eta)));
       li = y[i] * eta - softplus;
       di = y[i] - 1.0 / (1.0 + exp(-eta));
-    } else {
+    } else if (family == 2) {
       li = y[i] * eta - exp(eta) - lgamma(y[i] + 1.0);
       di = y[i] - exp(eta);
+    } else {
+      double phi = sigma, mu = exp(eta), lmp = log(mu + phi);
+      li = lgamma(y[i] + phi) - lgamma(y[i] + 1.0) - lgamma(phi) + phi * (log(phi) - lmp) + y[i] * (eta - lmp);
+      di = y[i] - (y[i] + phi) * mu / (mu + phi);
+      sds += oracle_digamma(y[i] + phi) - oracle_digamma(phi) + log(phi) - lmp + 1.0 - (y[i] + phi) / (mu + phi);
     }
     d[i] = di;
     slp += li;
@@ -435,7 +465,91 @@ int oracle_glm(int family, int n, int k, const double *X, int ldx, const double 
   }
   *lp = slp;
   *dalpha = sda;
-  *dsigma = family == 0 ? sds : 0.0;
+  *dsigma = (family == 0 || family == 3) ? sds : 0.0;
   free(d);
   return 0;
 }
+
+/* exported for the pins: the digamma above */
+double oracle_psi(double x) { return oracle_digamma(x); }
+
+/*
+ * Categorical-logit GLM (Section 3.4, multinomial logistic regression): C
+ * classes, y_i in {0, .., C-1}; the class scores are
+ *   eta_ic = alpha_c + sum_j X_ij beta_jc   (beta: k x C, row-major)
+ * and lp_i = eta_{i,y_i} - log sum_c exp(eta_ic) (the maximum is subtracted
+ * inside the log-sum-exp).  With p_ic = exp(eta_ic - logsumexp_i) and
+ * d_ic = [c == y_i] - p_ic:  dalpha_c = sum_i d_ic,  dbeta_jc = sum_i X_ij d_ic.
+ * Returns -1 if scratch cannot be allocated.
+ */
+int oracle_glm_categorical(int n, int k, int C, const double *X, int ldx, const double *y, const double *alpha,
+                           const double *beta, double *lp, double *dalpha, double *dbeta) {
+  double *eta = (double *)malloc((size_t)C * sizeof(double) + 8);
+  if (!eta) return -1;
+  double slp = 0.0;
+  for (int c = 0; c < C; ++c) dalpha[c] = 0.0;
+  for (int j = 0; j < k; ++j)
+    for (int c = 0; c < C; ++c) dbeta[(size_t)j * C + c] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double mx = -HUGE_VAL;
+    for (int c = 0; c < C; ++c) {
+      double e = alpha[c];
+      for (int j = 0; j < k; ++j) e += AT(X, ldx, i, j) * beta[(size_t)j * C + c];
+      eta[c] = e;
+      if (e > mx) mx = e;
+    }
+    double se = 0.0;
+    for (int c = 0; c < C; ++c) se += exp(eta[c] - mx);
+    double lse = mx + log(se);
+    int yi = (int)y[i];
+    slp += eta[yi] - lse;
+    for (int c = 0; c < C; ++c) {
+      double d = (c == yi ? 1.0 : 0.0) - exp(eta[c] - lse);
+      dalpha[c] += d;
+      for (int j = 0; j < k; ++j) dbeta[(size_t)j * C + c] += AT(X, ldx, i, j) * d;
+    }
+  }
+  *lp = slp;
+  free(eta);
+  return 0;
+}
+
+/*
+ * Ordinal-logit GLM (Section 3.4, ordinal logistic regression): C ordered
+ * classes, y_i in {0, .., C-1}, increasing cut points c_0 < .. < c_{C-2},
+ * eta_i = sum_j X_ij beta_j (the cut points take the intercept's place) and
+ * with s(t) = 1/(1 + exp(-t)):
+ *   P(y = 0) = 1 - s(eta - c_0),  P(y = m) = s(eta - c_{m-1}) - s(eta - c_m),
+ *   P(y = C-1) = s(eta - c_{C-2}).
+ * lp = sum_i log P(y_i).  With u = eta - c_{y-1} (absent for y = 0) and
+ * v = eta - c_y (absent for y = C-1), log P = log(s(u) - s(v)) and, since
+ * s' = s (1 - s),
+ *   d log P / d u = s(u)(1 - s(u)) / P,   d log P / d v = -s(v)(1 - s(v)) / P,
+ * so d/deta = (du + dv), d/dc_{y-1} = -du, d/dc_y = -dv, where the missing
+ * ends read s = 1 (u side) and s = 0 (v side) with no derivative.
+ * Outputs lp, dbeta (k) = sum_i X_ij d/deta_i, dcuts (C-1).
+ */
+void oracle_glm_ordinal(int n, int k, int C, const double *X, int ldx, const double *y, const double *beta,
+                        const double *cuts, double *lp, double *dbeta, double *dcuts) {
+  double slp = 0.0;
+  for (int j = 0; j < k; ++j) dbeta[j] = 0.0;
+  for (int m = 0; m + 1 < C; ++m) dcuts[m] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double eta = 0.0;
+    for (int j = 0; j < k; ++j) eta += AT(X, ldx, i, j) * beta[j];
+    int yi = (int)y[i];
+    double su = 1.0, sv = 0.0;
+    if (yi > 0) su = 1.0 / (1.0 + exp(-(eta - cuts[yi - 1])));
+    if (yi < C - 1) sv = 1.0 / (1.0 + exp(-(eta - cuts[yi])));
+    double P = su - sv;
+    slp += log(P);
+    double du = yi > 0 ? su * (1.0 - su) / P : 0.0;
+    double dv = yi < C - 1 ? -sv * (1.0 - sv) / P : 0.0;
+    double deta = du + dv;
+    for (int j = 0; j < k; ++j) dbeta[j] += AT(X, ldx, i, j) * deta;
+    if (yi > 0) dcuts[yi - 1] -= du;
+    if (yi < C - 1) dcuts[yi] -= dv;
+  }
+  *lp = slp;
+}
+

@@ -68,6 +68,12 @@ def _load():
         lib.oracle_gemm_adjoint.restype = None
         lib.oracle_glm.argtypes = [i, i, i, _D, i, _D, d, _D, d, _D, _D, _D, _D]
         lib.oracle_glm.restype = i
+        lib.oracle_psi.argtypes = [d]
+        lib.oracle_psi.restype = d
+        lib.oracle_glm_categorical.argtypes = [i, i, i, _D, i, _D, _D, _D, _D, _D, _D]
+        lib.oracle_glm_categorical.restype = i
+        lib.oracle_glm_ordinal.argtypes = [i, i, i, _D, i, _D, _D, _D, _D, _D, _D]
+        lib.oracle_glm_ordinal.restype = None
         _lib = lib
     return _lib
 
@@ -204,11 +210,17 @@ def gemm_adjoint(A, B, Cbar):
     return Abar, Bbar
 
 
-GLM_FAMILIES = {"normal_id": 0, "bernoulli_logit": 1, "poisson_log": 2}
+GLM_FAMILIES = {"normal_id": 0, "bernoulli_logit": 1, "poisson_log": 2, "neg_binomial_2_log": 3}
+
+
+def psi(x: float) -> float:
+    """Digamma (recurrence to x >= 12, then the asymptotic series)."""
+    return float(_load().oracle_psi(float(x)))
 
 
 def glm(family: str, X, y, alpha: float, beta, sigma: float = 1.0) -> dict:
-    """GLM log likelihood and gradient: dict(lp, dalpha, dbeta, dsigma)."""
+    """GLM log likelihood and gradient: dict(lp, dalpha, dbeta, dsigma); for the
+    negative binomial, sigma is the dispersion phi and dsigma is d lp / d phi."""
     X = _rect(X)
     n, k = X.shape
     y = np.ascontiguousarray(y, dtype=np.float64)
@@ -221,6 +233,38 @@ def glm(family: str, X, y, alpha: float, beta, sigma: float = 1.0) -> dict:
                           ctypes.byref(lp), ctypes.byref(da), _p(db), ctypes.byref(ds)) != 0:
         raise MemoryError("oracle scratch allocation failed")
     return {"lp": lp.value, "dalpha": da.value, "dbeta": db, "dsigma": ds.value}
+
+
+def glm_categorical(X, y, alpha, beta) -> dict:
+    """Categorical-logit GLM: y in {0..C-1}, alpha (C), beta (k x C); dict(lp, dalpha, dbeta)."""
+    X = _rect(X)
+    n, k = X.shape
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    C = alpha.shape[0]
+    beta = np.ascontiguousarray(beta, dtype=np.float64).reshape(k, C)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    if y.shape != (n,):
+        raise ValueError("shape mismatch")
+    lp = ctypes.c_double()
+    da, db = np.zeros(C), np.zeros((k, C))
+    if _load().oracle_glm_categorical(n, k, C, _p(X), k, _p(y), _p(alpha), _p(beta), ctypes.byref(lp), _p(da),
+                                      _p(db)) != 0:
+        raise MemoryError("oracle scratch allocation failed")
+    return {"lp": lp.value, "dalpha": da, "dbeta": db}
+
+
+def glm_ordinal(X, y, beta, cuts) -> dict:
+    """Ordinal-logit GLM: y in {0..C-1}, increasing cuts (C-1), beta (k); dict(lp, dbeta, dcuts)."""
+    X = _rect(X)
+    n, k = X.shape
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    cuts = np.ascontiguousarray(cuts, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    C = cuts.shape[0] + 1
+    lp = ctypes.c_double()
+    db, dc = np.zeros(k), np.zeros(C - 1)
+    _load().oracle_glm_ordinal(n, k, C, _p(X), k, _p(y), _p(beta), _p(cuts), ctypes.byref(lp), _p(db), _p(dc))
+    return {"lp": lp.value, "dbeta": db, "dcuts": dc}
 
 
 def se_cov(X, alpha: float, rho: float, sigma: float, jitter: float = 0.0,

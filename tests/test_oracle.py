@@ -504,3 +504,122 @@ def test_glm_gradient_finite_differences(family):
     if family == "normal_id":
         fd = (f(alpha, beta, sigma + h) - f(alpha, beta, sigma - h)) / (2 * h)
         assert abs(r["dsigma"] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------- the other GLMs of Section 3.4
+def test_digamma_matches_scipy():
+    import scipy.special as sp
+    for x in [1e-4, 0.3, 1.0, 1.4616321449683623, 2.5, 7.0, 11.999, 12.0, 40.0, 1e5]:
+        ref = sp.digamma(x)
+        assert abs(O.psi(x) - ref) <= 1e-14 * max(1.0, abs(ref)), x
+
+
+def test_glm_negative_binomial_matches_scipy():
+    rng, X, beta, alpha = glm_data(seed=6)
+    eta = alpha + X @ beta
+    phi = 2.5
+    mu = np.exp(eta)
+    y = rng.negative_binomial(phi, phi / (mu + phi)).astype(float)
+    r = O.glm("neg_binomial_2_log", X, y, alpha, beta, phi)
+    ref = scipy.stats.nbinom.logpmf(y, phi, phi / (mu + phi)).sum()
+    assert abs(r["lp"] - ref) <= 1e-12 * abs(ref)
+
+
+def test_glm_negative_binomial_gradient_finite_differences():
+    rng, X, beta, alpha = glm_data(n=30, k=3, seed=7)
+    mu = np.exp(alpha + X @ beta)
+    phi = 1.7
+    y = rng.negative_binomial(phi, phi / (mu + phi)).astype(float)
+    r = O.glm("neg_binomial_2_log", X, y, alpha, beta, phi)
+
+    def f(a, b, p):
+        return O.glm("neg_binomial_2_log", X, y, a, b, p)["lp"]
+
+    h = 1e-6
+    assert abs(r["dalpha"] - (f(alpha + h, beta, phi) - f(alpha - h, beta, phi)) / (2 * h)) <= 1e-6
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        fd = (f(alpha, beta + e, phi) - f(alpha, beta - e, phi)) / (2 * h)
+        assert abs(r["dbeta"][j] - fd) <= 1e-6 * max(1.0, abs(fd))
+    fd = (f(alpha, beta, phi + h) - f(alpha, beta, phi - h)) / (2 * h)
+    assert abs(r["dsigma"] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_glm_categorical_matches_log_softmax_and_normalises():
+    import scipy.special as sp
+    rng = np.random.default_rng(8)
+    n, k, C = 40, 3, 4
+    X = rng.standard_normal((n, k))
+    alpha, beta = rng.standard_normal(C), rng.standard_normal((k, C))
+    y = rng.integers(0, C, n).astype(float)
+    r = O.glm_categorical(X, y, alpha, beta)
+    ls = sp.log_softmax(alpha + X @ beta, axis=1)
+    assert abs(r["lp"] - ls[np.arange(n), y.astype(int)].sum()) <= 1e-12 * abs(r["lp"])
+    # one observation: the class probabilities sum to one
+    tot = sum(np.exp(O.glm_categorical(X[:1], [c], alpha, beta)["lp"]) for c in range(C))
+    assert abs(tot - 1.0) <= 1e-14
+
+
+def test_glm_categorical_two_classes_is_bernoulli_logit():
+    rng, X, beta, alpha = glm_data(seed=9)
+    y = (rng.random(len(X)) < 0.5).astype(float)
+    rb = O.glm("bernoulli_logit", X, y, alpha, beta)
+    rc = O.glm_categorical(X, y, [0.0, alpha], np.stack([np.zeros_like(beta), beta], axis=1))
+    assert abs(rc["lp"] - rb["lp"]) <= 1e-12 * abs(rb["lp"])
+    assert np.abs(rc["dbeta"][:, 1] - rb["dbeta"]).max() <= 1e-12
+    assert abs(rc["dalpha"][1] - rb["dalpha"]) <= 1e-12
+
+
+def test_glm_categorical_gradient_finite_differences():
+    rng = np.random.default_rng(10)
+    n, k, C = 25, 2, 3
+    X = rng.standard_normal((n, k))
+    alpha, beta = rng.standard_normal(C), rng.standard_normal((k, C))
+    y = rng.integers(0, C, n).astype(float)
+    r = O.glm_categorical(X, y, alpha, beta)
+    h = 1e-6
+    for c in range(C):
+        e = np.zeros(C)
+        e[c] = h
+        fd = (O.glm_categorical(X, y, alpha + e, beta)["lp"] - O.glm_categorical(X, y, alpha - e, beta)["lp"]) / (2 * h)
+        assert abs(r["dalpha"][c] - fd) <= 1e-6
+        for j in range(k):
+            E = np.zeros((k, C))
+            E[j, c] = h
+            fd = (O.glm_categorical(X, y, alpha, beta + E)["lp"] - O.glm_categorical(X, y, alpha, beta - E)["lp"]) / (2 * h)
+            assert abs(r["dbeta"][j, c] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_glm_ordinal_normalises_and_two_classes_is_bernoulli_logit():
+    rng, X, beta, alpha = glm_data(n=50, k=3, seed=11)
+    cuts = np.array([-1.0, 0.2, 1.5])
+    for i in range(5):
+        tot = sum(np.exp(O.glm_ordinal(X[i:i + 1], [c], beta, cuts)["lp"]) for c in range(4))
+        assert abs(tot - 1.0) <= 1e-14
+    y = (rng.random(50) < 0.5).astype(float)
+    ro = O.glm_ordinal(X, y, beta, [0.7])
+    rb = O.glm("bernoulli_logit", X, y, -0.7, beta)
+    assert abs(ro["lp"] - rb["lp"]) <= 1e-12 * abs(rb["lp"])
+    assert np.abs(ro["dbeta"] - rb["dbeta"]).max() <= 1e-12
+    assert abs(ro["dcuts"][0] + rb["dalpha"]) <= 1e-12
+
+
+def test_glm_ordinal_gradient_finite_differences():
+    rng = np.random.default_rng(12)
+    n, k = 30, 2
+    X = rng.standard_normal((n, k))
+    beta, cuts = np.array([0.8, -0.5]), np.array([-1.2, -0.1, 0.9, 2.0])
+    y = rng.integers(0, 5, n).astype(float)
+    r = O.glm_ordinal(X, y, beta, cuts)
+    h = 1e-6
+    for j in range(k):
+        e = np.zeros(k)
+        e[j] = h
+        fd = (O.glm_ordinal(X, y, beta + e, cuts)["lp"] - O.glm_ordinal(X, y, beta - e, cuts)["lp"]) / (2 * h)
+        assert abs(r["dbeta"][j] - fd) <= 1e-6 * max(1.0, abs(fd))
+    for m in range(4):
+        e = np.zeros(4)
+        e[m] = h
+        fd = (O.glm_ordinal(X, y, beta, cuts + e)["lp"] - O.glm_ordinal(X, y, beta, cuts - e)["lp"]) / (2 * h)
+        assert abs(r["dcuts"][m] - fd) <= 1e-6 * max(1.0, abs(fd))

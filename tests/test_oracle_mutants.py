@@ -53,6 +53,15 @@ MUTANTS = {
     "glm_poisson_lgamma": ("li = y[i] * eta - exp(eta) - lgamma(y[i] + 1.0);", "li = y[i] * eta - exp(eta);"),
     "glm_normal_dsigma": ("sds += (y[i] - eta) * (y[i] - eta) / (sigma * sigma * sigma) - 1.0 / sigma;",
                           "sds += (y[i] - eta) * (y[i] - eta) / (sigma * sigma) - 1.0 / sigma;"),
+    "digamma_recurrence_sign": ("    acc -= 1.0 / x;\n", "    acc += 1.0 / x;\n"),
+    "negbin_dropped_lgamma_phi": ("li = lgamma(y[i] + phi) - lgamma(y[i] + 1.0) - lgamma(phi) + phi",
+                                  "li = lgamma(y[i] + phi) - lgamma(y[i] + 1.0) + phi"),
+    "negbin_derivative_factor": ("di = y[i] - (y[i] + phi) * mu / (mu + phi);", "di = y[i] - y[i] * mu / (mu + phi);"),
+    "categorical_wrong_class": ("slp += eta[yi] - lse;", "slp += eta[0] - lse;"),
+    "categorical_dropped_alpha": ("    double e = alpha[c];\n", "    double e = 0.0;\n"),
+    "ordinal_cut_sign": ("if (yi > 0) dcuts[yi - 1] -= du;", "if (yi > 0) dcuts[yi - 1] += du;"),
+    "ordinal_wrong_cut_index": ("if (yi < C - 1) sv = 1.0 / (1.0 + exp(-(eta - cuts[yi])));",
+                                "if (yi < C - 1) sv = 1.0 / (1.0 + exp(-(eta - cuts[yi > 0 ? yi - 1 : 0])));"),
 }
 
 
