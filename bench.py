@@ -198,6 +198,30 @@ def cpu_baseline(ns: int, d: int, hyp):
                        f"(flops n^3/3 + 2n^3/3), {dt:.1f} s on {os.cpu_count()} host cores available")}
 
 
+def cpu_parallel_baseline(ns: int, d: int, hyp):
+    """The same unblocked chol + reverse mode in column order with OpenMP over
+    the rows of each column, on all host cores, on the same leading ns x ns
+    block.  Reported beside the oracle; unavailable (not an error) where its
+    OpenMP build failed."""
+    try:
+        from oracle import oracle as O
+        from paper_1907_01063_gb300 import workloads as W
+        threads = O.cpu_threads()
+        X = W.gp_inputs(ns, d, seed=0)
+        K = O.se_cov(X, hyp[0], hyp[1], hyp[2], 0.0)
+        Lbar = W.random_lower(ns, seed=2)
+        t0 = time.perf_counter()
+        L = O.cpu_chol(K)
+        O.cpu_chol_adjoint(L, Lbar)
+        dt = time.perf_counter() - t0
+    except Exception as exc:  # noqa: BLE001 - reported in the JSON line instead
+        return {"unavailable": f"{type(exc).__name__}: {exc}"}
+    fl = chol_flops(ns) + 2.0 * ns ** 3 / 3.0
+    return {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": threads, "kind": "multi-core CPU baseline",
+            "sample": (f"unblocked FP64 Cholesky + reverse mode in column order, OpenMP over the rows of each "
+                       f"column, leading {ns}x{ns} block of the workload (flops n^3/3 + 2n^3/3), {dt:.2f} s")}
+
+
 # ---------------------------------------------------------------- distributed
 def make_sync(world, device):
     """Barrier and max-over-ranks around the timed regions: NCCL between GPU
@@ -669,9 +693,10 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    cpu = None
+    cpu = cpu_par = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(args.cpu_sample, d, hyp)
+        cpu_par = cpu_parallel_baseline(args.cpu_sample, d, hyp)
     head = results["mixed"] if "mixed" in results else results["fp64"]
     prec = head["prec"]
 
@@ -694,6 +719,7 @@ def main():
         "gpu_launches": head["launches"],
         "roofline": roofline(head),
         "cpu_baseline": cpu,
+        "cpu_parallel_baseline": cpu_par,
         "clocks": head["clocks"],
         "flops_per_step": head["step_flops"],
         "kernel_ms_per_step": kernel_ms(head),

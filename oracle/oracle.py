@@ -1,4 +1,5 @@
-"""NumPy/ctypes front end of the plain FP64 CPU oracle (``gpchol_oracle.c``).
+"""NumPy/ctypes front end of the plain FP64 CPU oracle (``gpchol_oracle.c``) and
+of the multi-core CPU baseline (``cpu_baseline.c``, timed by the benchmark).
 
 This is test infrastructure: only the tests, the smoke check and the
 benchmark's CPU-baseline leg import it.  It shares nothing with the GPU
@@ -32,6 +33,63 @@ def build(force: bool = False) -> str:
                                "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+_CPU_SRC = os.path.join(_HERE, "cpu_baseline.c")
+_CPU_LIB_PATH = os.path.join(_HERE, "_build", "libgpchol_cpu_baseline.so")
+_cpu_lib = None
+
+
+def build_cpu_baseline(force: bool = False) -> str:
+    """Compile the multi-core CPU baseline (OpenMP) into ``oracle/_build``."""
+    os.makedirs(os.path.dirname(_CPU_LIB_PATH), exist_ok=True)
+    stale = (not os.path.exists(_CPU_LIB_PATH)
+             or os.path.getmtime(_CPU_LIB_PATH) < os.path.getmtime(_CPU_SRC))
+    if force or stale:
+        tmp = _CPU_LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-std=c11", "-shared", "-fPIC", "-o", tmp, _CPU_SRC, "-lm"])
+        os.replace(tmp, _CPU_LIB_PATH)
+    return _CPU_LIB_PATH
+
+
+def _load_cpu():
+    global _cpu_lib
+    if _cpu_lib is None:
+        lib = ctypes.CDLL(build_cpu_baseline())
+        i = ctypes.c_int
+        lib.cpu_baseline_threads.argtypes = []
+        lib.cpu_baseline_threads.restype = i
+        lib.cpu_baseline_chol.argtypes = [i, _D, _D]
+        lib.cpu_baseline_chol.restype = i
+        lib.cpu_baseline_chol_adjoint.argtypes = [i, _D, _D, _D]
+        lib.cpu_baseline_chol_adjoint.restype = i
+        _cpu_lib = lib
+    return _cpu_lib
+
+
+def cpu_threads() -> int:
+    """Threads the multi-core CPU baseline uses."""
+    return int(_load_cpu().cpu_baseline_threads())
+
+
+def cpu_chol(K) -> np.ndarray:
+    """Multi-core CPU baseline Cholesky (column order, rows of a column in parallel)."""
+    K = _mat(K)
+    n = K.shape[0]
+    L = np.zeros_like(K)
+    info = _load_cpu().cpu_baseline_chol(n, _p(K), _p(L))
+    if info >= 0:
+        raise NotPositiveDefinite(info)
+    return L
+
+
+def cpu_chol_adjoint(L, Lbar) -> np.ndarray:
+    """Multi-core CPU baseline reverse mode of cpu_chol."""
+    L, Lbar = _mat(L), _mat(Lbar)
+    Kbar = np.zeros_like(L)
+    if _load_cpu().cpu_baseline_chol_adjoint(L.shape[0], _p(L), _p(Lbar), _p(Kbar)) != 0:
+        raise MemoryError("scratch allocation failed")
+    return Kbar
 
 
 def _load():
