@@ -14,6 +14,14 @@ sigma^2 = lambda_max(K^f) / 1e5 (condition number about 1e5), targets from an
 approximate GP draw.  K, L and Kbar are 2 GiB each, far larger than L2, so no
 L2 flush is needed between steps.
 
+The same JSON line also carries:
+  * the FP64 path's step beside the mixed headline (mixed_vs_fp64);
+  * the batched workload: 512 GPs per GPU, one persistent launch, dealt to the ranks by n^3;
+  * `tri`: the triangular inverse and the triangular solve's reverse mode at the same n;
+  * `gemm_glm`: the FP64 GEMM and its reverse mode, and the fused Bernoulli-logit GLM likelihood;
+  * the oracle (`cpu_baseline`) and the multi-core CPU baseline (`cpu_parallel_baseline`) on a
+    leading block of the workload.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs an independent replica on its own GPU
 (replicas only: one dense factorisation is not sharded).
