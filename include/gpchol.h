@@ -4,9 +4,11 @@
  *
  * The operations follow "GPU-based Parallel Computation Support for Stan"
  * (Cesnovar et al., 2019): the blocked Cholesky decomposition and its blocked
- * reverse mode (Section 3.3), triangular solves (Section 3.2), and the
- * Gaussian-process log marginal likelihood that the GP regression example of
- * Section 4.2 evaluates on top of them.
+ * reverse mode (Section 3.3), the Gaussian-process log marginal likelihood
+ * that the GP regression example of Section 4.2 evaluates on top of them,
+ * triangular solves, the lower-triangular inverse and the solve's reverse
+ * mode (Section 3.2), the general matrix product and its reverse mode
+ * (Section 3.1), and fused GLM likelihoods with their gradients (Section 3.4).
  *
  * Conventions shared by every call
  * --------------------------------
