@@ -203,13 +203,24 @@ void oracle_se_cov(int n, int d, const double *X, int ldx, double alpha, double 
  *   L = chol(K);  z = L^{-1} y;  alpha = L^{-T} z;
  *   logdet = 2 sum_i log L_ii;
  *   value = -1/2 z.z - 1/2 logdet - (n/2) log(2 pi).
+ * oracle_gp_lml_factored takes the steps after L = chol(K) for a given factor
+ * L; oracle_gp_lml is oracle_chol followed by it.
  * Writes L (may alias K), z and alpha (n each; may be NULL), logdet and value.
- * Returns -1 on success or the failing pivot of oracle_chol.
+ * Returns -1 on success, the failing pivot of oracle_chol, or -2 if scratch
+ * cannot be allocated.
  */
+int oracle_gp_lml_factored(int n, const double *L, int ldl, const double *y, double *z, double *alpha,
+                           double *logdet, double *value);
+
 int oracle_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int ldl,
                   double *z, double *alpha, double *logdet, double *value) {
   int info = oracle_chol(n, K, ldk, L, ldl);
   if (info >= 0) return info;
+  return oracle_gp_lml_factored(n, L, ldl, y, z, alpha, logdet, value);
+}
+
+int oracle_gp_lml_factored(int n, const double *L, int ldl, const double *y, double *z, double *alpha,
+                           double *logdet, double *value) {
   double *zz = (double *)malloc((size_t)n * sizeof(double) + 8);
   double *aa = (double *)malloc((size_t)n * sizeof(double) + 8);
   if (!zz || !aa) { free(zz); free(aa); return -2; }

@@ -47,7 +47,8 @@ def build_cpu_baseline(force: bool = False) -> str:
              or os.path.getmtime(_CPU_LIB_PATH) < os.path.getmtime(_CPU_SRC))
     if force or stale:
         tmp = _CPU_LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-std=c11", "-shared", "-fPIC", "-o", tmp, _CPU_SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-std=c11",
+                               "-shared", "-fPIC", "-o", tmp, _CPU_SRC, "-lm"])
         os.replace(tmp, _CPU_LIB_PATH)
     return _CPU_LIB_PATH
 
@@ -110,6 +111,8 @@ def _load():
         lib.oracle_se_cov.restype = None
         lib.oracle_gp_lml.argtypes = [i, _D, i, _D, _D, i, _D, _D, _D, _D]
         lib.oracle_gp_lml.restype = i
+        lib.oracle_gp_lml_factored.argtypes = [i, _D, i, _D, _D, _D, _D, _D]
+        lib.oracle_gp_lml_factored.restype = i
         lib.oracle_lml_lbar.argtypes = [i, _D, i, _D, _D, d, _D, i]
         lib.oracle_lml_lbar.restype = None
         lib.oracle_se_hyper_grad.argtypes = [i, i, _D, i, d, d, d, _D, i, _D]
@@ -354,6 +357,22 @@ def gp_lml(K, y):
     return {"L": L, "z": z, "alpha": a, "logdet": ld.value, "value": val.value}
 
 
+def gp_lml_factored(L, y):
+    """The steps of gp_lml after the factorisation, for a given factor L:
+    dict(z, alpha, logdet, value)."""
+    L = _mat(L)
+    n = L.shape[0]
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    z = np.zeros(n)
+    a = np.zeros(n)
+    ld = ctypes.c_double()
+    val = ctypes.c_double()
+    if _load().oracle_gp_lml_factored(n, _p(L), n, _p(y), _p(z), _p(a), ctypes.byref(ld),
+                                      ctypes.byref(val)) == -2:
+        raise MemoryError("oracle scratch allocation failed")
+    return {"z": z, "alpha": a, "logdet": ld.value, "value": val.value}
+
+
 def lml_lbar(L, alpha, z, gbar: float = 1.0) -> np.ndarray:
     """Upstream Lbar = gbar (tril(alpha z^T) - diag(1/L_ii))."""
     L = _mat(L)
@@ -383,4 +402,25 @@ def gp_lml_and_grad(X, y, alpha: float, rho: float, sigma: float, jitter: float 
     Kbar = chol_adjoint(r["L"], Lbar)
     g = se_hyper_grad(X, alpha, rho, sigma, Kbar)
     r.update({"K": K, "Lbar": Lbar, "Kbar": Kbar, "grad": g})
+    return r
+
+
+def gp_lml_and_grad_multicore(X, y, alpha: float, rho: float, sigma: float, jitter: float = 0.0):
+    """The pass of gp_lml_and_grad with its two O(n^3) steps taken by the
+    multi-core unblocked routines of cpu_baseline.c, for sizes the
+    single-threaded oracle cannot finish in test time (n = 16384: about two
+    minutes on 16 cores instead of half an hour).  cpu_chol runs the oracle's
+    recurrence with the same operations in the same order for every entry, so
+    its factor is bitwise equal to chol's; cpu_chol_adjoint runs the same
+    statements with the rows of a column summed in another order (within
+    1e-13 of chol_adjoint).  tests/test_cpu_baseline.py checks both.  Every
+    other step is the oracle's own."""
+    K = se_cov(X, alpha, rho, sigma, jitter)
+    L = cpu_chol(K)
+    r = gp_lml_factored(L, y)
+    Lbar = lml_lbar(L, r["alpha"], r["z"], 1.0)
+    Kbar = cpu_chol_adjoint(L, Lbar)
+    del Lbar
+    g = se_hyper_grad(X, alpha, rho, sigma, Kbar)
+    r.update({"K": K, "L": L, "Kbar": Kbar, "grad": g})
     return r
