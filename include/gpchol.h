@@ -63,6 +63,26 @@ typedef struct CUstream_st *gpc_stream_t;
  * stream before their first kernel.
  */
 
+/*
+ * Library error word (one per device).  Every kernel of this library that
+ * waits on another thread block or on an asynchronous copy bounds the wait in
+ * time; when a wait gives up, the kernel records GPC_ERR_TIMEOUT here (the
+ * first status recorded since the last clear is kept) besides any per-call
+ * info array, so calls that take no info (gpc_trsv, gpc_trsv_noalloc,
+ * gpc_chol_adjoint, gpc_gp_lml_grad) still report it.  The outputs of a call
+ * whose wait gave up are unspecified.
+ * gpc_get_error synchronises `stream` (so call it after the calls of interest
+ * were enqueued on that stream, or after the device was synchronised), then
+ * copies the current device's word into *status (host pointer): GPC_OK or
+ * GPC_ERR_TIMEOUT.  clear != 0 resets the word to GPC_OK afterwards.  The
+ * first call on a device looks the word's device address up (a runtime query;
+ * make it before any stream capture); the call itself cannot be captured.
+ * Returns GPC_ERR_INVALID_ARG for a null status, GPC_ERR_CUDA if the copy or
+ * the synchronisation fails.  No counterpart in the paper: the paper's OpenCL
+ * framework reports device errors through exceptions on the host.
+ */
+int gpc_get_error(int *status, int clear, gpc_stream_t stream);
+
 /* Human-readable text of a status code (static storage, never NULL). */
 const char *gpc_status_string(int status);
 
@@ -143,8 +163,9 @@ int gpc_chol_adjoint(int n, const double *L, int ldl, const double *Lbar, int ld
  *   trans == 0: x <- L^{-1} x      trans != 0: x <- L^{-T} x
  * x is a device vector of n doubles, overwritten.  ws/ws_bytes: scratch for
  * the solve's ready flags; gpc_workspace_size(n, GPC_FP64) bytes always
- * suffice.  Each 64-row block waits (bounded) on the blocks before it; a
- * wait that gives up leaves x unspecified.
+ * suffice.  Each 64-row block waits (bounded, 2 s) on the blocks before it; a
+ * wait that gives up leaves x unspecified and records GPC_ERR_TIMEOUT in the
+ * library error word (gpc_get_error).
  */
 int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, size_t ws_bytes,
              gpc_stream_t stream);
@@ -159,10 +180,15 @@ int gpc_trsv(int n, const double *L, int ldl, double *x, int trans, void *ws, si
  * ready flag per 64-row block -- is a fixed 16.25 KiB array inside the library,
  * held by every GPU that loads the library until the process exits.
  *  - n must be <= GPC_TRSV_NOALLOC_MAX_N; larger n returns GPC_ERR_INVALID_ARG
- *    before anything is enqueued.  Other arguments as in gpc_trsv.
+ *    before anything is enqueued.  Other arguments as in gpc_trsv.  A bounded
+ *    wait that gives up leaves x unspecified; the call still returns GPC_OK
+ *    (it is asynchronous) and the timeout is recorded in the library error
+ *    word, which the caller reads with gpc_get_error after a sync.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current) and caches it; make that
- *    first call before any stream capture.  No call allocates memory.
+ *    (cudaGetSymbolAddress, with that device current) and caches it with the
+ *    device's current context; a later call in a new context (for example
+ *    after cudaDeviceReset) looks it up again.  Make the first call in each
+ *    context before any stream capture.  No call allocates memory.
  *  - All calls on a device share the one array, which keeps the last call's
  *    contents; each call clears the flags it uses on `stream` before its
  *    kernel.  Calls whose execution overlaps on the GPU (different streams
@@ -277,7 +303,10 @@ int gpc_glm(int family, long long n, int k, const double *X, long long ldx, cons
             void *ws, size_t ws_bytes, gpc_stream_t stream);
 
 /*
- * Gaussian-process log marginal likelihood of y ~ N(0, K):
+ * Gaussian-process log marginal likelihood of y ~ N(0, K), the likelihood of
+ * the paper's GP regression example (Section 4.2), evaluated through the
+ * Cholesky factor (Section 3.3, primitive function) and two triangular solves
+ * (Section 3.2):
  *   L = chol(K), z = L^{-1} y, alpha = L^{-T} z, logdet = 2 sum log L_ii,
  *   value = -1/2 y^T alpha - 1/2 logdet - (n/2) log(2 pi).
  * Writes L (may alias K when precision == GPC_FP64), alpha (n doubles), and
@@ -291,9 +320,12 @@ int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int 
                size_t ws_bytes, int *info, gpc_stream_t stream);
 
 /*
- * Kbar = gbar * d value / d K for the likelihood of gpc_gp_lml, through the
- * Cholesky adjoint: Lbar = gbar (tril(alpha z^T) - diag(1 / L_ii)) with
- * z = L^T alpha, then Kbar = chol_adjoint(L, Lbar) (lower convention).
+ * Kbar = gbar * d value / d K for the likelihood of gpc_gp_lml -- the reverse
+ * pass that the GP regression example of Section 4.2 needs for its sampler's
+ * gradient -- through the Cholesky adjoint (Section 3.3, reverse mode
+ * function): Lbar = gbar (tril(alpha z^T) - diag(1 / L_ii)) with
+ * z = L^T alpha (the reverse of the solves and of logdet = 2 sum log L_ii),
+ * then Kbar = chol_adjoint(L, Lbar) (lower convention).
  */
 int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double gbar,
                     double *Kbar, int ldkb, int precision, void *ws, size_t ws_bytes,
@@ -301,7 +333,10 @@ int gpc_gp_lml_grad(int n, const double *L, int ldl, const double *alpha, double
 
 /*
  * Hyperparameter gradient from Kbar (lower convention) for the covariance of
- * gpc_se_cov: grad3 = (d/d alpha, d/d rho, d/d sigma) of f, with
+ * gpc_se_cov -- the last step of the gradient that the GP regression example
+ * of Section 4.2 takes with respect to its covariance hyperparameters (the
+ * reverse mode of the covariance build): grad3 = (d/d alpha, d/d rho,
+ * d/d sigma) of f, with
  *   d K_ij/d alpha = 2 K^f_ij / alpha, d K_ij/d rho = K^f_ij r2_ij / rho^3,
  *   d K_ii/d sigma = 2 sigma   (K^f: the noise-free part; jitter is constant),
  * summed over i >= j.  K^f is recomputed from X; grad3: 3 device doubles.

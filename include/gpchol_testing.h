@@ -27,6 +27,41 @@ int gpc_test_ozaki_workspace_size(int M, int N, int K, size_t *bytes);
 int gpc_test_ozaki_gemm(int M, int N, int K, const double *A, const double *B, double *C, void *ws,
                         size_t ws_bytes, int *err, gpc_stream_t stream);
 
+/*
+ * The reciprocal and reciprocal square root that the diagonal-block
+ * factorisation uses on its serial path (the hardware approximations refined
+ * by two Newton-Raphson steps), evaluated on the n device doubles x next to
+ * CUDA's own correctly rounded 1.0 / x and its rsqrt(x):
+ *   out[4 i + 0] = refined 1/x_i      out[4 i + 1] = CUDA 1.0 / x_i
+ *   out[4 i + 2] = refined 1/sqrt(x_i) out[4 i + 3] = CUDA rsqrt(x_i)
+ * out: 4 n device doubles.  Meant for positive normal x; other x fall back to
+ * the plain division and square root.
+ */
+int gpc_test_recip_rsqrt(int n, const double *x, double *out, gpc_stream_t stream);
+
+/*
+ * Fault injection for the tests of the bounded device waits.  These knobs
+ * change what later launches do (process-wide, host-side; not thread-safe):
+ *   GPC_TEST_WAIT_NS         budget of every bounded wait of the solve and
+ *                            split-product kernels, in ns (1 .. 1e10);
+ *                            0 restores the default of 2 s.
+ *   GPC_TEST_TRSV_WITHHOLD   gpc_trsv / gpc_trsv_noalloc: the 64-row block
+ *                            (0-based, in solve order) that computes its
+ *                            rows but never publishes its ready flag, so the
+ *                            blocks after it run out their waits and record
+ *                            GPC_ERR_TIMEOUT; -1 (default) withholds none.
+ *   GPC_TEST_OZAKI_NO_LOADS  1: the split product's copy warp issues no
+ *                            copies, so the MMA warp's waits run out; the
+ *                            kernel records GPC_ERR_TIMEOUT, releases its
+ *                            tensor memory and returns.  0 (default): normal.
+ * Every wait stays bounded, so no setting can hang a kernel.  Returns
+ * GPC_ERR_INVALID_ARG for an unknown key or an out-of-range value.
+ */
+#define GPC_TEST_WAIT_NS 0
+#define GPC_TEST_TRSV_WITHHOLD 1
+#define GPC_TEST_OZAKI_NO_LOADS 2
+int gpc_test_set_fault(int key, long long value);
+
 #ifdef __cplusplus
 }
 #endif

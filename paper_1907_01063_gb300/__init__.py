@@ -42,6 +42,9 @@ _c_int, _c_double, _c_size, _c_vp = ctypes.c_int, ctypes.c_double, ctypes.c_size
 # name -> (argtypes, restype)
 _SIGNATURES = {
     "gpc_status_string": ([_c_int], ctypes.c_char_p),
+    "gpc_get_error": ([ctypes.POINTER(_c_int), _c_int, _c_vp], _c_int),
+    "gpc_test_set_fault": ([_c_int, ctypes.c_longlong], _c_int),
+    "gpc_test_recip_rsqrt": ([_c_int, _c_vp, _c_vp, _c_vp], _c_int),
     "gpc_version": ([], _c_int),
     "gpc_workspace_size": ([_c_int, _c_int, ctypes.POINTER(_c_size)], _c_int),
     "gpc_set_tuning": ([_c_int, _c_int], _c_int),
@@ -179,6 +182,25 @@ def precision_code(precision) -> int:
         return PRECISIONS[precision]
     except KeyError:
         raise ValueError(f"unknown precision {precision!r}") from None
+
+
+def get_error(clear: bool = False) -> int:
+    """The library error word of the current device after synchronising the
+    current stream: GPC_OK, or GPC_ERR_TIMEOUT if a bounded device wait gave
+    up since the last clear.  clear=True resets it."""
+    v = ctypes.c_int()
+    _check(capi.gpc_get_error(ctypes.byref(v), 1 if clear else 0, _stream()), "gpc_get_error")
+    return v.value
+
+
+GPC_TEST_WAIT_NS = 0
+GPC_TEST_TRSV_WITHHOLD = 1
+GPC_TEST_OZAKI_NO_LOADS = 2
+
+
+def set_test_fault(key: int, value: int):
+    """Fault-injection knob of the test hooks (gpc_test_set_fault)."""
+    _check(capi.gpc_test_set_fault(int(key), int(value)), "gpc_test_set_fault")
 
 
 def set_tuning(key: int, value: int):

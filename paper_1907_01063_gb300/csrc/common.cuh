@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/gpchol.h"
 
@@ -22,6 +23,34 @@ Tuning &tuning();
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+
+// ---------------------------------------------------------------- error word, symbols, test faults
+// Device address of a file-scope __device__ variable on the current device,
+// cached per device together with the context it was looked up in (a new
+// context triggers a new lookup).  The first lookup on a device is a runtime
+// query: make it before any stream capture.
+struct SymbolCache {
+  static constexpr int kMaxDevices = 64;
+  std::mutex mu;
+  void *ctx[kMaxDevices] = {};
+  void *addr[kMaxDevices] = {};
+};
+cudaError_t symbol_address(const void *symbol, SymbolCache &cache, void **out);
+// The library error word of the current device (gpc_get_error), or null if
+// the lookup failed.  Kernels record device-side conditions with record_error.
+int *error_word();
+__device__ __forceinline__ void record_error(int *word, int status) {
+  if (word) atomicCAS(word, 0, status);
+}
+// Fault-injection knobs of the test hooks (gpc_test_set_fault).  wait_ns is
+// the budget of every bounded device wait in the solve and product kernels.
+struct Faults {
+  static constexpr unsigned long long kDefaultWaitNs = 2000000000ull;  // 2 s
+  unsigned long long wait_ns = kDefaultWaitNs;
+  int trsv_withhold = -1;  // 64-row block of trsv_kernel that never publishes its ready flag
+  int ozaki_no_loads = 0;  // the split product's producer issues no copies
+};
+Faults &faults();
 
 // ---------------------------------------------------------------- FP64 GEMM
 // C = beta * C + alpha * op(A) * op(B), row-major, op(A) M x K, op(B) K x N.
@@ -100,6 +129,8 @@ cudaError_t phi_block(int nb, double *A, long long lda, cudaStream_t s);
 // Lower Kbar -> full symmetric G: G_ii = Kbar_ii, G_ij = G_ji = Kbar_ij / 2.
 cudaError_t lower_to_symmetric_half(int n, double *A, long long lda, cudaStream_t s);
 cudaError_t reset_info(int *info, cudaStream_t s);
+// Test hook: out[4 i ..] = {recip_nr(x_i), 1.0 / x_i, rsqrt_nr(x_i), rsqrt(x_i)}.
+cudaError_t recip_rsqrt_probe(int n, const double *x, double *out, cudaStream_t s);
 
 // ---------------------------------------------------------------- drivers
 // Fused GLM likelihood and gradient (glm.cu).

@@ -113,8 +113,11 @@ trtri_batched_kernel(int n, const double *L, long long ldl, int first, int b, do
 // 1/x and 1/sqrt(x) for normal positive x: the hardware's approximations
 // refined by two Newton-Raphson steps, y <- y (2 - x y) and
 // y <- y (3 - x y^2) / 2 (each step doubles the correct bits; the result is
-// within a few ulp).  FP64 instructions are scarce on this part, so this short
-// dependent chain is what the diagonal factorisation's serial part waits on.
+// within 2 ulp of the correctly rounded value, checked against CUDA's 1.0 / x
+// and rsqrt over the normal range by gpc_test_recip_rsqrt's test; recip_nr
+// needs 1/x normal too, x < 2^1022, which holds for any pivot of a matrix whose
+// entries are below 2^511).  FP64 instructions are scarce on this part, so this
+// short dependent chain is what the diagonal factorisation's serial part waits on.
 __device__ __forceinline__ double recip_nr(double x) {
   if (!(x >= 2.2250738585072014e-308)) return 1.0 / x;
   double y;
@@ -428,6 +431,17 @@ __global__ void reset_info_kernel(int *info) {
 
 unsigned blocks_for(long long total, int threads) { return (unsigned)((total + threads - 1) / threads); }
 
+// Test hook: the refined reciprocals next to CUDA's own 1.0 / x and rsqrt(x).
+__global__ void recip_rsqrt_probe_kernel(int n, const double *x, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  out[4 * i + 0] = recip_nr(v);
+  out[4 * i + 1] = 1.0 / v;
+  out[4 * i + 2] = rsqrt_nr(v);
+  out[4 * i + 3] = rsqrt(v);
+}
+
 }  // namespace
 
 static cudaError_t launch_diag(int nb, double *A, long long lda, double *Winv, int *info,
@@ -560,6 +574,12 @@ cudaError_t lower_to_symmetric_half(int n, double *A, long long lda, cudaStream_
   if (n <= 0) return cudaSuccess;
   GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 16.0 * (double)n * n, s,
              lower_to_symmetric_half_kernel<<<blocks_for((long long)n * n, 256), 256, 0, s>>>(n, A, lda));
+  return cudaGetLastError();
+}
+
+cudaError_t recip_rsqrt_probe(int n, const double *x, double *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 40.0 * n, s, recip_rsqrt_probe_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, out));
   return cudaGetLastError();
 }
 

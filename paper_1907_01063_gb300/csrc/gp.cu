@@ -250,7 +250,6 @@ sum3_kernel(const double *partial, long long count, double *out) {
 // solved, 2 = gave up); every wait is bounded and a timeout is reported as
 // GPC_ERR_TIMEOUT and propagated to later blocks as flag 2.
 constexpr int TB = 64;
-constexpr long long kSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
 __device__ __forceinline__ unsigned long long clock_ns() {
@@ -258,10 +257,23 @@ __device__ __forceinline__ unsigned long long clock_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+// Wait until *flag is non-zero (value receives it) or wait_ns of %globaltimer
+// have passed (returns false).
+__device__ __forceinline__ bool wait_flag(const int *flag, int &value, unsigned long long wait_ns) {
+  const unsigned long long t0 = clock_ns();
+  for (unsigned it = 0;; ++it) {
+    value = ld_volatile(flag);
+    if (value != 0) return true;
+    if ((it & 255) == 255 && clock_ns() - t0 > wait_ns) return false;
+    if (it > 1024) __nanosleep(32);
+  }
+}
 
+// withhold >= 0 (test hook): the block with that index in solve order computes
+// its rows but never publishes its ready flag.
 __global__ void __launch_bounds__(256)
 trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sync, int *info,
-            const int *skip) {
+            const int *skip, int *gerr, unsigned long long wait_ns, int withhold) {
   if (skip && *skip) return;  // the same value for every CTA: nothing waits on anything
   __shared__ int s_order, s_abort;
   __shared__ double diag[TB][TB + 1];
@@ -284,10 +296,8 @@ trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sy
   for (int step = 0; step < order; ++step) {
     const int c = trans ? (nblk - 1 - step) : step;
     if (threadIdx.x == 0) {
-      long long spins = 0;
       int f;
-      while ((f = ld_volatile(&sync[1 + c])) == 0 && ++spins < kSpinLimit) __nanosleep(64);
-      if (f != 1) s_abort = 1;
+      if (!wait_flag(&sync[1 + c], f, wait_ns) || f != 1) s_abort = 1;
       __threadfence();
     }
     __syncthreads();
@@ -315,8 +325,9 @@ trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sy
   if (s_abort) {
     if (threadIdx.x == 0) {
       if (info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
+      record_error(gerr, GPC_ERR_TIMEOUT);
       __threadfence();
-      atomicExch(&sync[1 + blk], 2);
+      if (order != withhold) atomicExch(&sync[1 + blk], 2);
     }
     return;
   }
@@ -376,7 +387,7 @@ trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sy
     if (lane + 32 < nb) x[b0 + lane + 32] = v1;
     __threadfence();
     __syncwarp();
-    if (lane == 0) atomicExch(&sync[1 + blk], 1);
+    if (lane == 0 && order != withhold) atomicExch(&sync[1 + blk], 1);
   }
 }
 
@@ -387,15 +398,6 @@ trsv_kernel(int n, const double *L, long long ldl, double *x, int trans, int *sy
 // Blocks are b rows from the top (the last may be shorter); Dinv_I is at
 // inv + I b^2 with leading dimension equal to the block size.  Same ticket
 // order, ready flags and bounded waits as trsv_kernel.
-__device__ __forceinline__ bool wait_flag(const int *flag, int &value) {
-  const unsigned long long t0 = clock_ns();
-  for (unsigned it = 0;; ++it) {
-    value = ld_volatile(flag);
-    if (value != 0) return true;
-    if ((it & 255) == 255 && clock_ns() - t0 > 2000000000ull) return false;
-    if (it > 1024) __nanosleep(32);
-  }
-}
 
 // Latency matters more than bandwidth here: every block waits for the one
 // before it, and on GB300 each dependent FP64 instruction costs about 64
@@ -413,7 +415,7 @@ constexpr int TS = 64, TQ = 4, TW = TS / TQ;
 
 __global__ void __launch_bounds__(256)
 trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b, int sb, double *x, int trans,
-                int *sync, int *info, const int *skip) {
+                int *sync, int *info, const int *skip, int *gerr, unsigned long long wait_ns) {
   if (skip && *skip) return;
   __shared__ double dinv_s[TS][TS + 1];
   __shared__ int s_order, s_ab[2];
@@ -453,7 +455,7 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
     for (int c = 0; c < sbk; ++c) {
       if (threadIdx.x == 0) {
         int f;
-        if (!wait_flag(&sync[1 + c], f) || f != 1) s_ab[c & 1] = 1;
+        if (!wait_flag(&sync[1 + c], f, wait_ns) || f != 1) s_ab[c & 1] = 1;
         __threadfence();
       }
       __syncthreads();
@@ -511,7 +513,7 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
       const int c = nsb - 1 - step;
       if (threadIdx.x == 0) {
         int f;
-        if (!wait_flag(&sync[1 + c], f) || f != 1) s_ab[step & 1] = 1;
+        if (!wait_flag(&sync[1 + c], f, wait_ns) || f != 1) s_ab[step & 1] = 1;
         __threadfence();
       }
       __syncthreads();
@@ -557,6 +559,7 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
   __syncthreads();
   if (threadIdx.x == 0) {
     if (aborted && info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
+    if (aborted) record_error(gerr, GPC_ERR_TIMEOUT);
     __threadfence();
     atomicExch(&sync[1 + sbk], aborted ? 2 : 1);
   }
@@ -706,7 +709,8 @@ cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, vo
   cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nblk + 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n, 4.0 * (double)n * (n + 1) + 16.0 * n, s,
-             trsv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, x, trans ? 1 : 0, sync, info, skip));
+             trsv_kernel<<<nblk, 256, 0, s>>>(n, L, ldl, x, trans ? 1 : 0, sync, info, skip, error_word(),
+                                              faults().wait_ns, faults().trsv_withhold));
   return cudaGetLastError();
 }
 
@@ -721,7 +725,8 @@ cudaError_t trsv_inv(int n, const double *L, long long ldl, const double *inv, i
   cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(nsb + 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n + 2.0 * n * b, 4.0 * (double)n * (n + 1) + 8.0 * n * b, s,
-             trsv_inv_kernel<<<nsb, 256, 0, s>>>(n, L, ldl, inv, b, sb, x, trans ? 1 : 0, sync, info, skip));
+             trsv_inv_kernel<<<nsb, 256, 0, s>>>(n, L, ldl, inv, b, sb, x, trans ? 1 : 0, sync, info, skip,
+                                                 error_word(), faults().wait_ns));
   return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ constexpr int OZ_EPI_LD2 = 18;                          // the same for the 16-b
 constexpr int OZ_EPI_BUF = 32 * OZ_EPI_LD2 * 8;          // 32 rows x 16 columns of double-floats per warp
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + OZ_EPI_WARPS * OZ_EPI_BUF +
                               1024 /*barriers*/ + 1024 /*align*/;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr unsigned long long kDrainNs = 2000000000ull;  // 2 s: bound of the waits that drain the kernel's own work
 
 struct OzParams {
   int M, N, chunks, qpc;  // qpc: 32-wide K stages used per chunk (chunks shorter than 128)
@@ -82,7 +82,10 @@ struct OzParams {
   float2 *C;
   long long ldc;
   float2 *partial;
-  int *err;
+  int *err;                    // per-call status slot (may be null)
+  int *gerr;                   // library error word (may be null)
+  unsigned long long wait_ns;  // budget of each bounded wait
+  int no_loads;                // test hook: the copy warp issues nothing
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -117,15 +120,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false on timeout or when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+// Bounded wait: false after wait_ns or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned long long wait_ns) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (unsigned it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 63) == 0) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > kWaitNs) return false;
+      if (global_ns() - t0 > wait_ns) return false;
     }
   }
 }
@@ -134,8 +138,12 @@ __device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
   const unsigned long long t0 = global_ns();
   for (;;) {
     if (mbar_try(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > kDrainNs) return false;
   }
+}
+__device__ __forceinline__ void report_timeout(const OzParams &p) {
+  if (p.err) atomicExch(p.err, GPC_ERR_TIMEOUT);
+  record_error(p.gerr, GPC_ERR_TIMEOUT);
 }
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
                                             uint32_t bar) {
@@ -327,12 +335,12 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       uint32_t phase = 0;
       long long issued = 0;
       bool ok = true;
-      for (int w = blockIdx.x; w < p.num_work && ok; w += gridDim.x) {
+      for (int w = blockIdx.x; w < p.num_work && ok && !p.no_loads; w += gridDim.x) {
         int tm, tn, c0, c1;
         work_coords(p, w, tm, tn, c0, c1);
         for (int c = c0; c < c1 && ok; ++c) {
           for (int h = 0; h < p.qpc; ++h) {
-            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.wait_ns)) { ok = false; break; }
             mbar_expect_tx(full0 + 8 * stage, OZ_A_STAGE + OZ_B_STAGE);
             const int ka = p.a_k0 + c * OZ_CHUNK + h * OZ_BK;
             const int kb = p.b_k0 + c * OZ_CHUNK + h * OZ_BK;
@@ -345,7 +353,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       }
       if (!ok) {
         *abort_flag = 1;
-        if (p.err) atomicExch(p.err, GPC_ERR_TIMEOUT);
+        report_timeout(p);
         // Drain: wait for the copies of the last (up to OZ_STAGES) issued loads.
         const long long first = issued > OZ_STAGES ? issued - OZ_STAGES : 0;
         for (long long i = first; i < issued; ++i) {
@@ -368,11 +376,11 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         int tm, tn, c0, c1;
         work_coords(p, w, tm, tn, c0, c1);
         for (int c = c0; c < c1 && ok; ++c) {
-          if (!mbar_wait(tempty0 + 8 * buf, tphase ^ 1, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(tempty0 + 8 * buf, tphase ^ 1, abort_flag, p.wait_ns)) { ok = false; break; }
           fence_after();
           const uint32_t tacc = tbase + (uint32_t)(buf * OZ_ACC_COLS);
           for (int h = 0; h < p.qpc && ok; ++h) {
-            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.wait_ns)) { ok = false; break; }
             fence_after();
             const uint64_t da = sdesc(smem_u32(sA + stage * OZ_A_STAGE));
             const uint64_t db = sdesc(smem_u32(sB + stage * OZ_B_STAGE));
@@ -390,7 +398,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       }
       if (!ok) {
         *abort_flag = 1;
-        if (p.err) atomicExch(p.err, GPC_ERR_TIMEOUT);
+        report_timeout(p);
       }
       // Drain: every MMA issued above completes before TMEM is released.
       if (any) {
@@ -494,7 +502,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
       }
       for (int c = c0; c < c1; ++c) {
-        if (!mbar_wait(tfull0 + 8 * buf, tphase, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(tfull0 + 8 * buf, tphase, abort_flag, p.wait_ns)) { ok = false; break; }
         fence_after();
         const uint32_t tacc = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * OZ_ACC_COLS) + half * 32;
 #pragma unroll
@@ -559,7 +567,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
-      if (p.err) atomicExch(p.err, GPC_ERR_TIMEOUT);
+      report_timeout(p);
     }
   }
 
@@ -769,6 +777,9 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
   p.ldc = ldc;
   p.partial = splits > 1 ? partial : nullptr;
   p.err = err;
+  p.gerr = error_word();
+  p.wait_ns = faults().wait_ns;
+  p.no_loads = faults().ozaki_no_loads;
   const int ctas = max_ctas > 0 ? std::min(max_ctas, sm_count()) : sm_count();
   // output entries: the whole M x N block, or its lower part (col <= row)
   const double mn = !lower ? (double)M * N

@@ -54,3 +54,10 @@ extern "C" int gpc_test_ozaki_gemm(int M, int N, int K, const double *A, const d
   if (e == cudaSuccess) e = from_df_rect(M, N, C, N, s);
   return e == cudaSuccess ? GPC_OK : GPC_ERR_CUDA;
 }
+
+extern "C" int gpc_test_recip_rsqrt(int n, const double *x, double *out, gpc_stream_t stream) {
+  if (n < 0) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (!x || !out) return GPC_ERR_INVALID_ARG;
+  return recip_rsqrt_probe(n, x, out, stream) == cudaSuccess ? GPC_OK : GPC_ERR_CUDA;
+}

@@ -13,18 +13,20 @@
 // The array is a file-scope __device__ object: every GPU that loads this
 // library holds its 16.25 KiB until the process exits.  In host code its name
 // is only a host-side stand-in for the symbol, not a device address, so the
-// device address is looked up with cudaGetSymbolAddress once per device (with
-// that device current) on the first call made on that device, and cached.
-// That first call therefore does one extra runtime query; make it before any
-// stream capture.  No call here allocates device or pinned memory.
+// device address is looked up with cudaGetSymbolAddress (with the device
+// current) on the first call made on that device, and cached together with
+// the device's current context.  A call in a different context (the old one
+// destroyed by cudaDeviceReset, say, which also reloads the module) looks the
+// address up again instead of using a stale one.  The first call in a context
+// therefore does one extra runtime query; make it before any stream capture.
+// A bounded wait of the solve that gives up records GPC_ERR_TIMEOUT in the
+// library error word (gpc_get_error).  No call here allocates device or pinned
+// memory.
 #include "common.cuh"
-
-#include <mutex>
 
 namespace gpc {
 namespace {
 
-constexpr int kMaxDevices = 64;
 constexpr int kSolveBlock = 64;  // rows per block of the solve kernel
 constexpr int kMaxBlocks = GPC_TRSV_NOALLOC_MAX_N / kSolveBlock;
 
@@ -35,26 +37,11 @@ constexpr int kMaxBlocks = GPC_TRSV_NOALLOC_MAX_N / kSolveBlock;
 constexpr int kScratchInts = (kMaxBlocks + 1 + 63) / 64 * 64;
 static __device__ __align__(256) int g_trsv_scratch[kScratchInts];
 
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
+SymbolCache g_scratch_cache;
 
-// Device address of g_trsv_scratch on the current device (set-up on first use).
-cudaError_t scratch_address(void **out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> g(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_trsv_scratch);
-    if (e != cudaSuccess) return e;
-    if (!p) return cudaErrorInvalidSymbol;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
-  return cudaSuccess;
-}
+// Device address of g_trsv_scratch on the current device and context (looked
+// up on first use in each context).
+cudaError_t scratch_address(void **out) { return symbol_address(g_trsv_scratch, g_scratch_cache, out); }
 
 }  // namespace
 }  // namespace gpc
@@ -71,6 +58,7 @@ extern "C" int gpc_trsv_noalloc(int n, const double *L, int ldl, double *x, int 
   void *scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return GPC_ERR_CUDA;
   // gpc::trsv clears the ticket and flags it uses (on the stream) and then
-  // launches the same solve kernel as gpc_trsv, with this array as its scratch.
+  // launches the same solve kernel as gpc_trsv, with this array as its scratch;
+  // a timed-out wait is recorded in the library error word.
   return trsv(n, L, ldl, x, trans, scratch, nullptr, stream) == cudaSuccess ? GPC_OK : GPC_ERR_CUDA;
 }

@@ -157,3 +157,19 @@ def test_gemm_and_glm_argument_checks_return_before_any_launch():
                      None) == bad  # short workspace
     assert c.gpc_glm(1, 10, 3, fake, 3, None, 0.0, farther, 1.0, out, out + 8, out + 32, out + 16, 0x500000, ws,
                      None) == bad  # no y
+
+
+def test_error_word_and_fault_knobs_host_checks():
+    c = gp.capi
+    bad = gp.GPC_ERR_INVALID_ARG
+    assert c.gpc_get_error(None, 0, None) == bad  # null status: rejected before any CUDA call
+    assert c.gpc_test_set_fault(99, 0) == bad
+    assert c.gpc_test_set_fault(gp.GPC_TEST_WAIT_NS, -1) == bad
+    assert c.gpc_test_set_fault(gp.GPC_TEST_WAIT_NS, 10 ** 11) == bad
+    assert c.gpc_test_set_fault(gp.GPC_TEST_TRSV_WITHHOLD, -2) == bad
+    assert c.gpc_test_set_fault(gp.GPC_TEST_OZAKI_NO_LOADS, 2) == bad
+    # valid settings are host-side only; restore the defaults
+    for key, value, default in ((gp.GPC_TEST_WAIT_NS, 1000, 0), (gp.GPC_TEST_TRSV_WITHHOLD, 3, -1),
+                                (gp.GPC_TEST_OZAKI_NO_LOADS, 1, 0)):
+        assert c.gpc_test_set_fault(key, value) == gp.GPC_OK
+        assert c.gpc_test_set_fault(key, default) == gp.GPC_OK
