@@ -20,7 +20,10 @@ The same JSON line also carries:
   * `tri`: the triangular inverse and the triangular solve's reverse mode at the same n;
   * `gemm_glm`: the FP64 GEMM and its reverse mode, and the fused Bernoulli-logit GLM likelihood;
   * the oracle (`cpu_baseline`) and the multi-core CPU baseline (`cpu_parallel_baseline`) on a
-    leading block of the workload.
+    leading block of the workload;
+  * `fp64_vs_oracle` and `mixed_vs_oracle`: each path's L, Kbar, alpha, log det, LML and
+    gradient against the oracle's pass on the whole workload, computed after every timed
+    leg (--no-oracle-parity skips it).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs an independent replica on its own GPU
@@ -65,6 +68,9 @@ def parse_args():
     p.add_argument("--ref-sample", type=int, default=2048,
                    help="order of the leading block one reference step factors")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-oracle-parity", action="store_true",
+                   help="skip the comparison of both paths' results with the oracle's pass at the full size "
+                        "(about two minutes of host work after every timed leg)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched-GP workload")
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--no-autotune", action="store_true")
@@ -228,6 +234,37 @@ def cpu_parallel_baseline(ns: int, d: int, hyp):
     return {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": threads, "kind": "multi-core CPU baseline",
             "sample": (f"unblocked FP64 Cholesky + reverse mode in column order, OpenMP over the rows of each "
                        f"column, leading {ns}x{ns} block of the workload (flops n^3/3 + 2n^3/3), {dt:.2f} s")}
+
+
+def oracle_parity_legs(results, X, y, hyp, jitter):
+    """Each path's L, K-bar, alpha, log det, LML value and hyperparameter
+    gradient against the oracle's pass on the same workload (the oracle's
+    O(n^3) steps by the multi-core routines whose factor is bitwise the
+    oracle's; tests/test_cpu_baseline.py).  Run after every timed leg."""
+    import numpy as np
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    ref = O.gp_lml_and_grad_multicore(X, y, hyp[0], hyp[1], hyp[2], jitter)
+    dt = time.perf_counter() - t0
+
+    def frob(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    out = {}
+    for prec, res in results.items():
+        h = res.pop("host", None)
+        if h is None:
+            continue
+        out[f"{prec}_vs_oracle"] = {
+            "L_rel_frob": frob(h["L"], ref["L"]), "Kbar_rel_frob": frob(h["Kbar"], ref["Kbar"]),
+            "alpha_rel": frob(h["alpha"], ref["alpha"]),
+            "logdet_rel_err": abs(h["logdet"] - ref["logdet"]) / abs(ref["logdet"]),
+            "lml_rel_err": abs(h["value"] - ref["value"]) / abs(ref["value"]),
+            "grad_rel_err": frob(h["grad"], ref["grad"]),
+            "oracle": (f"oracle pass on the host ({O.cpu_threads()} threads for the two O(n^3) steps, "
+                       f"{dt:.0f} s)")}
+        out[f"{prec}_vs_oracle"]["meets_lml_1e-8"] = out[f"{prec}_vs_oracle"]["lml_rel_err"] <= 1e-8
+    return out
 
 
 # ---------------------------------------------------------------- distributed
@@ -405,6 +442,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     barrier, max_over_ranks = make_sync(world, dev)
+    oracle_parity = not args.no_oracle_parity and rank == 0 and n <= 16384
 
     def run(prec):
         b = gp.get_tuning(gp.GPC_TUNE_BLOCK) if prec == "fp64" else 128
@@ -504,6 +542,13 @@ def main():
         out["e2e"] = {"value": whole_job_rate(world, e2e_steps, step_flops, e2e_ms) / 1e9, "unit": "GFLOP/s",
                       "h2d_bytes_per_step": Xh.numel() * 8 + yh.numel() * 8, "d2h_bytes_per_step": 32,
                       "ms_per_step": e2e_ms / e2e_steps}
+        if oracle_parity:
+            # the last step's outputs (same inputs every step), kept on the host
+            # for the comparison with the oracle after every timed leg
+            torch.cuda.synchronize()
+            out["host"] = {"L": L.cpu().numpy(), "Kbar": Kbar.cpu().numpy(), "alpha": res_e["alpha"].cpu().numpy(),
+                           "logdet": res_e["logdet"].item(), "value": res_e["value"].item(),
+                           "grad": g3.cpu().numpy()}
         return out
 
     tuned = {}
@@ -768,6 +813,8 @@ def main():
         }
     else:
         line.update({"lml": head["lml"], "grad": head["grad"]})
+    if oracle_parity:
+        line.update(oracle_parity_legs(results, X, y, hyp, jitter))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

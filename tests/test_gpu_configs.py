@@ -7,7 +7,15 @@
 * n = 8192, d = 16, rho = 4, sigma = 0.1: the autograd gradient of the LML in
   (alpha, rho, sigma) against central finite differences of the LML with
   h = 1e-6 (FP64 path), and the mixed path's value and gradient against it.
+* n = 4096, d = 16, rho = 4 with sigma^2 = lambda_max(K^f) / 1e6
+  (tests/golden/cond_sigma_n4096_1e6.json: condition number 9.5e5), the edge
+  of the conditioning range of the FP64 bar: the whole GP pass (covariance,
+  factor, solves, LML, K-bar, hyperparameter gradient) against the oracle's
+  pass at relative 1e-10 (FP64), and the mixed path's errors against it.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -112,3 +120,62 @@ def test_autograd_8192_mixed_matches_fp64(gp8192):
     print(f"n=8192 mixed vs fp64: value {abs(vm - vf) / abs(vf):.3e} grad {rel(gm, gf):.3e}")
     assert abs(vm - vf) <= 1e-8 * abs(vf)
     assert rel(gm, gf) <= 1e-7
+
+
+@pytest.fixture(scope="module")
+def cond1e6():
+    rec = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                      "cond_sigma_n4096_1e6.json")))
+    n, d, a, r, s = rec["n"], rec["d"], rec["alpha"], rec["rho"], rec["sigma"]
+    assert rec["cond"] > 5e5
+    X = W.gp_inputs(n, d, seed=rec["seed"])
+    y = W.gp_targets(X, a, r, s, seed=1)
+    # the oracle's pass, its two O(n^3) steps by the multi-core routines whose
+    # factor is bitwise the oracle's (tests/test_cpu_baseline.py)
+    ref = O.gp_lml_and_grad_multicore(X, y, a, r, s, 0.0)
+    return X, y, (a, r, s), ref
+
+
+def gp_pass(X, y, hyp, prec):
+    n = X.shape[0]
+    a, r, s = hyp
+    Xd, yd = dev(X), dev(y)
+    K = gp.se_cov(Xd, a, r, s, 0.0, precision=prec)
+    ws = gp.workspace(n, prec, Xd.device)
+    info = gp.new_info(Xd.device)
+    res = gp.gp_lml(K, yd, prec, ws=ws, info=info, check=False)
+    L = res["L"]
+    Kbar = torch.empty_like(K)
+    gp.gp_lml_grad(L, res["alpha"], 1.0, prec, out=Kbar, ws=ws)
+    g = gp.se_hyper_grad(Xd, a, r, s, Kbar, precision=prec)
+    torch.cuda.synchronize()
+    return {"L": L.cpu().numpy(), "Kbar": Kbar.cpu().numpy(), "alpha": res["alpha"].cpu().numpy(),
+            "logdet": res["logdet"].item(), "value": res["value"].item(), "grad": g.cpu().numpy(),
+            "info": info.tolist()}
+
+
+def pass_errors(out, ref):
+    return {"L": rel(out["L"], ref["L"]), "Kbar": rel(out["Kbar"], ref["Kbar"]),
+            "alpha": rel(out["alpha"], ref["alpha"]),
+            "logdet": abs(out["logdet"] - ref["logdet"]) / abs(ref["logdet"]),
+            "value": abs(out["value"] - ref["value"]) / abs(ref["value"]), "grad": rel(out["grad"], ref["grad"])}
+
+
+def test_cond1e6_fp64_pass_matches_oracle(cond1e6):
+    X, y, hyp, ref = cond1e6
+    out = gp_pass(X, y, hyp, "fp64")
+    assert out["info"] == [-1, gp.GPC_OK]
+    e = pass_errors(out, ref)
+    print("cond 1e6, n=4096, fp64 vs oracle:", {k: f"{v:.2e}" for k, v in e.items()})
+    assert max(e.values()) <= 1e-10, e
+
+
+def test_cond1e6_mixed_pass_errors(cond1e6):
+    X, y, hyp, ref = cond1e6
+    out = gp_pass(X, y, hyp, "mixed")
+    assert out["info"][1] in (gp.GPC_OK, gp.GPC_ERR_NO_CONVERGENCE)
+    e = pass_errors(out, ref)
+    print("cond 1e6, n=4096, mixed vs oracle:", {k: f"{v:.2e}" for k, v in e.items()},
+          "refinement status", out["info"][1])
+    assert e["value"] <= 1e-8 and e["logdet"] <= 1e-8, e
+    assert e["grad"] <= 1e-6, e
