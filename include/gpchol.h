@@ -110,6 +110,19 @@ int gpc_workspace_size(int n, int precision, size_t *bytes);
 #define GPC_TUNE_SLICES 1
 #define GPC_TUNE_SPLITK_MIN 2
 #define GPC_TUNE_BATCH_BLOCK 3  /* block size inside gpc_batched_gp_lml_grad: 32 or 64 */
+/* Mixed factorisation (GPC_MIXED): block columns (128 wide) whose trailing
+ * updates are merged into one product with K = 128 x value (1..8, default 4;
+ * enters the mixed workspace size); SMs its background products leave to the
+ * FP64 chain (0..32, default 4); work items per CTA of a background product
+ * (0 = one persistent CTA per SM, else 1..1024, so CTAs retire and the
+ * chain's kernels get SMs); and whether the chain's launches take the
+ * device's greatest stream priority (0 or 1, default 1). */
+#define GPC_TUNE_MIXED_DEFER 4
+#define GPC_TUNE_MIXED_FREE_SMS 5
+#define GPC_TUNE_MIXED_CTA_ITEMS 6
+#define GPC_TUNE_MIXED_PRIORITY 7
+/* Mixed adjoint: SMs its background products leave to the chain (0..64, default 16). */
+#define GPC_TUNE_MIXED_ADJ_FREE_SMS 8
 int gpc_set_tuning(int key, int value);
 int gpc_get_tuning(int key, int *value);
 

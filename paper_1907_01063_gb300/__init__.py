@@ -34,6 +34,11 @@ GPC_TUNE_BLOCK = 0
 GPC_TUNE_SLICES = 1
 GPC_TUNE_SPLITK_MIN = 2
 GPC_TUNE_BATCH_BLOCK = 3
+GPC_TUNE_MIXED_DEFER = 4
+GPC_TUNE_MIXED_FREE_SMS = 5
+GPC_TUNE_MIXED_CTA_ITEMS = 6
+GPC_TUNE_MIXED_PRIORITY = 7
+GPC_TUNE_MIXED_ADJ_FREE_SMS = 8
 
 PRECISIONS = {"fp64": GPC_FP64, "mixed": GPC_MIXED, GPC_FP64: GPC_FP64, GPC_MIXED: GPC_MIXED}
 

@@ -133,6 +133,26 @@ int gpc_set_tuning(int key, int value) {
       if (value != 32 && value != 64) return GPC_ERR_INVALID_ARG;
       tuning().batch_block = value;
       return GPC_OK;
+    case GPC_TUNE_MIXED_DEFER:
+      if (value < 1 || value > 8) return GPC_ERR_INVALID_ARG;
+      tuning().mixed_defer = value;
+      return GPC_OK;
+    case GPC_TUNE_MIXED_FREE_SMS:
+      if (value < 0 || value > 32) return GPC_ERR_INVALID_ARG;
+      tuning().mixed_free_sms = value;
+      return GPC_OK;
+    case GPC_TUNE_MIXED_CTA_ITEMS:
+      if (value < 0 || value > 1024) return GPC_ERR_INVALID_ARG;
+      tuning().mixed_cta_items = value;
+      return GPC_OK;
+    case GPC_TUNE_MIXED_PRIORITY:
+      if (value != 0 && value != 1) return GPC_ERR_INVALID_ARG;
+      tuning().mixed_priority = value;
+      return GPC_OK;
+    case GPC_TUNE_MIXED_ADJ_FREE_SMS:
+      if (value < 0 || value > 64) return GPC_ERR_INVALID_ARG;
+      tuning().mixed_adj_free_sms = value;
+      return GPC_OK;
     default:
       return GPC_ERR_INVALID_ARG;
   }
@@ -145,6 +165,11 @@ int gpc_get_tuning(int key, int *value) {
     case GPC_TUNE_SLICES: *value = slices_count(); return GPC_OK;
     case GPC_TUNE_SPLITK_MIN: *value = tuning().splitk_min; return GPC_OK;
     case GPC_TUNE_BATCH_BLOCK: *value = tuning().batch_block; return GPC_OK;
+    case GPC_TUNE_MIXED_DEFER: *value = tuning().mixed_defer; return GPC_OK;
+    case GPC_TUNE_MIXED_FREE_SMS: *value = tuning().mixed_free_sms; return GPC_OK;
+    case GPC_TUNE_MIXED_CTA_ITEMS: *value = tuning().mixed_cta_items; return GPC_OK;
+    case GPC_TUNE_MIXED_PRIORITY: *value = tuning().mixed_priority; return GPC_OK;
+    case GPC_TUNE_MIXED_ADJ_FREE_SMS: *value = tuning().mixed_adj_free_sms; return GPC_OK;
     default: return GPC_ERR_INVALID_ARG;
   }
 }

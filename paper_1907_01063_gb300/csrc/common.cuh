@@ -18,8 +18,44 @@ struct Tuning {
   int splitk_min = 32;    // minimum K per split of a split-K product
   int batch_block = 64;   // block size inside the batched per-GP pass (32 or 64)
   int batch_ctas_per_sm = 1;
+  int mixed_defer = 4;    // mixed path: block columns whose trailing updates are merged (K = 128 x this)
+  int mixed_free_sms = 4; // mixed factorisation: SMs the background products leave to the FP64 chain
+  int mixed_adj_free_sms = 16;  // mixed adjoint: the same
+  int mixed_cta_items = 0;  // mixed path: work items per CTA of a background product (0: persistent)
+  int mixed_priority = 1;   // mixed path: launch the critical chain at the device's greatest priority
 };
 Tuning &tuning();
+
+// ---------------------------------------------------------------- launch priority
+// Priority given to the launches this thread makes through launch_k (0: the
+// stream's own).  The mixed factorisation raises it for its critical chain so
+// that pending CTAs of the chain's kernels are scheduled before pending CTAs
+// of the products running in the background.
+int launch_priority();
+int greatest_priority();  // of the current device (numerically lowest value)
+struct PriorityScope {
+  int saved;
+  explicit PriorityScope(int p);
+  ~PriorityScope();
+};
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  const int prio = launch_priority();
+  if (prio != 0) {
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
@@ -208,8 +244,11 @@ size_t slice_bytes(int rows, int kchunks);
 SliceBuf slice_view(void *base, int rows, int kchunks);
 // Operand element (r, k) = src[r * rs + k * ks]; chunk 0 is k in [0, first).
 // chunk_offset: operand chunk c is written to slice chunk c + chunk_offset.
+// row_offset: operand row r is written to slice row r + row_offset, and only
+// rows row_offset .. row_offset + M - 1 are written (row_offset == 0 also
+// zeroes the padding rows up to the buffer's rows_pad).
 cudaError_t split_operand(const double *src, long long rs, long long ks, int M, int K, int first,
-                          const SliceBuf &out, cudaStream_t s, int chunk_offset = 0);
+                          const SliceBuf &out, cudaStream_t s, int chunk_offset = 0, int row_offset = 0);
 size_t ozaki_partial_bytes(int M, int N, int splits);
 // C (double-float storage, ld in 8-byte elements) += alpha * A[a_row0 + i, a_k0 + k] B[b_row0 + j, b_k0 + k], alpha = +1 or -1
 // over `chunks` K chunks; lower: only col <= row (M == N).  splits > 1 sums
@@ -218,10 +257,13 @@ size_t ozaki_partial_bytes(int M, int N, int splits);
 // caps the persistent grid (leaves SMs free for work on another stream).
 // kdepth (multiple of 32, at most 128; 0 = 128): K entries of each chunk that
 // are multiplied -- the rest of the chunk must be zero slices.
+// max_items > 0: at most that many work items per CTA (the grid grows past
+// the SM count, so CTAs retire regularly and pending CTAs of other kernels,
+// higher-priority ones first, get SMs).
 cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &B, int b_row0, int b_k0,
                        int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
                        int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas = 0,
-                       int kdepth = 0);
+                       int kdepth = 0, int max_items = 0);
 // Lower triangle of src (FP64) -> dst in double-float storage (upper set to 0); src may == dst.
 cudaError_t to_df_lower(int n, const double *src, long long lds, double *dst, long long ldd, cudaStream_t s);
 // m x c block in double-float storage -> FP64, in place.

@@ -508,41 +508,64 @@ cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_of
   }
   const size_t smem = (size_t)nb * (nb + 1) * sizeof(double);
   GPC_LAUNCH(GPC_TRACE_DIAG, (double)nb * nb * nb / 3.0, 16.0 * nb * nb, s,
-             potrf_diag_kernel<<<1, DIAG_THREADS, smem, s>>>(nb, A, lda, info, pivot_offset, df ? 1 : 0));
+             launch_k(potrf_diag_kernel, 1, DIAG_THREADS, smem, s, nb, A, lda, info, pivot_offset, df ? 1 : 0));
   return cudaGetLastError();
+}
+
+// The panel solves run beside the split products' CTAs (one product CTA per
+// SM holds ~219 KB of shared memory, leaving room for a small solve CTA).  An
+// SM runs CTAs of one shared-memory configuration at a time, so the solve
+// kernels ask for the same maximal shared-memory carveout as the products.
+bool g_trsm_carveout[64];
+cudaError_t trsm_carveout() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaSuccess;
+  if (g_trsm_carveout[dev]) return cudaSuccess;
+  const void *fns[] = {(const void *)trsm_quad_kernel<64, 0>, (const void *)trsm_quad_kernel<64, 1>,
+                       (const void *)trsm_quad_kernel<128, 0>, (const void *)trsm_quad_kernel<128, 1>,
+                       (const void *)trsm_rows_kernel<8>, (const void *)trsm_rows_kernel<16>,
+                       (const void *)trsm_rows_kernel<32>};
+  for (const void *f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  g_trsm_carveout[dev] = true;
+  return cudaSuccess;
 }
 
 cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, long long ldt, int mode,
                       cudaStream_t s, bool df) {
   if (m <= 0 || nb <= 0) return cudaSuccess;
   if (nb > kMaxBlock) return cudaErrorInvalidValue;
+  if (cudaError_t ce = trsm_carveout(); ce != cudaSuccess) return ce;
   const double fl = (double)m * nb * nb, by = 16.0 * (double)m * nb + 4.0 * nb * nb;
   const unsigned qgrid = (unsigned)((m + TQ_THREADS / 4 - 1) / (TQ_THREADS / 4));
   if (nb == 64 || nb == 128) {
     if (nb == 64 && mode == 0)
-      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, trsm_quad_kernel<64, 0><<<qgrid, TQ_THREADS, 0, s>>>(m, X, ldx, T, ldt, df));
+      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, launch_k(trsm_quad_kernel<64, 0>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df));
     else if (nb == 64)
-      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, trsm_quad_kernel<64, 1><<<qgrid, TQ_THREADS, 0, s>>>(m, X, ldx, T, ldt, df));
+      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, launch_k(trsm_quad_kernel<64, 1>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df));
     else if (mode == 0)
-      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, trsm_quad_kernel<128, 0><<<qgrid, TQ_THREADS, 0, s>>>(m, X, ldx, T, ldt, df));
+      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, launch_k(trsm_quad_kernel<128, 0>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df));
     else
-      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, trsm_quad_kernel<128, 1><<<qgrid, TQ_THREADS, 0, s>>>(m, X, ldx, T, ldt, df));
+      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, launch_k(trsm_quad_kernel<128, 1>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df));
     return cudaGetLastError();
   }
   // other block sizes: 32 rows per CTA when that still gives two CTAs per SM, else 16 or 8
   const int sms = sm_count();
   if ((m + 31) / 32 >= 2 * sms) {
     GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
-               trsm_rows_kernel<32><<<(m + 31) / 32, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode,
-                                                                            df ? 1 : 0));
+               launch_k(trsm_rows_kernel<32>, (m + 31) / 32, 256, 0, s, m, nb, X, ldx, T, ldt, mode,
+                        df ? 1 : 0));
   } else if ((m + 15) / 16 >= sms) {
     GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
-               trsm_rows_kernel<16><<<(m + 15) / 16, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode,
-                                                                            df ? 1 : 0));
+               launch_k(trsm_rows_kernel<16>, (m + 15) / 16, 256, 0, s, m, nb, X, ldx, T, ldt, mode,
+                        df ? 1 : 0));
   } else {
     GPC_LAUNCH(GPC_TRACE_TRSM, (double)m * nb * nb, 16.0 * (double)m * nb + 4.0 * nb * nb, s,
-               trsm_rows_kernel<8><<<(m + 7) / 8, 256, 0, s>>>(m, nb, X, ldx, T, ldt, mode,
-                                                                            df ? 1 : 0));
+               launch_k(trsm_rows_kernel<8>, (m + 7) / 8, 256, 0, s, m, nb, X, ldx, T, ldt, mode,
+                        df ? 1 : 0));
   }
   return cudaGetLastError();
 }

@@ -604,22 +604,87 @@ __global__ void ltv_reduce_kernel(int n, int chunks, const double *partial, doub
   z[col] = s;
 }
 
-__global__ void lml_lbar_kernel(int n, const double *L, long long ldl, const double *alpha,
-                                const double *z, double gbar, double *Lbar, long long ldlb, int df) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * n) return;
-  const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
-  double v = 0.0;
-  if (j <= i) {
-    v = alpha[i] * z[j];
-    if (i == j) v -= 1.0 / L[(long long)i * ldl + i];
-    v *= gbar;
+// Lbar = gbar (tril(alpha z^T) - diag(1 / L_ii)), zero strict upper triangle.
+// 2-D tiles of 32 rows x 128 columns, 16 entries per thread (4 rows x 4
+// columns 32 apart, so every store of a warp covers one contiguous row piece).
+// FP64 path: v = alpha_i z_j (one FP64 multiply per lower entry, then gbar).
+// Double-float path (the mixed adjoint's input): alpha_i gbar and z_j are
+// split into FP32 pairs once per row / column and their product is formed
+// with the FMA-based two-product in FP32 arithmetic (about 2^-46 relative),
+// so no FP64 instruction runs per entry; the diagonal is formed in FP64.
+constexpr int LB_ROWS = 32, LB_COLS = 128;
+__global__ void __launch_bounds__(256)
+lml_lbar_kernel(int n, const double *L, long long ldl, const double *alpha, const double *z, double gbar,
+                double *Lbar, long long ldlb, int df) {
+  const int r0 = blockIdx.y * LB_ROWS, c0 = blockIdx.x * LB_COLS;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (c0 > r0 + LB_ROWS - 1) {  // tile wholly above the diagonal: zeros
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = r0 + ty + 8 * v;
+      if (i >= n) continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = c0 + tx + 32 * u;
+        if (j < n) Lbar[(long long)i * ldlb + j] = 0.0;
+      }
+    }
+    return;
   }
-  if (df) {  // double-float storage (FP32 hi + lo in the 8 bytes), as the mixed adjoint takes it
-    const float h = __double2float_rn(v);
-    reinterpret_cast<float2 *>(Lbar)[(long long)i * ldlb + j] = make_float2(h, __double2float_rn(v - (double)h));
-  } else {
-    Lbar[(long long)i * ldlb + j] = v;
+  if (!df) {
+    double zj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = c0 + tx + 32 * u;
+      zj[u] = j < n ? z[j] : 0.0;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = r0 + ty + 8 * v;
+      if (i >= n) continue;
+      const double ai = alpha[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = c0 + tx + 32 * u;
+        if (j >= n) continue;
+        double val = 0.0;
+        if (j <= i) {
+          val = ai * zj[u];
+          if (i == j) val -= 1.0 / L[(long long)i * ldl + i];
+          val *= gbar;
+        }
+        Lbar[(long long)i * ldlb + j] = val;
+      }
+    }
+    return;
+  }
+  dfa::df zj[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = c0 + tx + 32 * u;
+    zj[u] = dfa::from_double(j < n ? z[j] : 0.0);
+  }
+  float2 *out = reinterpret_cast<float2 *>(Lbar);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int i = r0 + ty + 8 * v;
+    if (i >= n) continue;
+    const dfa::df ai = dfa::from_double(alpha[i] * gbar);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = c0 + tx + 32 * u;
+      if (j >= n) continue;
+      float2 val = make_float2(0.f, 0.f);
+      if (j < i) {
+        const dfa::df p = dfa::mul(ai, zj[u]);
+        val = make_float2(p.hi, p.lo);
+      } else if (j == i) {
+        const double d = (alpha[i] * z[i] - 1.0 / L[(long long)i * ldl + i]) * gbar;
+        const dfa::df p = dfa::from_double(d);
+        val = make_float2(p.hi, p.lo);
+      }
+      out[(long long)i * ldlb + j] = val;
+    }
   }
 }
 
@@ -906,9 +971,9 @@ cudaError_t lml_lbar(int n, const double *L, long long ldl, const double *alpha,
                      double gbar, double *Lbar, long long ldlb, cudaStream_t s, bool df) {
   if (n <= 0) return cudaSuccess;
   const long long total = (long long)n * n;
+  dim3 grid((unsigned)((n + LB_COLS - 1) / LB_COLS), (unsigned)((n + LB_ROWS - 1) / LB_ROWS));
   GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (double)total, s,
-             lml_lbar_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, L, ldl, alpha, z,
-                                                                             gbar, Lbar, ldlb, df ? 1 : 0));
+             lml_lbar_kernel<<<grid, 256, 0, s>>>(n, L, ldl, alpha, z, gbar, Lbar, ldlb, df ? 1 : 0));
   return cudaGetLastError();
 }
 

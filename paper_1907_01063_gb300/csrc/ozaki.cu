@@ -583,10 +583,11 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 // Operand element (r, k) = src[r * rs + k * ks] for r < M, k < K.  Chunk 0
 // covers k in [0, first), chunk c >= 1 covers [first + 128 (c - 1), + 128).
 // Output planes: dst[p * plane + r * kpad + c * 128 + kk] (BF16), zero where
-// the operand has no element.  Grid: (chunks, rows_pad / 32), 256 threads.
+// the operand has no element; rows r >= row_end are not written.  Grid:
+// (chunks, ceil(row_end / 32)), 256 threads.
 __global__ void __launch_bounds__(256)
 split_kernel(const double *src, long long rs, long long ks, int M, int K, int first, __nv_bfloat16 *dst,
-             long long plane, int kpad) {
+             long long plane, int kpad, int row_end) {
   __shared__ double tile[32][129];
   const int c = blockIdx.x, r0 = blockIdx.y * 32;
   const int kbeg = (c == 0) ? 0 : first + (c - 1) * OZ_CHUNK;
@@ -624,6 +625,7 @@ split_kernel(const double *src, long long rs, long long ks, int M, int K, int fi
       for (int pp = 0; pp < OZ_S; ++pp) out[pp][i] = __bfloat16_as_ushort(__float2bfloat16_rn(v[pp]));
     }
     const int r = r0 + rr;
+    if (r >= row_end) continue;
 #pragma unroll
     for (int pp = 0; pp < OZ_S; ++pp) {
       uint2 pack;
@@ -715,17 +717,19 @@ SliceBuf slice_view(void *base, int rows, int kchunks) {
 }
 
 cudaError_t split_operand(const double *src, long long rs, long long ks, int M, int K, int first,
-                          const SliceBuf &out, cudaStream_t s, int chunk_offset) {
+                          const SliceBuf &out, cudaStream_t s, int chunk_offset, int row_offset) {
   if (M <= 0 || K <= 0) return cudaSuccess;
   const int op_chunks = (K <= first) ? 1 : 1 + (K - first + OZ_CHUNK - 1) / OZ_CHUNK;
   const int chunks = std::min(op_chunks, out.kpad / OZ_CHUNK - chunk_offset);
-  if (chunks <= 0) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)chunks, (unsigned)(out.rows_pad / 32));
+  if (chunks <= 0 || row_offset < 0 || row_offset + M > out.rows_pad) return cudaErrorInvalidValue;
+  // rows written: the operand's M rows (at row_offset), or every row of the buffer when row_offset == 0
+  const int row_end = row_offset > 0 ? M : out.rows_pad;
+  dim3 grid((unsigned)chunks, (unsigned)((row_end + 31) / 32));
   const long long plane = (long long)out.rows_pad * out.kpad;
-  GPC_LAUNCH(GPC_TRACE_SPLIT, 0.0, 8.0 * M * K + 2.0 * OZ_S * (double)out.rows_pad * chunks * OZ_CHUNK, s,
-             split_kernel<<<grid, 256, 0, s>>>(src, rs, ks, M, K, first,
-                                               (__nv_bfloat16 *)out.base + (long long)chunk_offset * OZ_CHUNK,
-                                               plane, out.kpad));
+  GPC_LAUNCH(GPC_TRACE_SPLIT, 0.0, 8.0 * M * K + 2.0 * OZ_S * (double)row_end * chunks * OZ_CHUNK, s,
+             launch_k(split_kernel, grid, 256, 0, s, src, rs, ks, M, K, first,
+                      (__nv_bfloat16 *)out.base + (long long)row_offset * out.kpad + (long long)chunk_offset * OZ_CHUNK,
+                      plane, out.kpad, row_end));
   return cudaGetLastError();
 }
 
@@ -735,7 +739,8 @@ size_t ozaki_partial_bytes(int M, int N, int splits) {
 
 cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &B, int b_row0, int b_k0,
                        int M, int N, int chunks, bool lower, float alpha, float2 *C, long long ldc,
-                       int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas, int kdepth) {
+                       int splits, float2 *partial, int *err, cudaStream_t s, int max_ctas, int kdepth,
+                       int max_items) {
   if (M <= 0 || N <= 0 || chunks <= 0) return cudaSuccess;
   if (kdepth <= 0) kdepth = OZ_CHUNK;
   if (kdepth > OZ_CHUNK || kdepth % OZ_BK) return cudaErrorInvalidValue;
@@ -786,13 +791,14 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
                            : (M >= N ? 0.5 * (double)N * (N + 1) + (double)(M - N) * N : 0.5 * (double)M * (M + 1));
   const double flops = 2.0 * mn * (double)chunks * kdepth * 15.0;  // 15 slice products
   const double bytes = 16.0 * mn * chunks + (double)(M + N) * chunks * kdepth * 2 * OZ_S;
-  const int grid = std::min(p.num_work, ctas);
+  int grid = std::min(p.num_work, ctas);
+  if (max_items > 0) grid = std::max(grid, (p.num_work + max_items - 1) / max_items);
   if (alpha < 0.0f)
     GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, bytes, s,
-               ozaki_gemm_kernel<true><<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
+               launch_k(ozaki_gemm_kernel<true>, grid, OZ_THREADS, OZ_SMEM_BYTES, s, ma, mb, p));
   else
     GPC_LAUNCH(GPC_TRACE_GEMM_MIXED, flops, bytes, s,
-               ozaki_gemm_kernel<false><<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, p));
+               launch_k(ozaki_gemm_kernel<false>, grid, OZ_THREADS, OZ_SMEM_BYTES, s, ma, mb, p));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const long long total = (long long)M * N;

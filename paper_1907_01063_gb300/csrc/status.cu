@@ -72,6 +72,29 @@ int *error_word() {
   return symbol_address(g_error_word, g_error_cache, &p) == cudaSuccess ? (int *)p : nullptr;
 }
 
+namespace {
+thread_local int t_launch_priority = 0;
+}
+
+int launch_priority() { return t_launch_priority; }
+
+PriorityScope::PriorityScope(int p) : saved(t_launch_priority) { t_launch_priority = p; }
+PriorityScope::~PriorityScope() { t_launch_priority = saved; }
+
+int greatest_priority() {
+  static int cached[SymbolCache::kMaxDevices];
+  static bool have[SymbolCache::kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SymbolCache::kMaxDevices) return 0;
+  if (!have[dev]) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) greatest = 0;
+    cached[dev] = greatest;
+    have[dev] = true;
+  }
+  return cached[dev];
+}
+
 Faults &faults() {
   static Faults f;
   return f;

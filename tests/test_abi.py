@@ -173,3 +173,28 @@ def test_error_word_and_fault_knobs_host_checks():
                                 (gp.GPC_TEST_OZAKI_NO_LOADS, 1, 0)):
         assert c.gpc_test_set_fault(key, value) == gp.GPC_OK
         assert c.gpc_test_set_fault(key, default) == gp.GPC_OK
+
+
+def test_mixed_schedule_knobs_roundtrip_and_validation():
+    knobs = {gp.GPC_TUNE_MIXED_DEFER: ((1, 8), (0, 9)), gp.GPC_TUNE_MIXED_FREE_SMS: ((0, 32), (-1, 33)),
+             gp.GPC_TUNE_MIXED_CTA_ITEMS: ((0, 1024), (-1, 1025)), gp.GPC_TUNE_MIXED_PRIORITY: ((0, 1), (-1, 2))}
+    for key, (good, bad) in knobs.items():
+        old = gp.get_tuning(key)
+        try:
+            for v in good:
+                gp.set_tuning(key, v)
+                assert gp.get_tuning(key) == v
+            for v in bad:
+                with pytest.raises(gp.GpcholError):
+                    gp.set_tuning(key, v)
+        finally:
+            gp.set_tuning(key, old)
+    # the deferral depth enters the mixed workspace size (its group slice buffers)
+    old = gp.get_tuning(gp.GPC_TUNE_MIXED_DEFER)
+    try:
+        gp.set_tuning(gp.GPC_TUNE_MIXED_DEFER, 1)
+        small = gp.workspace_size(8192, "mixed")
+        gp.set_tuning(gp.GPC_TUNE_MIXED_DEFER, 8)
+        assert gp.workspace_size(8192, "mixed") >= small
+    finally:
+        gp.set_tuning(gp.GPC_TUNE_MIXED_DEFER, old)
