@@ -111,8 +111,8 @@ trtri_batched_kernel(int n, const double *L, long long ldl, int first, int b, do
 }
 
 // 1/x and 1/sqrt(x) for normal positive x: the hardware's approximations
-// refined by two Newton-Raphson steps, y <- y (2 - x y) and
-// y <- y (3 - x y^2) / 2 (each step doubles the correct bits; the result is
+// refined, 1/x by two Newton-Raphson steps y <- y (2 - x y) (each doubles the
+// correct bits), 1/sqrt(x) as below; the results are
 // within 2 ulp of the correctly rounded value, checked against CUDA's 1.0 / x
 // and rsqrt over the normal range by gpc_test_recip_rsqrt's test; recip_nr
 // needs 1/x normal too, x < 2^1022, which holds for any pivot of a matrix whose
@@ -127,13 +127,17 @@ __device__ __forceinline__ double recip_nr(double x) {
   e = fma(-x, y, 1.0);
   return fma(y, e, y);
 }
+// 1/sqrt(x) refines the hardware seed y with one third-order step of the
+// series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ..., e = 1 - x y^2 (the error of
+// a seed with relative error d is cubed, about 2.5 d^3): four dependent FP64
+// operations instead of the six of two Newton-Raphson steps.
 __device__ __forceinline__ double rsqrt_nr(double x) {
   if (!(x >= 2.2250738585072014e-308)) return 1.0 / sqrt(x);
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double hx = 0.5 * x;
-  y = y * fma(-hx, y * y, 1.5);
-  return y * fma(-hx, y * y, 1.5);
+  const double e = fma(-x, y * y, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  return fma(y * e, p, y);
 }
 
 // Cholesky factor of one nb x nb diagonal block in shared memory (the small-
@@ -442,6 +446,163 @@ __global__ void recip_rsqrt_probe_kernel(int n, const double *x, double *out) {
   out[4 * i + 3] = rsqrt(v);
 }
 
+// Cholesky factor of one nb x nb diagonal block, nb <= 64, with a one-column
+// lookahead (the small-block step of Section 3.3).  Column k+1 is finished
+// (pivot, 1/sqrt, scaling) by one warp while six other warps apply column k
+// to the rest of the block.  On this part a dependent FP64 operation costs
+// about 60 cycles and one SM sustains under two FP64 multiply-adds per cycle,
+// so the pivot chain and the trailing updates must overlap, and no FP64
+// instruction may issue with lanes that have nothing to do (a warp
+// instruction costs the FP64 pipe the same time whatever its active mask):
+//   * warp 0 (the pivot warp) finishes columns: for column k+1 it applies the
+//     column-k update itself, takes r = 1/sqrt(pivot) and writes the final
+//     column to shared memory, then publishes col_ready = k+1;
+//   * warps 1-3 and 5-7 (the updaters, u = 0..5) own whole columns j = u mod 6,
+//     lane l holding rows j + l and j + l + 32 in registers, so whether a
+//     column takes part in a step is the same for the whole warp; at step k,
+//     once column k is final, the owner of column k+2 (the one the pivot warp
+//     finishes next) updates and stores it first and marks rounds[k+1], then
+//     every warp updates its later columns (rounds[0]: columns 0 and 1 stored
+//     as loaded, one mark per warp);
+//   * warp 4 idles, so the pivot warp has its SM sub-partition to itself.
+// Every wait is a bounded spin on a shared-memory word; a wait that runs out
+// records GPC_ERR_TIMEOUT and stops the block.  The first failing pivot is
+// recorded like potrf_diag_kernel does, and the rest of the block is written
+// back unfinished.
+constexpr int PL_NB = 64, PL_LD = PL_NB + 1, PL_W = 6, PL_COLS = (PL_NB + PL_W - 1) / PL_W;
+constexpr long long PL_SPIN = 1LL << 24;
+
+__global__ void __launch_bounds__(256)
+potrf_la_kernel(int nb, double *A, long long lda, int *info, int pivot_offset, int df, int *gerr) {
+  __shared__ double M[PL_NB * PL_LD];
+  __shared__ int col_ready, stop;
+  __shared__ int rounds[PL_NB];  // rounds[r]: marks of round r
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    col_ready = -1;
+    stop = 0;
+  }
+  if (threadIdx.x < PL_NB) rounds[threadIdx.x] = 0;
+  const bool updater = warp != 0 && warp != 4;
+  const int uw = updater ? warp - 1 - (warp > 4) : 0;
+  double a0[PL_COLS], a1[PL_COLS];  // column uw + 6 c: rows j + lane, j + lane + 32
+  if (updater) {
+#pragma unroll
+    for (int c = 0; c < PL_COLS; ++c) {
+      const int j = uw + PL_W * c, r0 = j + lane, r1 = r0 + 32;
+      a0[c] = (j < nb && r0 < nb) ? load_entry(A + (long long)r0 * lda + j, df) : 0.0;
+      a1[c] = (j < nb && r1 < nb) ? load_entry(A + (long long)r1 * lda + j, df) : 0.0;
+    }
+  }
+  __syncthreads();
+  volatile int *vready = &col_ready, *vstop = &stop;
+  // Polls: the updaters back off between polls, so that their loads do not
+  // queue in front of the pivot warp's shared-memory accesses.
+  auto spin_ge = [&](volatile int *w, int target) -> bool {
+    for (long long it = 0; it < PL_SPIN; ++it) {
+      if (*w >= target) return true;
+      if (*vstop) return false;
+      if (updater) __nanosleep(64);
+    }
+    return false;
+  };
+  auto give_up = [&]() {  // a wait ran out: report and stop the block
+    if (info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
+    record_error(gerr, GPC_ERR_TIMEOUT);
+    *vstop = 1;
+  };
+  if (updater) {
+    // round 0: columns 0 and 1 as loaded (owned by updaters 0 and 1)
+    if (uw <= 1 && uw < nb) {
+      const int j = uw, r0 = j + lane, r1 = r0 + 32;
+      if (r0 < nb) M[r0 * PL_LD + j] = a0[0];
+      if (r1 < nb) M[r1 * PL_LD + j] = a1[0];
+    }
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) atomicAdd(&rounds[0], 1);
+  }
+  if (warp == 0) {
+    // ---- pivot warp: lanes own rows lane and lane + 32
+    for (int c = 0; c < nb; ++c) {
+      // column c comes from round max(c - 1, 0)
+      if (!spin_ge((volatile int *)&rounds[max(c - 1, 0)], c <= 1 ? PL_W : 1)) {
+        if (!*vstop && lane == 0) give_up();
+        break;
+      }
+      __threadfence_block();
+      const int i0 = lane, i1 = lane + 32;
+      double v0 = (i0 >= c && i0 < nb) ? M[i0 * PL_LD + c] : 0.0;
+      double v1 = (i1 >= c && i1 < nb) ? M[i1 * PL_LD + c] : 0.0;
+      if (c > 0) {  // the update by column c - 1, finished by this warp just before
+        const double lc = M[c * PL_LD + c - 1];
+        if (i0 >= c && i0 < nb) v0 = fma(-M[i0 * PL_LD + c - 1], lc, v0);
+        if (i1 >= c && i1 < nb) v1 = fma(-M[i1 * PL_LD + c - 1], lc, v1);
+      }
+      const double pv = (c < 32) ? __shfl_sync(0xffffffffu, v0, c) : __shfl_sync(0xffffffffu, v1, c - 32);
+      if (!(pv > 0.0 && pv <= 1.79769313486231570e308)) {
+        if (lane == 0) {
+          if (info && info[1] == 0) {
+            info[0] = pivot_offset + c;
+            info[1] = (pv != pv || pv > 1.79769313486231570e308) ? GPC_ERR_NAN : GPC_ERR_NOT_PD;
+          }
+          *vstop = 1;
+        }
+        break;
+      }
+      const double r = rsqrt_nr(pv);  // every lane: no broadcast on the chain
+      if (i0 >= c && i0 < nb) M[i0 * PL_LD + c] = (i0 == c) ? pv * r : v0 * r;
+      if (i1 >= c && i1 < nb) M[i1 * PL_LD + c] = (i1 == c) ? pv * r : v1 * r;
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) *vready = c;
+    }
+  } else if (updater) {
+    // ---- updaters: step k applies column k to columns k + 2 .. nb - 1
+    for (int k = 0; k + 2 < nb; ++k) {
+      if (!spin_ge(vready, k)) {
+        if (!*vstop && lane == 0) give_up();
+        break;
+      }
+      __threadfence_block();
+#pragma unroll
+      for (int c = 0; c < PL_COLS; ++c) {
+        const int j = uw + PL_W * c;
+        if (j == k + 2) {  // warp-uniform: the column the pivot warp needs next
+          const double ljk = M[j * PL_LD + k];
+          const int r0 = j + lane, r1 = r0 + 32;
+          if (r0 < nb) {
+            a0[c] = fma(-M[r0 * PL_LD + k], ljk, a0[c]);
+            M[r0 * PL_LD + j] = a0[c];
+          }
+          if (r1 < nb) {
+            a1[c] = fma(-M[r1 * PL_LD + k], ljk, a1[c]);
+            M[r1 * PL_LD + j] = a1[c];
+          }
+          __threadfence_block();
+          __syncwarp();
+          if (lane == 0) atomicAdd(&rounds[k + 1], 1);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < PL_COLS; ++c) {
+        const int j = uw + PL_W * c;
+        if (j > k + 2 && j < nb) {  // warp-uniform
+          const double ljk = M[j * PL_LD + k];
+          const int r0 = j + lane, r1 = r0 + 32;
+          if (r0 < nb) a0[c] = fma(-M[r0 * PL_LD + k], ljk, a0[c]);
+          if (j + 32 < nb && r1 < nb) a1[c] = fma(-M[r1 * PL_LD + k], ljk, a1[c]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx / nb, c = idx - r * nb;
+    A[(long long)r * lda + c] = (c <= r) ? M[r * PL_LD + c] : 0.0;
+  }
+}
+
 }  // namespace
 
 static cudaError_t launch_diag(int nb, double *A, long long lda, double *Winv, int *info,
@@ -505,6 +666,11 @@ cudaError_t potrf_diag(int nb, double *A, long long lda, int *info, int pivot_of
                                          (int)((size_t)kMaxBlock * (kMaxBlock + 1) * sizeof(double)));
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
+  }
+  if (nb <= PL_NB) {  // blocks of up to 64: the lookahead kernel
+    GPC_LAUNCH(GPC_TRACE_DIAG, (double)nb * nb * nb / 3.0, 16.0 * nb * nb, s,
+               launch_k(potrf_la_kernel, 1, 256, 0, s, nb, A, lda, info, pivot_offset, df ? 1 : 0, error_word()));
+    return cudaGetLastError();
   }
   const size_t smem = (size_t)nb * (nb + 1) * sizeof(double);
   GPC_LAUNCH(GPC_TRACE_DIAG, (double)nb * nb * nb / 3.0, 16.0 * nb * nb, s,
