@@ -555,6 +555,11 @@ def main():
     if not args.no_autotune:
         from paper_1907_01063_gb300 import autotune
         tuned["fp64_block"] = autotune.tune_fp64_block()["best"]
+        if "mixed" in precisions:
+            rec = autotune.tune_mixed(n)
+            tuned["mixed_schedule"] = dict(rec["best"], timed_at_n=rec["n"],
+                                           product_k_tile=128 * rec["best"]["mixed_defer"])
+            tuned["mixed_schedule_ms"] = rec["ms"]
 
     results = {p_: run(p_) for p_ in precisions}
 

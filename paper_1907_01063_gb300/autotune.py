@@ -13,7 +13,19 @@ Knobs:
     on a batch of GPs with the caller's size mix, separately per precision.
   * fp64_block: block size of the FP64 blocked factorisation and adjoint
     (64, 96 or 128), timed on chol + adjoint at a stand-in order.
-The mixed path's block is fixed to its 128-wide slice chunk.
+  * the mixed schedule (tune_mixed): the update depth D -- the tcgen05
+    trailing and background products take K = 128 D per read-modify-write of
+    their double-float output tiles (D in 1, 2, 4, 6, 8) -- and the SMs the
+    background products leave to the FP64 chain in the factorisation (2, 4,
+    8) and in the adjoint (8, 16, 24); the slice chunk (the K tile of one
+    exponent group) stays 128.
+  * the FP64 schedule (tune_fp64): the block size above together with the
+    minimum K per split of the split-K products (the K tile of a partial
+    product: 32, 64, 128).
+Schedules with several knobs are searched coordinate by coordinate
+(coordinate_search): each knob in turn over its candidates with the others
+held at their best so far.  Cache keys carry the device, the precision and the
+order rounded up to a power of two between 1024 and 16384 (n_bucket).
 """
 from __future__ import annotations
 
@@ -119,6 +131,112 @@ def tune_fp64_block(n: int = 4096, force: bool = False) -> dict:
     db[key] = rec
     _store(db)
     return rec
+
+
+def n_bucket(n: int) -> int:
+    """The order a tuning result is keyed and timed at: n rounded up to a power
+    of two, clamped to [1024, 16384]."""
+    b = 1024
+    while b < n and b < 16384:
+        b *= 2
+    return b
+
+
+def coordinate_search(knobs, measure, start=None) -> dict:
+    """Coordinate search over knob values.
+
+    knobs: list of (name, candidates); measure(config: dict) -> ms.  Starting
+    from ``start`` (default: every knob's first candidate), each knob in turn
+    is set to each of its candidates with the other knobs fixed at their best
+    so far, and keeps the fastest (ties: the earlier candidate).  Returns
+    {"best": config, "ms": {description: ms}} with every configuration timed."""
+    best = dict(start) if start else {name: cands[0] for name, cands in knobs}
+    times = {}
+
+    def key(cfg):
+        return ",".join(f"{k}={cfg[k]}" for k, _ in knobs)
+
+    for name, cands in knobs:
+        scores = []
+        for c in cands:
+            cfg = dict(best, **{name: c})
+            k = key(cfg)
+            if k not in times:
+                times[k] = float(measure(cfg))
+            scores.append((times[k], c))
+        best[name] = min(scores, key=lambda sc: sc[0])[1]
+    return {"best": best, "ms": times}
+
+
+_MIXED_KNOBS = [("mixed_defer", (4, 1, 2, 6, 8)), ("mixed_free_sms", (4, 2, 8)),
+                ("mixed_adj_free_sms", (16, 8, 24))]
+_FP64_KNOBS = [("fp64_block", (128, 64, 96)), ("splitk_min", (32, 64, 128))]
+_KNOB_IDS = {"mixed_defer": gp.GPC_TUNE_MIXED_DEFER, "mixed_free_sms": gp.GPC_TUNE_MIXED_FREE_SMS,
+             "mixed_adj_free_sms": gp.GPC_TUNE_MIXED_ADJ_FREE_SMS, "fp64_block": gp.GPC_TUNE_BLOCK,
+             "splitk_min": gp.GPC_TUNE_SPLITK_MIN}
+
+
+def _apply(cfg: dict):
+    for name, value in cfg.items():
+        gp.set_tuning(_KNOB_IDS[name], int(value))
+
+
+def _chol_adjoint_stand_in(n: int):
+    """An SE covariance of order n (built by the library) and a random lower L-bar."""
+    X = torch.as_tensor(W.gp_inputs(n, 16, seed=0), device="cuda")
+    K = gp.se_cov(X, 1.0, 4.0, 0.3, 1e-6)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    return K, torch.tril(torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g))
+
+
+def _tune_schedule(kind: str, precision: str, knobs, n: int, force: bool) -> dict:
+    nb = n_bucket(n)
+    key = f"{_device_key()}/{kind}/{nb}"
+    db = _load()
+    if key in db and not force:
+        _apply(db[key]["best"])
+        return db[key]
+    K, Lbar = _chol_adjoint_stand_in(nb)
+    saved = {name: gp.get_tuning(_KNOB_IDS[name]) for name, _ in knobs}
+    ws_cache = {}
+
+    def measure(cfg):
+        _apply(cfg)
+        size = gp.workspace_size(nb, precision)
+        if size not in ws_cache:
+            ws_cache.clear()
+            torch.cuda.empty_cache()
+            ws_cache[size] = gp.workspace(nb, precision)
+        ws = ws_cache[size]
+        L = torch.empty_like(K)
+
+        def run():
+            gp.chol(K, precision, out=L, ws=ws, check=False)
+            gp.chol_adjoint(L, Lbar, precision=precision, ws=ws)
+
+        return _time(run)
+
+    try:
+        res = coordinate_search(knobs, measure, start=saved)
+    finally:
+        _apply(saved)
+    _apply(res["best"])
+    rec = {"best": res["best"], "ms": res["ms"], "n": nb, "when": time.time()}
+    db[key] = rec
+    _store(db)
+    return rec
+
+
+def tune_mixed(n: int = 16384, force: bool = False) -> dict:
+    """Tune the mixed schedule (update depth D, free SMs of the factorisation
+    and of the adjoint) on chol + adjoint at n_bucket(n); applies the result."""
+    return _tune_schedule("mixed", "mixed", _MIXED_KNOBS, n, force)
+
+
+def tune_fp64(n: int = 4096, force: bool = False) -> dict:
+    """Tune the FP64 schedule (block size, split-K minimum K per split) on
+    chol + adjoint at n_bucket(n); applies the result."""
+    return _tune_schedule("fp64", "fp64", _FP64_KNOBS, n, force)
 
 
 class _EventTimer:
@@ -233,11 +351,15 @@ def apply_cached() -> dict:
         if "/fp64_block/" in key:
             gp.set_tuning(gp.GPC_TUNE_BLOCK, rec["best"])
             applied["fp64_block"] = rec["best"]
+        elif "/mixed/" in key or "/fp64/" in key:
+            _apply(rec["best"])
+            applied.update(rec["best"])
     return applied
 
 
 if __name__ == "__main__":
     print(tune_fp64_block(force=True))
+    print(tune_mixed(16384, force=True))
     sizes = W.batch_sizes(512, 64, 1024, seed=0)
     b = gp.Batch(sizes)
     rows = int(np.sum(sizes))

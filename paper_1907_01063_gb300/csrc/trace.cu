@@ -97,14 +97,30 @@ void drain(TraceState &t, bool block) {
 
 }  // namespace
 
-// The kernel's name is the launch expression's text up to "<<<".
+// The kernel's name is the launch expression's text up to "<<<", or, for a
+// launch through launch_k(kernel, ...), its first argument (commas inside
+// template brackets belong to the name).
 int name_id(TraceState &t, const char *what) {
   auto it = t.name_ids.find(what);
   if (it != t.name_ids.end()) return it->second;
   std::string n(what);
-  const size_t cut = n.find("<<<");
-  if (cut != std::string::npos) n.resize(cut);
+  const std::string lk = "launch_k(";
+  const size_t at = n.find(lk);
+  if (at != std::string::npos && n.find("<<<") == std::string::npos) {
+    size_t i = at + lk.size(), depth = 0, end = i;
+    for (; end < n.size(); ++end) {
+      const char ch = n[end];
+      if (ch == '<') ++depth;
+      else if (ch == '>' && depth > 0) --depth;
+      else if (ch == ',' && depth == 0) break;
+    }
+    n = n.substr(i, end - i);
+  } else {
+    const size_t cut = n.find("<<<");
+    if (cut != std::string::npos) n.resize(cut);
+  }
   while (!n.empty() && (n.back() == ' ' || n.back() == '\n')) n.pop_back();
+  while (!n.empty() && (n.front() == ' ' || n.front() == '\n' || n.front() == '{')) n.erase(0, 1);
   const int id = (int)t.names.size();
   t.names.push_back(n);
   t.name_ids.emplace(what, id);

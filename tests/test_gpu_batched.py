@@ -10,6 +10,13 @@ from paper_1907_01063_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
+# Mixed path: split-BF16 products with double-float accumulation and FP64
+# refinement of alpha; the value and gradient stay within 1e-9 / 1e-7
+# (relative) of the FP64 oracle on these conditioning levels (sigma = 0.1, so
+# cond(K) is at most about n / sigma^2 ~ 1e5).
+MIXED_VALUE_TOL, MIXED_GRAD_TOL = 1e-9, 1e-7
+
+
 def make_batch(sizes, d=4, seed=0, sigma=0.1):
     rho = W.batch_lengthscales(len(sizes), 0.2, 2.0, seed=seed + 1)
     Xs, ys, hyps = [], [], []
@@ -97,17 +104,22 @@ def test_batched_rejects_sizes_above_nmax_on_device():
     assert info[0, 1] == gp.GPC_OK and info[1, 1] == gp.GPC_ERR_INVALID_ARG
 
 
-def test_batched_config5_sample():
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_config5_sample(precision):
     # the batch workload's size mix (n ~ U{64..1024}, d = 4, rho ~ U(0.2, 2)),
-    # checked on a few members against the oracle
+    # checked against the oracle on its three smallest and three largest
+    # members (the largest take the most blocks of the per-GP sweep)
     sizes = list(W.batch_sizes(64, 64, 1024, seed=0))
     Xs, ys, hyps = make_batch(sizes, seed=0)
-    _, v, g, info = run_batch(sizes, Xs, ys, hyps)
+    _, v, g, info = run_batch(sizes, Xs, ys, hyps, precision=precision)
     assert np.all(info[:, 1] == gp.GPC_OK)
-    for i in np.argsort(sizes)[:3]:
+    vtol, gtol = (1e-10, 1e-8) if precision == "fp64" else (MIXED_VALUE_TOL, MIXED_GRAD_TOL)
+    order = np.argsort(sizes)
+    assert sizes[order[-1]] > 900
+    for i in list(order[:3]) + list(order[-3:]):
         ref = O.gp_lml_and_grad(Xs[i], ys[i], *hyps[i], 0.0)
-        assert abs(v[i] - ref["value"]) <= 1e-10 * max(1.0, abs(ref["value"]))
-        assert np.linalg.norm(g[i] - ref["grad"]) <= 1e-8 * np.linalg.norm(ref["grad"])
+        assert abs(v[i] - ref["value"]) <= vtol * max(1.0, abs(ref["value"])), (i, sizes[i])
+        assert np.linalg.norm(g[i] - ref["grad"]) <= gtol * np.linalg.norm(ref["grad"]), (i, sizes[i])
 
 
 def test_batched_graph_replay_matches_direct_call():
@@ -131,11 +143,7 @@ def test_batched_graph_replay_matches_direct_call():
 
 
 # ---------------------------------------------------------------- mixed path
-# Split-BF16 products with double-float accumulation and FP64 refinement of
-# alpha: the value and gradient stay within 1e-9 / 1e-7 (relative) of the
-# FP64 oracle on these conditioning levels (sigma = 0.1, so cond(K) is at most
-# about n / sigma^2 ~ 1e5).
-MIXED_VALUE_TOL, MIXED_GRAD_TOL = 1e-9, 1e-7
+# (tolerances MIXED_VALUE_TOL, MIXED_GRAD_TOL are defined at the top)
 
 
 @pytest.mark.parametrize("block", [32, 64])

@@ -21,7 +21,8 @@ def test_timeline_lists_every_launch_in_order():
     spans = gp.trace_timeline()
     assert len(spans) == gp.launch_count() - c0 > 0
     names = [s["kernel"] for s in spans]
-    assert names.count("potrf_diag_kernel") == (n + 127) // 128
+    assert names.count("potrf_diag_kernel") == (n + 127) // 128  # FP64 block 128: the 128-wide kernel
+    assert all("launch_k" not in nm and "<<<" not in nm for nm in names)
     assert all(s["dur_ms"] > 0 for s in spans)
     starts = [s["start_ms"] for s in spans]
     assert starts[0] == 0.0 and all(b >= a for a, b in zip(starts, starts[1:]))

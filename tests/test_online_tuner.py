@@ -94,3 +94,59 @@ def test_online_tuner_on_the_fp64_factorisation():
     ref = O.chol(L0 @ L0.T)
     for L in outs:
         assert np.linalg.norm(L.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_coordinate_search_walks_each_knob_with_the_others_at_their_best():
+    from paper_1907_01063_gb300.autotune import coordinate_search
+    # separable cost with a unique optimum at a=2, b=30; first candidates are the start
+    cost = {("a", 1): 5.0, ("a", 2): 1.0, ("a", 3): 4.0, ("b", 10): 3.0, ("b", 20): 2.0, ("b", 30): 0.5}
+    calls = []
+
+    def measure(cfg):
+        calls.append(dict(cfg))
+        return cost[("a", cfg["a"])] + cost[("b", cfg["b"])]
+
+    res = coordinate_search([("a", (1, 2, 3)), ("b", (10, 20, 30))], measure)
+    assert res["best"] == {"a": 2, "b": 30}
+    # a varied with b at its start value, then b varied with a at its best; no repeats
+    assert calls == [{"a": 1, "b": 10}, {"a": 2, "b": 10}, {"a": 3, "b": 10}, {"a": 2, "b": 20}, {"a": 2, "b": 30}]
+    assert len(res["ms"]) == 5
+    # ties keep the earlier candidate; an explicit start is honoured
+    res = coordinate_search([("a", (1, 2))], lambda cfg: 1.0, start={"a": 2})
+    assert res["best"] == {"a": 1}
+
+
+def test_n_bucket():
+    from paper_1907_01063_gb300.autotune import n_bucket
+    assert [n_bucket(n) for n in (1, 1024, 1025, 3000, 16384, 20000)] == [1024, 1024, 2048, 4096, 16384, 16384]
+
+
+@pytest.mark.gpu
+def test_tuned_mixed_schedule_runs_at_parity(tmp_path, monkeypatch):
+    # tune the mixed schedule at a small order (cache in a scratch file), then
+    # run the factorisation and adjoint with the chosen knobs against the oracle
+    from oracle import oracle as O
+    from paper_1907_01063_gb300 import workloads as W
+    monkeypatch.setenv("GPCHOL_TUNE_CACHE", str(tmp_path / "tune.json"))
+    ids = [gp.GPC_TUNE_MIXED_DEFER, gp.GPC_TUNE_MIXED_FREE_SMS, gp.GPC_TUNE_MIXED_ADJ_FREE_SMS]
+    saved = [gp.get_tuning(k) for k in ids]
+    try:
+        rec = autotune.tune_mixed(1000)
+        assert rec["n"] == 1024 and set(rec["best"]) == {"mixed_defer", "mixed_free_sms", "mixed_adj_free_sms"}
+        assert gp.get_tuning(gp.GPC_TUNE_MIXED_DEFER) == rec["best"]["mixed_defer"]
+        n = 1000
+        X = W.gp_inputs(n, 3, seed=4)
+        K = O.se_cov(X, 1.0, 1.0, 0.3, 1e-6)
+        Lo = O.chol(K)
+        Lbar = W.random_lower(n, seed=5)
+        Go = O.chol_adjoint(Lo, Lbar)
+        L = gp.chol(torch.as_tensor(K, device="cuda"), "mixed").cpu().numpy()
+        G = gp.chol_adjoint(torch.as_tensor(Lo, device="cuda"), torch.as_tensor(Lbar, device="cuda"),
+                            precision="mixed").cpu().numpy()
+        assert np.linalg.norm(L - Lo) <= 1e-9 * np.linalg.norm(Lo)
+        assert np.linalg.norm(G - Go) <= 1e-8 * np.linalg.norm(Go)
+        # a second call reads the cache instead of timing again
+        assert autotune.tune_mixed(1000)["when"] == rec["when"]
+    finally:
+        for k, v in zip(ids, saved):
+            gp.set_tuning(k, v)
