@@ -297,7 +297,8 @@ int gpc_gemm_adjoint(int m, int n, int k, const double *A, int lda, const double
  *   GPC_GLM_BERNOULLI_LOGIT  y_i ~ Bernoulli(1 / (1 + e^-eta_i)) (y_i in {0, 1})
  *   GPC_GLM_POISSON_LOG      y_i ~ Poisson(e^eta_i)              (y_i = 0, 1, 2, ...)
  * Writes lp = sum_i log p(y_i), dalpha = d lp / d alpha, dbeta (k) = d lp / d beta,
- * and dsigma = d lp / d sigma (normal family; 0 otherwise); all four are
+ * and dsigma = d lp / d sigma (normal family; d lp / d phi for the negative
+ * binomial below; 0 otherwise); all four are
  * device pointers.  alpha and sigma are host scalars; y and beta are device
  * vectors.  One pass over X; results are bitwise reproducible.  The family's
  * support of y is not checked.
@@ -309,11 +310,49 @@ int gpc_gemm_adjoint(int m, int n, int k, const double *A, int lda, const double
 #define GPC_GLM_NORMAL_ID 0
 #define GPC_GLM_BERNOULLI_LOGIT 1
 #define GPC_GLM_POISSON_LOG 2
+#define GPC_GLM_NEG_BINOMIAL_LOG 3
 #define GPC_GLM_MAX_K 12288
 int gpc_glm_workspace_size(int k, size_t *bytes);
 int gpc_glm(int family, long long n, int k, const double *X, long long ldx, const double *y, double alpha,
             const double *beta, double sigma, double *lp, double *dalpha, double *dbeta, double *dsigma,
             void *ws, size_t ws_bytes, gpc_stream_t stream);
+
+/*
+ * GPC_GLM_NEG_BINOMIAL_LOG (gpc_glm above, Section 3.4): y_i ~ NegBinomial with
+ * mean mu_i = e^eta_i and dispersion phi = sigma (> 0), variance mu + mu^2/phi:
+ *   log p(y_i) = lgamma(y_i + phi) - lgamma(y_i + 1) - lgamma(phi)
+ *                + phi (log phi - log(mu_i + phi)) + y_i (eta_i - log(mu_i + phi));
+ * dsigma receives d lp / d phi (with the digamma function).
+ *
+ * Ordinal-logit GLM (Section 3.4, ordinal regression): C ordered classes,
+ * y_i in {0, .., C - 1} (device vector of exact integers), eta_i = X_i . beta
+ * (no intercept: the C - 1 increasing cut points c_m take its place) and
+ *   P(y = m) = s(eta - c_{m-1}) - s(eta - c_m),  s(t) = 1 / (1 + e^-t),
+ * with s(eta - c_{-1}) = 1 and s(eta - c_{C-1}) = 0.  Writes lp = sum log P(y_i),
+ * dbeta (k) and dcuts (C - 1) = d lp / d c (device pointers).  2 <= C <=
+ * GPC_GLM_MAX_CLASSES; a y_i outside the classes makes lp NaN.  Workspace:
+ * gpc_glm_workspace_size(k).  One pass over X, bitwise reproducible.
+ *
+ * Categorical-logit GLM (Section 3.4, multinomial logistic regression): C
+ * classes, scores eta_ic = alpha_c + X_i . beta_c with alpha (C) and beta
+ * (k x C, row-major: beta[j * C + c]) device arrays; lp_i = eta_{i,y_i} -
+ * log sum_c e^eta_ic.  Writes lp, dalpha (C) and dbeta (k x C, same layout).
+ * 2 <= C <= GPC_GLM_MAX_CLASSES and k C <= GPC_GLM_MAX_KC; a y_i outside the
+ * classes makes lp NaN.  Workspace: gpc_glm_categorical_workspace_size(k, C).
+ *
+ * Both: GPC_ERR_INVALID_ARG (nothing enqueued) for n < 0, k < 0, C outside
+ * its range, null pointers, ldx < k or a short workspace; GPC_ERR_CUDA on a
+ * launch error.
+ */
+#define GPC_GLM_MAX_CLASSES 16
+#define GPC_GLM_MAX_KC 8192
+int gpc_glm_ordinal(long long n, int k, int C, const double *X, long long ldx, const double *y,
+                    const double *beta, const double *cuts, double *lp, double *dbeta, double *dcuts, void *ws,
+                    size_t ws_bytes, gpc_stream_t stream);
+int gpc_glm_categorical_workspace_size(int k, int C, size_t *bytes);
+int gpc_glm_categorical(long long n, int k, int C, const double *X, long long ldx, const double *y,
+                        const double *alpha, const double *beta, double *lp, double *dalpha, double *dbeta,
+                        void *ws, size_t ws_bytes, gpc_stream_t stream);
 
 /*
  * Gaussian-process log marginal likelihood of y ~ N(0, K), the likelihood of

@@ -70,6 +70,11 @@ _SIGNATURES = {
     "gpc_glm_workspace_size": ([_c_int, ctypes.POINTER(_c_size)], _c_int),
     "gpc_glm": ([_c_int, ctypes.c_longlong, _c_int, _c_vp, ctypes.c_longlong, _c_vp, _c_double, _c_vp, _c_double,
                  _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
+    "gpc_glm_ordinal": ([ctypes.c_longlong, _c_int, _c_int, _c_vp, ctypes.c_longlong, _c_vp, _c_vp, _c_vp, _c_vp,
+                         _c_vp, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
+    "gpc_glm_categorical_workspace_size": ([_c_int, _c_int, ctypes.POINTER(_c_size)], _c_int),
+    "gpc_glm_categorical": ([ctypes.c_longlong, _c_int, _c_int, _c_vp, ctypes.c_longlong, _c_vp, _c_vp, _c_vp,
+                             _c_vp, _c_vp, _c_vp, _c_vp, _c_size, _c_vp], _c_int),
     "gpc_tri_solve": ([_c_int, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp],
                       _c_int),
     "gpc_tri_solve_adjoint": ([_c_int, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_int,
@@ -100,7 +105,9 @@ _SIGNATURES = {
 
 TRACE_CLASSES = {"gemm_f64": 0, "diag": 1, "trsv": 2, "se_cov": 3, "hyper_grad": 4, "elementwise": 5,
                  "gemm_mixed": 6, "split": 7, "trsm": 8, "glm": 9}
-GLM_FAMILIES = {"normal_id": 0, "bernoulli_logit": 1, "poisson_log": 2}
+GLM_FAMILIES = {"normal_id": 0, "bernoulli_logit": 1, "poisson_log": 2, "neg_binomial_2_log": 3}
+GPC_GLM_MAX_CLASSES = 16
+GPC_GLM_MAX_KC = 8192
 GPC_GLM_MAX_K = 12288
 
 
@@ -497,6 +504,48 @@ def glm(family: str, X: torch.Tensor, y: torch.Tensor, alpha: float, beta: torch
                         out.data_ptr(), out.data_ptr() + 8, _ptr(dbeta), out.data_ptr() + 16, _ptr(ws), ws.numel(),
                         _stream()), "gpc_glm")
     return {"lp": out[0], "dalpha": out[1], "dbeta": dbeta, "dsigma": out[2]}
+
+
+def glm_ordinal(X: torch.Tensor, y: torch.Tensor, beta: torch.Tensor, cuts: torch.Tensor,
+                ws: torch.Tensor | None = None) -> dict:
+    """Ordinal-logit GLM: y in {0..C-1}, increasing cuts (C-1); dict(lp, dbeta, dcuts) of device tensors."""
+    n, k, ldx = _rows(X, "X")
+    _vector(y, n, "y")
+    _vector(beta, k, "beta")
+    C = int(cuts.shape[0]) + 1
+    _vector(cuts, C - 1, "cuts")
+    dev = X.device
+    if ws is None:
+        ws = glm_workspace(k, dev)
+    lp = torch.empty((), dtype=torch.float64, device=dev)
+    dbeta = torch.empty(k, dtype=torch.float64, device=dev)
+    dcuts = torch.empty(C - 1, dtype=torch.float64, device=dev)
+    _check(capi.gpc_glm_ordinal(n, k, C, _ptr(X), ldx, _ptr(y), _ptr(beta), _ptr(cuts), lp.data_ptr(), _ptr(dbeta),
+                                dcuts.data_ptr(), _ptr(ws), ws.numel(), _stream()), "gpc_glm_ordinal")
+    return {"lp": lp, "dbeta": dbeta, "dcuts": dcuts}
+
+
+def glm_categorical(X: torch.Tensor, y: torch.Tensor, alpha: torch.Tensor, beta: torch.Tensor,
+                    ws: torch.Tensor | None = None) -> dict:
+    """Categorical-logit GLM: y in {0..C-1}, alpha (C), beta (k x C); dict(lp, dalpha, dbeta) of device tensors."""
+    n, k, ldx = _rows(X, "X")
+    _vector(y, n, "y")
+    C = int(alpha.shape[0])
+    _vector(alpha, C, "alpha")
+    if not (beta.is_cuda and beta.dtype == torch.float64 and tuple(beta.shape) == (k, C) and beta.is_contiguous()):
+        raise ValueError(f"beta must be a contiguous float64 CUDA matrix of shape ({k}, {C})")
+    dev = X.device
+    if ws is None:
+        b = ctypes.c_size_t()
+        _check(capi.gpc_glm_categorical_workspace_size(k, C, ctypes.byref(b)), "gpc_glm_categorical_workspace_size")
+        ws = torch.empty(b.value, dtype=torch.uint8, device=dev)
+    lp = torch.empty((), dtype=torch.float64, device=dev)
+    dalpha = torch.empty(C, dtype=torch.float64, device=dev)
+    dbeta = torch.empty(k, C, dtype=torch.float64, device=dev)
+    _check(capi.gpc_glm_categorical(n, k, C, _ptr(X), ldx, _ptr(y), _ptr(alpha), _ptr(beta), lp.data_ptr(),
+                                    dalpha.data_ptr(), _ptr(dbeta), _ptr(ws), ws.numel(), _stream()),
+           "gpc_glm_categorical")
+    return {"lp": lp, "dalpha": dalpha, "dbeta": dbeta}
 
 
 def gp_lml(K: torch.Tensor, y: torch.Tensor, precision="fp64", L: torch.Tensor | None = None,

@@ -315,15 +315,45 @@ int gpc_glm_workspace_size(int k, size_t *bytes) {
 int gpc_glm(int family, long long n, int k, const double *X, long long ldx, const double *y, double alpha,
             const double *beta, double sigma, double *lp, double *dalpha, double *dbeta, double *dsigma,
             void *ws, size_t ws_bytes, gpc_stream_t stream) {
-  if (family != GPC_GLM_NORMAL_ID && family != GPC_GLM_BERNOULLI_LOGIT && family != GPC_GLM_POISSON_LOG)
+  if (family != GPC_GLM_NORMAL_ID && family != GPC_GLM_BERNOULLI_LOGIT && family != GPC_GLM_POISSON_LOG &&
+      family != GPC_GLM_NEG_BINOMIAL_LOG)
     return GPC_ERR_INVALID_ARG;
   if (n < 0 || k < 0 || k > GPC_GLM_MAX_K || !lp || !dalpha || !dsigma || !ws ||
       ws_bytes < glm_workspace_bytes(k))
     return GPC_ERR_INVALID_ARG;
-  if (family == GPC_GLM_NORMAL_ID && !(sigma > 0.0 && sigma <= 1.79769313486231570e308)) return GPC_ERR_INVALID_ARG;
+  if ((family == GPC_GLM_NORMAL_ID || family == GPC_GLM_NEG_BINOMIAL_LOG) &&
+      !(sigma > 0.0 && sigma <= 1.79769313486231570e308))
+    return GPC_ERR_INVALID_ARG;
   if (!(alpha == alpha) || (k > 0 && (!beta || !dbeta)) || (n > 0 && (!y || (k > 0 && (!X || ldx < k)))))
     return GPC_ERR_INVALID_ARG;
   return status_of(glm(family, n, k, X, ldx, y, alpha, beta, sigma, lp, dalpha, dbeta, dsigma, ws, stream));
+}
+
+int gpc_glm_ordinal(long long n, int k, int C, const double *X, long long ldx, const double *y,
+                    const double *beta, const double *cuts, double *lp, double *dbeta, double *dcuts, void *ws,
+                    size_t ws_bytes, gpc_stream_t stream) {
+  if (n < 0 || k < 0 || k > GPC_GLM_MAX_K || C < 2 || C > GPC_GLM_MAX_CLASSES || !lp || !dcuts || !cuts || !ws ||
+      ws_bytes < glm_workspace_bytes(k))
+    return GPC_ERR_INVALID_ARG;
+  if ((k > 0 && (!beta || !dbeta)) || (n > 0 && (!y || (k > 0 && (!X || ldx < k))))) return GPC_ERR_INVALID_ARG;
+  return status_of(glm_ordinal(n, k, C, X, ldx, y, beta, cuts, lp, dbeta, dcuts, ws, stream));
+}
+
+int gpc_glm_categorical_workspace_size(int k, int C, size_t *bytes) {
+  if (!bytes || k < 0 || C < 2 || C > GPC_GLM_MAX_CLASSES || (long long)k * C > GPC_GLM_MAX_KC)
+    return GPC_ERR_INVALID_ARG;
+  *bytes = glm_categorical_workspace_bytes(k, C);
+  return GPC_OK;
+}
+
+int gpc_glm_categorical(long long n, int k, int C, const double *X, long long ldx, const double *y,
+                        const double *alpha, const double *beta, double *lp, double *dalpha, double *dbeta,
+                        void *ws, size_t ws_bytes, gpc_stream_t stream) {
+  if (n < 0 || k < 0 || C < 2 || C > GPC_GLM_MAX_CLASSES || (long long)k * C > GPC_GLM_MAX_KC || !lp || !alpha ||
+      !dalpha || !ws || ws_bytes < glm_categorical_workspace_bytes(k, C))
+    return GPC_ERR_INVALID_ARG;
+  if ((k > 0 && (!beta || !dbeta)) || (n > 0 && (!y || (k > 0 && (!X || ldx < k))))) return GPC_ERR_INVALID_ARG;
+  return status_of(glm_categorical(n, k, C, X, ldx, y, alpha, beta, lp, dalpha, dbeta, ws, stream));
 }
 
 int gpc_tri_inverse(int n, const double *L, int ldl, double *Linv, int ldi, gpc_stream_t stream) {

@@ -174,6 +174,15 @@ size_t glm_workspace_bytes(int k);
 cudaError_t glm(int family, long long n, int k, const double *X, long long ldx, const double *y, double alpha,
                 const double *beta, double sigma, double *lp, double *dalpha, double *dbeta, double *dsigma,
                 void *ws, cudaStream_t s);
+// Ordinal-logit GLM (C ordered classes, C - 1 cut points); workspace as glm.
+cudaError_t glm_ordinal(long long n, int k, int C, const double *X, long long ldx, const double *y,
+                        const double *beta, const double *cuts, double *lp, double *dbeta, double *dcuts, void *ws,
+                        cudaStream_t s);
+// Categorical-logit GLM (C classes, beta k x C row-major).
+size_t glm_categorical_workspace_bytes(int k, int C);
+cudaError_t glm_categorical(long long n, int k, int C, const double *X, long long ldx, const double *y,
+                            const double *alpha, const double *beta, double *lp, double *dalpha, double *dbeta,
+                            void *ws, cudaStream_t s);
 // Triangular inverse, solve and solve adjoint (trinv.cu); X is the inverse.
 cudaError_t tri_inverse(int n, const double *L, long long ldl, double *X, long long ldx, cudaStream_t s);
 cudaError_t tri_solve(int n, int m, const double *L, long long ldl, const double *B, long long ldb, double *X,

@@ -198,3 +198,22 @@ def test_mixed_schedule_knobs_roundtrip_and_validation():
         assert gp.workspace_size(8192, "mixed") >= small
     finally:
         gp.set_tuning(gp.GPC_TUNE_MIXED_DEFER, old)
+
+
+def test_glm_family_argument_checks():
+    c = gp.capi
+    bad = gp.GPC_ERR_INVALID_ARG
+    fake = 0x1000
+    size = ctypes.c_size_t()
+    assert c.gpc_glm_categorical_workspace_size(10, 1, ctypes.byref(size)) == bad       # C < 2
+    assert c.gpc_glm_categorical_workspace_size(10, 17, ctypes.byref(size)) == bad      # C > max
+    assert c.gpc_glm_categorical_workspace_size(4096, 3, ctypes.byref(size)) == bad     # k C > max
+    assert c.gpc_glm_categorical_workspace_size(100, 3, ctypes.byref(size)) == gp.GPC_OK and size.value > 0
+    # ordinal: C range, missing cuts, short workspace -- all before any launch
+    assert c.gpc_glm_ordinal(10, 2, 1, fake, 2, fake, fake, fake, fake, fake, fake, fake, 1 << 30, None) == bad
+    assert c.gpc_glm_ordinal(10, 2, 3, fake, 2, fake, fake, None, fake, fake, fake, fake, 1 << 30, None) == bad
+    assert c.gpc_glm_ordinal(10, 2, 3, fake, 2, fake, fake, fake, fake, fake, fake, fake, 8, None) == bad
+    assert c.gpc_glm_categorical(-1, 2, 3, fake, 2, fake, fake, fake, fake, fake, fake, fake, 1 << 30, None) == bad
+    assert c.gpc_glm_categorical(10, 2, 3, fake, 1, fake, fake, fake, fake, fake, fake, fake, 1 << 30, None) == bad
+    # the negative binomial needs a positive dispersion
+    assert c.gpc_glm(3, 10, 2, fake, 2, fake, 0.0, fake, 0.0, fake, fake, fake, fake, fake, 1 << 30, None) == bad

@@ -67,7 +67,7 @@ def test_autograd_matmul_matches_oracle():
     assert rel(Bt.grad.cpu().numpy(), Bb0) <= TOL
 
 
-FAMILIES = ["normal_id", "bernoulli_logit", "poisson_log"]
+FAMILIES = ["normal_id", "bernoulli_logit", "poisson_log", "neg_binomial_2_log"]
 GLM_SIZES = [(0, 5), (1, 1), (7, 0), (100, 3), (1000, 64), (3000, 300), (2000, 1025), (50, 5000)]
 
 
@@ -77,9 +77,12 @@ def glm_case(family, n, k, seed):
     beta = rng.standard_normal(k) / max(1.0, np.sqrt(k))
     alpha = 0.2
     eta = alpha + X @ beta
+    mu = np.exp(np.clip(eta, -5, 5))
+    phi = 0.7  # the dispersion check_glm passes as sigma
     y = {"normal_id": eta + rng.standard_normal(n),
          "bernoulli_logit": (rng.random(n) < 0.5).astype(float),
-         "poisson_log": rng.poisson(np.exp(np.clip(eta, -5, 5))).astype(float)}[family]
+         "poisson_log": rng.poisson(mu).astype(float),
+         "neg_binomial_2_log": rng.negative_binomial(phi, phi / (phi + mu)).astype(float)}[family]
     return X, y, alpha, beta
 
 
@@ -143,3 +146,88 @@ def test_glm_bench_workload_whole():
     beta = np.zeros(k)
     beta[0], beta[1] = 3.0, -2.0
     check_glm("bernoulli_logit", X, y, 1.0, beta)
+
+
+@pytest.mark.parametrize("phi", [0.013, 0.7, 3.0, 9.99, 10.0, 57.5, 2500.0])
+def test_neg_binomial_dispersion_derivative_and_digamma(phi):
+    # one observation per call, no covariates: dsigma = psi(y + phi) - psi(phi)
+    # + log phi - log(mu + phi) + 1 - (y + phi)/(mu + phi), so the device
+    # digamma is compared with the oracle's over small and large arguments
+    for y0 in (0.0, 1.0, 3.0, 9.0, 42.0, 1000.0, 123456.0):
+        X = np.zeros((1, 0))
+        y = np.array([y0])
+        check_glm("neg_binomial_2_log", X, y, 0.3, np.zeros(0), sigma=phi)
+
+
+def ordinal_case(n, k, C, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, k))
+    beta = rng.standard_normal(k) / max(1.0, np.sqrt(k))
+    cuts = np.sort(rng.standard_normal(C - 1)) * 1.5
+    eta = X @ beta
+    s = 1.0 / (1.0 + np.exp(-(eta[:, None] - cuts[None, :])))  # P(y > m)
+    u = rng.random(n)
+    y = np.sum(u[:, None] < s, axis=1).astype(float)
+    return X, y, beta, cuts
+
+
+ORD_SIZES = [(0, 3, 3), (1, 1, 2), (7, 0, 4), (100, 3, 4), (1000, 64, 5), (3000, 300, 16), (2000, 1025, 3),
+             (50, 5000, 2)]
+
+
+@pytest.mark.parametrize("n,k,C", ORD_SIZES)
+def test_glm_ordinal_matches_oracle(n, k, C):
+    X, y, beta, cuts = ordinal_case(n, k, C, seed=n + k + C)
+    r0 = O.glm_ordinal(X, y, beta, cuts)
+    r = gp.glm_ordinal(dev(X), dev(y), dev(beta), dev(cuts))
+    assert abs(r["lp"].item() - r0["lp"]) <= TOL * max(1.0, abs(r0["lp"]))
+    if k:
+        assert rel(r["dbeta"].cpu().numpy(), r0["dbeta"]) <= 10 * TOL
+    assert np.allclose(r["dcuts"].cpu().numpy(), r0["dcuts"], rtol=10 * TOL,
+                       atol=10 * TOL * max(1.0, np.abs(r0["dcuts"]).max(initial=0.0)))
+
+
+def categorical_case(n, k, C, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, k))
+    beta = rng.standard_normal((k, C)) / max(1.0, np.sqrt(k))
+    alpha = rng.standard_normal(C) * 0.5
+    eta = alpha[None, :] + X @ beta
+    p = np.exp(eta - eta.max(axis=1, keepdims=True))
+    p /= p.sum(axis=1, keepdims=True)
+    u = rng.random(n)
+    y = np.minimum(np.sum(u[:, None] > np.cumsum(p, axis=1), axis=1), C - 1).astype(float)
+    return X, y, alpha, beta
+
+
+CAT_SIZES = [(0, 3, 3), (1, 1, 2), (7, 0, 4), (100, 3, 4), (1000, 64, 5), (3000, 300, 16), (2000, 500, 8),
+             (50, 4096, 2)]
+
+
+@pytest.mark.parametrize("n,k,C", CAT_SIZES)
+def test_glm_categorical_matches_oracle(n, k, C):
+    X, y, alpha, beta = categorical_case(n, k, C, seed=3 * n + k + C)
+    r0 = O.glm_categorical(X, y, alpha, beta)
+    r = gp.glm_categorical(dev(X), dev(y), dev(alpha), dev(beta))
+    assert abs(r["lp"].item() - r0["lp"]) <= TOL * max(1.0, abs(r0["lp"]))
+    da = r["dalpha"].cpu().numpy()
+    assert np.allclose(da, r0["dalpha"], rtol=10 * TOL, atol=10 * TOL * max(1.0, np.abs(r0["dalpha"]).max(initial=0.0)))
+    if k:
+        assert rel(r["dbeta"].cpu().numpy(), r0["dbeta"]) <= 10 * TOL
+
+
+def test_glm_class_labels_outside_the_support_give_nan():
+    X = np.ones((3, 2))
+    yo = np.array([0.0, 5.0, 1.0])  # 5 is not a class of C = 3
+    r = gp.glm_ordinal(dev(X), dev(yo), dev(np.array([0.1, 0.2])), dev(np.array([-0.5, 0.5])))
+    assert np.isnan(r["lp"].item())
+    yc = np.array([0.0, -1.0, 1.0])
+    r = gp.glm_categorical(dev(X), dev(yc), dev(np.zeros(3)), dev(np.ones((2, 3))))
+    assert np.isnan(r["lp"].item())
+
+
+def test_glm_categorical_is_bitwise_reproducible():
+    X, y, alpha, beta = categorical_case(40000, 100, 6, seed=9)
+    a = gp.glm_categorical(dev(X), dev(y), dev(alpha), dev(beta))
+    b = gp.glm_categorical(dev(X), dev(y), dev(alpha), dev(beta))
+    assert a["lp"].item() == b["lp"].item() and torch.equal(a["dbeta"], b["dbeta"])
