@@ -710,10 +710,11 @@ def main():
     fp64_peak = gp.fp64_peak_gflops(dev)
     nominal_fp64 = peaks.get("bf16_tflops", 1900.0) * 1e3 * 1.25 / 2250.0
 
-    # DRAM bytes (read + write) per launch of the split product, averaged over the
-    # 1015 launches of one mixed step at n = 16384, from the ncu capture summarised
-    # in profiles/gp_step_mixed_n16384_launches.md; other sizes have no capture.
-    ozaki_traffic = {16384: 237.17e6}
+    # DRAM bytes per launch of the split product averaged over a step: no capture
+    # of the current schedule (deferred K = 128 D updates) takes DRAM counters over
+    # every launch of a full-size step, so the field is null; one launch's DRAM
+    # traffic against its work is in profiles/ozaki_gemm_kernel_k128_vs_k768_n8192.md.
+    ozaki_traffic = {}
 
     def roofline(res):
         trace = {k: dict(v, ms=v["ms"] / res["trace_steps"], flops=v["flops"] / res["trace_steps"],
@@ -728,7 +729,7 @@ def main():
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": ozaki_traffic.get(n), "launches_per_step": dom["launches"],
                     "avg_launch_ms": avg, "peak_source": "of measured: MEASURED_PEAKS bf16_tflops_sustained",
-                    "traffic_unit": "bytes per launch (ncu, averaged over a step's launches)",
+                    "traffic_note": "null: no per-launch DRAM capture of the current schedule at this size",
                     "fp64_equivalent_gflops": dom["flops"] / 15.0 / (dom["ms"] / 1e3) / 1e9}
         if dom_name in ("gemm_f64", "diag", "trsm"):
             achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] else 0.0

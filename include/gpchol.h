@@ -111,9 +111,9 @@ int gpc_workspace_size(int n, int precision, size_t *bytes);
 #define GPC_TUNE_SPLITK_MIN 2
 #define GPC_TUNE_BATCH_BLOCK 3  /* block size inside gpc_batched_gp_lml_grad: 32 or 64 */
 /* Mixed factorisation (GPC_MIXED): block columns (128 wide) whose trailing
- * updates are merged into one product with K = 128 x value (1..8, default 4;
+ * updates are merged into one product with K = 128 x value (1..8, default 6;
  * enters the mixed workspace size); SMs its background products leave to the
- * FP64 chain (0..32, default 4); work items per CTA of a background product
+ * FP64 chain (0..32, default 2); work items per CTA of a background product
  * (0 = one persistent CTA per SM, else 1..1024, so CTAs retire and the
  * chain's kernels get SMs); and whether the chain's launches take the
  * device's greatest stream priority (0 or 1, default 1). */

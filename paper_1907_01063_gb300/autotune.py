@@ -168,7 +168,7 @@ def coordinate_search(knobs, measure, start=None) -> dict:
     return {"best": best, "ms": times}
 
 
-_MIXED_KNOBS = [("mixed_defer", (4, 1, 2, 6, 8)), ("mixed_free_sms", (4, 2, 8)),
+_MIXED_KNOBS = [("mixed_defer", (6, 1, 2, 4, 8)), ("mixed_free_sms", (2, 4, 8)),
                 ("mixed_adj_free_sms", (16, 8, 24))]
 _FP64_KNOBS = [("fp64_block", (128, 64, 96)), ("splitk_min", (32, 64, 128))]
 _KNOB_IDS = {"mixed_defer": gp.GPC_TUNE_MIXED_DEFER, "mixed_free_sms": gp.GPC_TUNE_MIXED_FREE_SMS,

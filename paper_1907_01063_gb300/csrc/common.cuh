@@ -18,8 +18,8 @@ struct Tuning {
   int splitk_min = 32;    // minimum K per split of a split-K product
   int batch_block = 64;   // block size inside the batched per-GP pass (32 or 64)
   int batch_ctas_per_sm = 1;
-  int mixed_defer = 4;    // mixed path: block columns whose trailing updates are merged (K = 128 x this)
-  int mixed_free_sms = 4; // mixed factorisation: SMs the background products leave to the FP64 chain
+  int mixed_defer = 6;    // mixed path: block columns whose trailing updates are merged (K = 128 x this)
+  int mixed_free_sms = 2; // mixed factorisation: SMs the background products leave to the FP64 chain
   int mixed_adj_free_sms = 16;  // mixed adjoint: the same
   int mixed_cta_items = 0;  // mixed path: work items per CTA of a background product (0: persistent)
   int mixed_priority = 1;   // mixed path: launch the critical chain at the device's greatest priority
