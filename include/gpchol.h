@@ -423,8 +423,13 @@ int gpc_se_hyper_grad_workspace_size(int n, size_t *bytes);
  *   value[i], grad3[3i..3i+2], info[2i..2i+1]  outputs per GP (info as for
  *              gpc_chol; a GP whose factorisation fails gets NaN outputs)
  * nmax: host int, at most 4096; workspace from gpc_batched_workspace_size
- * for the same precision (the mixed path needs more: an FP64 copy of each
- * covariance and a residual vector).
+ * for the same precision (per SM room for Kbar, the kernel values, the
+ * diagonal-block inverses and three vectors of order nmax; the mixed path
+ * adds BF16 slice buffers of about 10 nmax^2 bytes, so an FP64 workspace is
+ * too small for it).
+ * The panel solves of the factorisation and of the adjoint are products with
+ * the inverses of the diagonal blocks (formed once per block, right after it
+ * is factored), and the forward and backward solves apply the same inverses.
  * precision GPC_FP64: every step in FP64.  GPC_MIXED: the O(n^3) products
  * (trailing updates of the factorisation and the adjoint's block products)
  * run on the tensor cores as split-BF16 slice products with FP32 group sums

@@ -78,6 +78,36 @@ int *error_word();
 __device__ __forceinline__ void record_error(int *word, int status) {
   if (word) atomicCAS(word, 0, status);
 }
+// 1/x and 1/sqrt(x) for normal positive x: the hardware's approximations
+// refined, 1/x by two Newton-Raphson steps y <- y (2 - x y) (each doubles the
+// correct bits), 1/sqrt(x) as below; the results are
+// within 2 ulp of the correctly rounded value, checked against CUDA's 1.0 / x
+// and rsqrt over the normal range by gpc_test_recip_rsqrt's test; recip_nr
+// needs 1/x normal too, x < 2^1022, which holds for any pivot of a matrix whose
+// entries are below 2^511).  FP64 instructions are scarce on this part, so this
+// short dependent chain is what the diagonal factorisation's serial part waits on.
+__device__ __forceinline__ double recip_nr(double x) {
+  if (!(x >= 2.2250738585072014e-308)) return 1.0 / x;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+// 1/sqrt(x) refines the hardware seed y with one third-order step of the
+// series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ..., e = 1 - x y^2 (the error of
+// a seed with relative error d is cubed, about 2.5 d^3): four dependent FP64
+// operations instead of the six of two Newton-Raphson steps.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x >= 2.2250738585072014e-308)) return 1.0 / sqrt(x);
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y * y, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  return fma(y * e, p, y);
+}
+
 // Fault-injection knobs of the test hooks (gpc_test_set_fault).  wait_ns is
 // the budget of every bounded device wait in the solve and product kernels.
 struct Faults {

@@ -230,6 +230,22 @@ def test_batched_fp64_workspace_refuses_mixed_run():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_refuses_short_workspace(precision):
+    import ctypes
+    sizes = [10, 20]
+    b = gp.Batch(sizes, precision=precision)
+    X = torch.zeros(30, 4, dtype=torch.float64, device="cuda")
+    y = torch.zeros(30, dtype=torch.float64, device="cuda")
+    hyp = torch.ones(2, 3, dtype=torch.float64, device="cuda")
+    code = gp.precision_code(precision)
+    st = gp.capi.gpc_batched_gp_lml_grad(b.batch, b.nmax, b.n.data_ptr(), b.offK.data_ptr(), b.rowX.data_ptr(), 4,
+                                         X.data_ptr(), y.data_ptr(), hyp.data_ptr(), code, b.K.data_ptr(),
+                                         b.value.data_ptr(), b.grad3.data_ptr(), b.info.data_ptr(), b.ws.data_ptr(),
+                                         b.ws.numel() - 1, None)
+    assert st == gp.GPC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_sharded_batch_matches_whole_batch(precision):
     """The GPs of a batch run as three shards dealt by cost (one launch each,
     one after another on this GPU) give the whole batch's results."""
