@@ -230,6 +230,19 @@ __device__ __noinline__ void tile_gemm(const double *A, long long lda, const dou
       }
     }
   }
+  // epilogue: the outputs of a thread are loaded together (when beta != 0)
+  double cv[2][4][4];
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = m0 + frag_row(wm, mi) + g + ((r >> 1) << 3);
+        const int col = n0 + frag_col(wn, ni) + 2 * tg + (r & 1);
+        const bool in = row < M && col < N && !((flags & TG_LOWER) && col > row);
+        cv[mi][ni][r] = (in && beta != 0.0) ? C[(long long)row * ldc + col] : 0.0;
+      }
 #pragma unroll
   for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
@@ -239,9 +252,11 @@ __device__ __noinline__ void tile_gemm(const double *A, long long lda, const dou
         const int row = m0 + frag_row(wm, mi) + g + ((r >> 1) << 3);
         const int col = n0 + frag_col(wn, ni) + 2 * tg + (r & 1);
         if (row >= M || col >= N || ((flags & TG_LOWER) && col > row)) continue;
-        double *dst = C + (long long)row * ldc + col;
-        const double v = alpha * acc[mi][ni][r];
-        *dst = (beta == 0.0) ? v : fma(beta, *dst, v);
+        double v;
+        if (beta == 0.0) v = alpha * acc[mi][ni][r];
+        else if (beta == 1.0) v = fma(alpha, acc[mi][ni][r], cv[mi][ni][r]);  // alpha = +-1 in every call
+        else v = fma(beta, cv[mi][ni][r], alpha * acc[mi][ni][r]);
+        C[(long long)row * ldc + col] = v;
       }
   __syncthreads();
 }
@@ -273,48 +288,76 @@ struct SliceOp {
   int k0;           // first K index used
 };
 
-// Slices of the rows of A (rows x K, row-major, ld lda): operand row r is row r of A.
-__device__ void split_rows_cta(const double *A, long long lda, int rows, int K, bf16 *S, long long plane, int kpad) {
-  const int chunks = (K + SL_CH - 1) / SL_CH;
-  for (int u = threadIdx.x; u < rows * chunks; u += BT) {
-    const int r = u / chunks, c = u - (u / chunks) * chunks, k0 = c * SL_CH;
-    const double *src = A + (long long)r * lda + k0;
-    const int len = min(SL_CH, K - k0);
-    int ex = 0;
-    for (int i = 0; i < len; ++i) ex = max(ex, slice_exponent((unsigned long long)__double_as_longlong(src[i])));
-    bf16 *dst = S + (long long)r * kpad + k0;
-#pragma unroll 4
-    for (int i = 0; i < SL_CH; ++i) {
-      float v[kSlices];
-      split_value(i < len ? (unsigned long long)__double_as_longlong(src[i]) : 0ull, ex, v);
+// Slices of the rows of A (rows x K, row-major, ld lda): operand row r is row
+// r of A.  A warp takes (row, chunk) units, a lane one K index, so reads and
+// slice writes are contiguous; the chunk's exponent is a warp max.  A warp
+// loads eight units before it splits them, so one memory latency covers eight.
+__device__ __noinline__ void split_rows_cta(const double *A, long long lda, int rows, int K, bf16 *S, long long plane, int kpad) {
+  constexpr int U = 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int chunks = (K + SL_CH - 1) / SL_CH, units = rows * chunks;
+  for (int u0 = warp * U; u0 < units; u0 += U * (BT / 32)) {
+    unsigned long long bits[U];
 #pragma unroll
-      for (int pp = 0; pp < kSlices; ++pp) dst[pp * plane + i] = __float2bfloat16_rn(v[pp]);
+    for (int q = 0; q < U; ++q) {
+      const int u = u0 + q, r = u / chunks, k = (u - r * chunks) * SL_CH + lane;
+      bits[q] = (u < units && k < K) ? (unsigned long long)__double_as_longlong(A[(long long)r * lda + k]) : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int u = u0 + q, r = u / chunks, k = (u - r * chunks) * SL_CH + lane;
+      if (u >= units) break;
+      const int ex = __reduce_max_sync(0xffffffffu, slice_exponent(bits[q]));
+      float v[kSlices];
+      split_value(bits[q], ex, v);
+      bf16 *dst = S + (long long)r * kpad + k;
+#pragma unroll
+      for (int pp = 0; pp < kSlices; ++pp) dst[pp * plane] = __float2bfloat16_rn(v[pp]);
     }
   }
+  __syncthreads();
 }
 
 // Slices of the columns of A (Krows x cols, row-major, ld lda): operand row c is
 // column c of A, its K index k is row k of A, stored at K offset koff (a
-// multiple of the chunk).  Consecutive threads take consecutive columns.
-__device__ void split_cols_cta(const double *A, long long lda, int Krows, int cols, bf16 *S, long long plane,
-                               int kpad, int koff) {
-  const int chunks = (Krows + SL_CH - 1) / SL_CH;
-  for (int u = threadIdx.x; u < cols * chunks; u += BT) {
-    const int c = u % cols, ch = u / cols, k0 = ch * SL_CH;
-    const double *src = A + (long long)k0 * lda + c;
-    const int len = min(SL_CH, Krows - k0);
-    int ex = 0;
-    for (int i = 0; i < len; ++i)
-      ex = max(ex, slice_exponent((unsigned long long)__double_as_longlong(src[(long long)i * lda])));
-    bf16 *dst = S + (long long)c * kpad + koff + k0;
-#pragma unroll 4
-    for (int i = 0; i < SL_CH; ++i) {
-      float v[kSlices];
-      split_value(i < len ? (unsigned long long)__double_as_longlong(src[(long long)i * lda]) : 0ull, ex, v);
+// multiple of the chunk).  32 x 32 blocks of A pass through shared memory
+// (T, 32 x 33 doubles) so that both the reads of A and the slice writes are
+// contiguous; the next block is loaded into registers while one is split.
+__device__ __noinline__ void split_cols_cta(const double *A, long long lda, int Krows, int cols, bf16 *S, long long plane,
+                               int kpad, int koff, double (*T)[33]) {
+  constexpr int RW = SL_CH / (BT / 32);  // rows of a block per warp
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rch = (Krows + SL_CH - 1) / SL_CH, cch = (cols + 31) / 32, nblk = rch * cch;
+  double nxt[RW];
+  auto load = [&](int blk) {
+    const int r0 = (blk / cch) * SL_CH, c0 = (blk - (blk / cch) * cch) * 32, col = c0 + lane;
 #pragma unroll
-      for (int pp = 0; pp < kSlices; ++pp) dst[pp * plane + i] = __float2bfloat16_rn(v[pp]);
+    for (int q = 0; q < RW; ++q) {
+      const int row = r0 + warp + q * (BT / 32);
+      nxt[q] = (row < Krows && col < cols) ? A[(long long)row * lda + col] : 0.0;
+    }
+  };
+  if (nblk > 0) load(0);
+  for (int blk = 0; blk < nblk; ++blk) {
+    const int r0 = (blk / cch) * SL_CH, c0 = (blk - (blk / cch) * cch) * 32;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RW; ++q) T[warp + q * (BT / 32)][lane] = nxt[q];
+    __syncthreads();
+    if (blk + 1 < nblk) load(blk + 1);
+    for (int cc = warp; cc < 32; cc += BT / 32) {
+      const int col = c0 + cc;
+      if (col >= cols) break;
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(T[lane][cc]);
+      const int ex = __reduce_max_sync(0xffffffffu, slice_exponent(bits));
+      float v[kSlices];
+      split_value(bits, ex, v);
+      bf16 *dst = S + (long long)col * kpad + koff + r0 + lane;
+#pragma unroll
+      for (int pp = 0; pp < kSlices; ++pp) dst[pp * plane] = __float2bfloat16_rn(v[pp]);
     }
   }
+  __syncthreads();
 }
 
 __device__ __forceinline__ void hmma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
@@ -755,6 +798,8 @@ batched_gp_kernel(BatchParams p) {
   bf16 *sl = reinterpret_cast<bf16 *>(slot + slot_f64_elems(nmax));
   const int kpl = (int)round32(nmax);
   const SliceOp pan{sl + sl_pan_offset(nmax), sl_pan_plane(nmax), 64, 0};
+  double(*tbuf)[33] = reinterpret_cast<double(*)[33]>(&sm.As[0][0]);  // split transpose buffer (FP64 tiles idle)
+  static_assert(sizeof(SmemF::As) >= 32 * 33 * sizeof(double), "transpose buffer");
   for (;;) {
     if (t == 0) s_item = atomicAdd(p.queue, 1);
     __syncthreads();
@@ -783,25 +828,29 @@ batched_gp_kernel(BatchParams p) {
       info[0] = -1;
       info[1] = GPC_OK;
     }
-    // ---- covariance: L gets the lower triangle (zero upper), Kp the kernel values packed
+    // ---- covariance: L gets the lower triangle (zero upper), Kp the kernel
+    // values packed; a warp per row, lanes along the row
     {
       const double a2 = al * al, inv2r2 = 1.0 / (2.0 * rho * rho), dg = a2 + sig * sig;
-      const long long tot = (long long)n * n;
-      for (long long idx = t; idx < tot; idx += BT) {
-        const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
-        double v = 0.0;
-        if (j < i) {
-          double r2 = 0.0;
-          for (int q = 0; q < d; ++q) {
-            const double df = Xg[(long long)i * d + q] - Xg[(long long)j * d + q];
-            r2 = fma(df, df, r2);
+      const int warp = t >> 5, lane = t & 31;
+      for (int i = warp; i < n; i += BT / 32) {
+        const double *xi = Xg + (long long)i * d;
+        double *Li = L + (long long)i * ld;
+        double *Kpi = Kp + packed(i, 0);
+        for (int j = lane; j <= i; j += 32) {
+          double v = dg;
+          if (j < i) {
+            double r2 = 0.0;
+            for (int q = 0; q < d; ++q) {
+              const double df = xi[q] - Xg[(long long)j * d + q];
+              r2 = fma(df, df, r2);
+            }
+            v = a2 * exp(-r2 * inv2r2);
           }
-          v = a2 * exp(-r2 * inv2r2);
-        } else if (j == i) {
-          v = dg;
+          Li[j] = v;
+          Kpi[j] = v;
         }
-        L[idx] = v;
-        if (j <= i) Kp[packed(i, j)] = v;
+        for (int j = i + 1 + lane; j < n; j += 32) Li[j] = 0.0;
       }
     }
     __syncthreads();
@@ -872,21 +921,27 @@ batched_gp_kernel(BatchParams p) {
     q = cta_sum(q, sm);
     if (t == 0) p.value[gi] = -0.5 * q - lsum - 0.5 * (double)n * 1.8378770664093454835606594728112;
     // ---- upstream adjoint Lbar = tril(alpha z^T) - diag(1/L_ii)  (z = L^{-1} y)
-    for (long long idx = t; idx < (long long)n * n; idx += BT) {
-      const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
-      double v = 0.0;
-      if (j <= i) {
-        v = alpha[i] * z[j];
-        if (i == j) v -= 1.0 / L[(long long)i * ld + i];
+    {
+      const int warp = t >> 5, lane = t & 31;
+      for (int i = warp; i < n; i += BT / 32) {
+        const double ai = alpha[i];
+        double *Kbi = Kb + (long long)i * ld;
+        for (int j = lane; j < n; j += 32) {
+          double v = 0.0;
+          if (j <= i) {
+            v = ai * z[j];
+            if (i == j) v -= 1.0 / L[(long long)i * ld + i];
+          }
+          Kbi[j] = v;
+        }
       }
-      Kb[idx] = v;
     }
     __syncthreads();
     // ---- blocked adjoint sweep over the factorisation's blocks, last first
     const SliceOp lt{sl, sl_lt_plane(nmax), kpl, 0};  // operand row c = column c of L, K = rows of L
     const SliceOp bc{sl + sl_bc_offset(nmax), sl_bc_plane(nmax), kpl, 0};  // the block column [Dbar; Cbar]^T
     if constexpr (MIXED) {
-      split_cols_cta(L, ld, n, n, const_cast<bf16 *>(lt.S), lt.plane, lt.kpad, 0);
+      split_cols_cta(L, ld, n, n, const_cast<bf16 *>(lt.S), lt.plane, lt.kpad, 0, tbuf);
       __syncthreads();
     }
     for (int s = nblk - 1; s >= 0; --s) {
@@ -901,7 +956,7 @@ batched_gp_kernel(BatchParams p) {
         cta_gemm<false, false>(Cbar, ld, Di, bn, Cbar, ld, m, bn, bn, 1.0, 0.0, TG_B_KGE, sm);  // Cbar D^{-1}
         if constexpr (MIXED) {
           split_rows_cta(Cbar, ld, m, bn, const_cast<bf16 *>(pan.S), pan.plane, pan.kpad);
-          split_cols_cta(Cbar, ld, m, bn, const_cast<bf16 *>(bc.S), bc.plane, bc.kpad, bn);
+          split_cols_cta(Cbar, ld, m, bn, const_cast<bf16 *>(bc.S), bc.plane, bc.kpad, bn, tbuf);
           __syncthreads();
           if (j > 0)  // Bbar -= Cbar R
             cta_gemm_sl(pan, SliceOp{lt.S, lt.plane, lt.kpad, j}, Kb + (long long)k * ld, ld, m, j, bn, 0, *ss);
@@ -932,7 +987,7 @@ batched_gp_kernel(BatchParams p) {
       __syncthreads();
       if (j > 0) {  // Rbar -= [Dbar; Cbar]^T [R; B]
         if constexpr (MIXED) {
-          split_cols_cta(Dbar, ld, bn, bn, const_cast<bf16 *>(bc.S), bc.plane, bc.kpad, 0);
+          split_cols_cta(Dbar, ld, bn, bn, const_cast<bf16 *>(bc.S), bc.plane, bc.kpad, 0, tbuf);
           __syncthreads();
           cta_gemm_sl(bc, SliceOp{lt.S, lt.plane, lt.kpad, j}, Kb + (long long)j * ld, ld, bn, j, n - j, 0, *ss);
         } else {
@@ -952,24 +1007,27 @@ batched_gp_kernel(BatchParams p) {
     {
       const double a2 = al * al, two_over_al = 2.0 / al, ir3 = 1.0 / (rho * rho * rho);
       double ga = 0.0, gr = 0.0, gs = 0.0;
-      const long long tot = (long long)n * n;
-      for (long long idx = t; idx < tot; idx += BT) {
-        const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
-        if (j > i) continue;
-        const double kb = Kb[idx];
-        if (j == i) {
-          ga = fma(kb, two_over_al * a2, ga);
-          gs = fma(kb, 2.0 * sig, gs);
-          continue;
+      const int warp = t >> 5, lane = t & 31;
+      for (int i = warp; i < n; i += BT / 32) {
+        const double *xi = Xg + (long long)i * d;
+        const double *Kbi = Kb + (long long)i * ld;
+        const double *Kpi = Kp + packed(i, 0);
+        for (int j = lane; j <= i; j += 32) {
+          const double kb = Kbi[j];
+          if (j == i) {
+            ga = fma(kb, two_over_al * a2, ga);
+            gs = fma(kb, 2.0 * sig, gs);
+            continue;
+          }
+          double r2 = 0.0;
+          for (int q2 = 0; q2 < d; ++q2) {
+            const double df = xi[q2] - Xg[(long long)j * d + q2];
+            r2 = fma(df, df, r2);
+          }
+          const double kf = Kpi[j];
+          ga = fma(kb, two_over_al * kf, ga);
+          gr = fma(kb, kf * r2 * ir3, gr);
         }
-        double r2 = 0.0;
-        for (int q2 = 0; q2 < d; ++q2) {
-          const double df = Xg[(long long)i * d + q2] - Xg[(long long)j * d + q2];
-          r2 = fma(df, df, r2);
-        }
-        const double kf = Kp[packed(i, j)];
-        ga = fma(kb, two_over_al * kf, ga);
-        gr = fma(kb, kf * r2 * ir3, gr);
       }
       ga = cta_sum(ga, sm);
       gr = cta_sum(gr, sm);
