@@ -745,16 +745,17 @@ __device__ double cta_residual(int n, const double *Kp, const double *y, const d
   return cta_sum(rr, sm);
 }
 
-// Workspace slot of one CTA (doubles): Kbar (nmax^2) | kernel values, packed
-// lower (nmax (nmax + 1) / 2) | z, alpha, r (3 nmax) | block inverses
+// Workspace slot of one CTA (doubles): Kbar (nmax^2) | kernel values k_ij,
+// packed lower (nmax (nmax + 1) / 2) | k_ij r_ij^2, packed the same way | z,
+// alpha, r (3 nmax) | block inverses
 // ((nmax + MAXB) MAXB) | M and T of the diagonal adjoint step (2 MAXB^2);
 // the mixed path adds slice buffers (BF16): L^T (5 nmax kp), a row-split
 // panel (5 nmax 64) and the adjoint's block column (5 64 kp), kp = nmax
 // rounded up to the chunk.
 __host__ __device__ inline long long slot_kp_offset(long long nmax) { return nmax * nmax; }
-__host__ __device__ inline long long slot_vec_offset(long long nmax) {
-  return slot_kp_offset(nmax) + (nmax * (nmax + 1) / 2 + 1) / 2 * 2;
-}
+__host__ __device__ inline long long packed_elems(long long nmax) { return (nmax * (nmax + 1) / 2 + 1) / 2 * 2; }
+__host__ __device__ inline long long slot_kr_offset(long long nmax) { return slot_kp_offset(nmax) + packed_elems(nmax); }
+__host__ __device__ inline long long slot_vec_offset(long long nmax) { return slot_kr_offset(nmax) + packed_elems(nmax); }
 __host__ __device__ inline long long slot_inv_offset(long long nmax) { return slot_vec_offset(nmax) + 3 * nmax; }
 __host__ __device__ inline long long slot_mt_offset(long long nmax) {
   return slot_inv_offset(nmax) + (nmax + MAXB) * MAXB;
@@ -789,6 +790,7 @@ batched_gp_kernel(BatchParams p) {
   const int nb = p.nb, nmax = p.nmax;
   double *Kb = slot;
   double *Kp = slot + slot_kp_offset(nmax);
+  double *Kr = slot + slot_kr_offset(nmax);
   double *z = slot + slot_vec_offset(nmax);
   double *alpha = z + nmax;
   double *rv = alpha + nmax;
@@ -829,7 +831,8 @@ batched_gp_kernel(BatchParams p) {
       info[1] = GPC_OK;
     }
     // ---- covariance: L gets the lower triangle (zero upper), Kp the kernel
-    // values packed; a warp per row, lanes along the row
+    // values and Kr the products k_ij r_ij^2 (both packed, for the gradient);
+    // a warp per row, lanes along the row
     {
       const double a2 = al * al, inv2r2 = 1.0 / (2.0 * rho * rho), dg = a2 + sig * sig;
       const int warp = t >> 5, lane = t & 31;
@@ -837,8 +840,9 @@ batched_gp_kernel(BatchParams p) {
         const double *xi = Xg + (long long)i * d;
         double *Li = L + (long long)i * ld;
         double *Kpi = Kp + packed(i, 0);
+        double *Kri = Kr + packed(i, 0);
         for (int j = lane; j <= i; j += 32) {
-          double v = dg;
+          double v = dg, kr = 0.0;
           if (j < i) {
             double r2 = 0.0;
             for (int q = 0; q < d; ++q) {
@@ -846,9 +850,11 @@ batched_gp_kernel(BatchParams p) {
               r2 = fma(df, df, r2);
             }
             v = a2 * exp(-r2 * inv2r2);
+            kr = v * r2;
           }
           Li[j] = v;
           Kpi[j] = v;
+          Kri[j] = kr;
         }
         for (int j = i + 1 + lane; j < n; j += 32) Li[j] = 0.0;
       }
@@ -1003,35 +1009,34 @@ batched_gp_kernel(BatchParams p) {
       }
       __syncthreads();
     }
-    // ---- hyperparameter gradient from Kbar and the kept kernel values
+    // ---- hyperparameter gradient from Kbar and the kept kernel values:
+    // dk_ij/dalpha = 2 k_ij / alpha (k_ii without the noise), dk_ij/drho =
+    // k_ij r_ij^2 / rho^3, dk_ii/dsigma = 2 sigma; the constant factors are
+    // applied to the sums
     {
-      const double a2 = al * al, two_over_al = 2.0 / al, ir3 = 1.0 / (rho * rho * rho);
-      double ga = 0.0, gr = 0.0, gs = 0.0;
+      const double a2 = al * al;
+      double sk = 0.0, skr = 0.0, sd = 0.0;  // sum kb k (off-diagonal), sum kb k r^2, sum of the diagonal kb
       const int warp = t >> 5, lane = t & 31;
       for (int i = warp; i < n; i += BT / 32) {
-        const double *xi = Xg + (long long)i * d;
         const double *Kbi = Kb + (long long)i * ld;
         const double *Kpi = Kp + packed(i, 0);
+        const double *Kri = Kr + packed(i, 0);
         for (int j = lane; j <= i; j += 32) {
           const double kb = Kbi[j];
           if (j == i) {
-            ga = fma(kb, two_over_al * a2, ga);
-            gs = fma(kb, 2.0 * sig, gs);
-            continue;
+            sd += kb;
+          } else {
+            sk = fma(kb, Kpi[j], sk);
+            skr = fma(kb, Kri[j], skr);
           }
-          double r2 = 0.0;
-          for (int q2 = 0; q2 < d; ++q2) {
-            const double df = xi[q2] - Xg[(long long)j * d + q2];
-            r2 = fma(df, df, r2);
-          }
-          const double kf = Kpi[j];
-          ga = fma(kb, two_over_al * kf, ga);
-          gr = fma(kb, kf * r2 * ir3, gr);
         }
       }
-      ga = cta_sum(ga, sm);
-      gr = cta_sum(gr, sm);
-      gs = cta_sum(gs, sm);
+      sk = cta_sum(sk, sm);
+      skr = cta_sum(skr, sm);
+      sd = cta_sum(sd, sm);
+      const double ga = 2.0 * (sk + sd * a2) / al;
+      const double gr = skr / (rho * rho * rho);
+      const double gs = 2.0 * sig * sd;
       if (t == 0) {
         p.grad3[3 * gi] = ga;
         p.grad3[3 * gi + 1] = gr;
