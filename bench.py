@@ -554,12 +554,19 @@ def main():
     tuned = {}
     if not args.no_autotune:
         from paper_1907_01063_gb300 import autotune
-        tuned["fp64_block"] = autotune.tune_fp64_block()["best"]
+        # timed at the workload's own order: the best FP64 block moves with n
+        tuned["fp64_block"] = autotune.tune_fp64_block(autotune.n_bucket(n))["best"]
         if "mixed" in precisions:
             rec = autotune.tune_mixed(n)
             tuned["mixed_schedule"] = dict(rec["best"], timed_at_n=rec["n"],
                                            product_k_tile=128 * rec["best"]["mixed_defer"])
             tuned["mixed_schedule_ms"] = rec["ms"]
+        # the tuned schedule may need a larger workspace (the group depths enter its size)
+        need = gp.workspace_size(n, "mixed" if "mixed" in precisions else "fp64")
+        if ws.numel() < need:
+            del ws
+            torch.cuda.empty_cache()
+            ws = gp.workspace(n, "mixed" if "mixed" in precisions else "fp64", dev)
 
     results = {p_: run(p_) for p_ in precisions}
 

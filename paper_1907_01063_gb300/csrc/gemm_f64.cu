@@ -9,7 +9,8 @@
 // with far fewer instructions and shared-memory operand reads than DFMA.
 //
 // Tile: 64 x 64 per CTA, K step 16, 4 warps in a 2 x 2 grid, 32 x 32 per warp
-// (2 x 4 m16n8 fragments).  Operands are staged through shared memory with a
+// (2 x 4 m16n8 fragments); single products of at most 256 x 256 take 32 x 32
+// tiles instead (16 x 16 per warp), so that they spread over the part.  Operands are staged through shared memory with a
 // register prefetch of the next K step; FP64 throughput on this part is low
 // enough that one stage of prefetch hides global latency completely.
 // Triangular outputs launch only the lower tiles; thin-output / long-K
@@ -22,7 +23,7 @@
 namespace gpc {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, PAD = 4, THREADS = 128;
+constexpr int BK = 16, PAD = 4, THREADS = 128;
 constexpr size_t kScratchCap = size_t(40) << 20;  // split-K partial tiles, bytes
 
 struct Params {
@@ -56,76 +57,82 @@ __device__ __forceinline__ void dmma16816(double (&c)[4], const double (&a)[8], 
         "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
 }
 
-// Global -> registers for one K step.  Each thread holds 8 A and 8 B values.
-template <bool TA, bool TB>
+// Global -> registers for one K step of a T x T tile.  Each thread holds V A
+// and V B values (V = 8 for T = 64, 4 for T = 32).
+template <int T, bool TA, bool TB>
 __device__ __forceinline__ void load_tiles(const Params &p, int m0, int n0, int k0, int kend,
-                                           double (&ra)[8], double (&rb)[8]) {
+                                           double (&ra)[T * BK / THREADS], double (&rb)[T * BK / THREADS]) {
+  constexpr int V = T * BK / THREADS, RK = BK / V, RM = T / V;  // threads per K row / per operand row
   const int t = threadIdx.x;
   const double *A = p.A + (long long)blockIdx.y * p.sA, *B = p.B + (long long)blockIdx.y * p.sB;
-  if (!TA) {  // A[m][k]: 2 threads per row, 8 consecutive k each
-    const int r = t >> 1, c0 = (t & 1) * 8, m = m0 + r;
+  if (!TA) {  // A[m][k]: RK threads per row, V consecutive k each
+    const int r = t / RK, c0 = (t % RK) * V, m = m0 + r;
     const double *src = A + (long long)m * p.lda;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < V; ++i) {
       const int k = k0 + c0 + i;
       ra[i] = (m < p.M && k < kend) ? src[k] : 0.0;
     }
-  } else {  // A[k][m]: 8 threads per k-row, 8 consecutive m each
-    const int kk = t >> 3, mm0 = (t & 7) * 8, k = k0 + kk;
+  } else {  // A[k][m]: RM threads per k-row, V consecutive m each
+    const int kk = t / RM, mm0 = (t % RM) * V, k = k0 + kk;
     const double *src = A + (long long)k * p.lda;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < V; ++i) {
       const int m = m0 + mm0 + i;
       ra[i] = (m < p.M && k < kend) ? src[m] : 0.0;
     }
   }
   if (!TB) {  // B[k][n]
-    const int kk = t >> 3, nn0 = (t & 7) * 8, k = k0 + kk;
+    const int kk = t / RM, nn0 = (t % RM) * V, k = k0 + kk;
     const double *src = B + (long long)k * p.ldb;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < V; ++i) {
       const int n = n0 + nn0 + i;
       rb[i] = (n < p.N && k < kend) ? src[n] : 0.0;
     }
   } else {  // B[n][k]
-    const int r = t >> 1, c0 = (t & 1) * 8, n = n0 + r;
+    const int r = t / RK, c0 = (t % RK) * V, n = n0 + r;
     const double *src = B + (long long)n * p.ldb;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < V; ++i) {
       const int k = k0 + c0 + i;
       rb[i] = (n < p.N && k < kend) ? src[k] : 0.0;
     }
   }
 }
 
-template <bool TA, bool TB>
+template <int T, bool TA, bool TB>
 __device__ __forceinline__ void store_tiles(double (*As)[BK + PAD], double (*Bs)[BK + PAD],
-                                            const double (&ra)[8], const double (&rb)[8]) {
+                                            const double (&ra)[T * BK / THREADS], const double (&rb)[T * BK / THREADS]) {
+  constexpr int V = T * BK / THREADS, RK = BK / V, RM = T / V;
   const int t = threadIdx.x;
   if (!TA) {
-    const int r = t >> 1, c0 = (t & 1) * 8;
+    const int r = t / RK, c0 = (t % RK) * V;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) As[r][c0 + i] = ra[i];
+    for (int i = 0; i < V; ++i) As[r][c0 + i] = ra[i];
   } else {
-    const int kk = t >> 3, mm0 = (t & 7) * 8;
+    const int kk = t / RM, mm0 = (t % RM) * V;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) As[mm0 + i][kk] = ra[i];
+    for (int i = 0; i < V; ++i) As[mm0 + i][kk] = ra[i];
   }
   if (!TB) {
-    const int kk = t >> 3, nn0 = (t & 7) * 8;
+    const int kk = t / RM, nn0 = (t % RM) * V;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) Bs[nn0 + i][kk] = rb[i];
+    for (int i = 0; i < V; ++i) Bs[nn0 + i][kk] = rb[i];
   } else {
-    const int r = t >> 1, c0 = (t & 1) * 8;
+    const int r = t / RK, c0 = (t % RK) * V;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) Bs[r][c0 + i] = rb[i];
+    for (int i = 0; i < V; ++i) Bs[r][c0 + i] = rb[i];
   }
 }
 
-template <bool TA, bool TB>
+// T x T output tile per CTA (T = 64, or 32 for products too small to fill the
+// part with 64-wide tiles); 4 warps in a 2 x 2 grid, (T/2) x (T/2) per warp.
+template <int T, bool TA, bool TB>
 __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
-  __shared__ double As[2][BM][BK + PAD];
-  __shared__ double Bs[2][BN][BK + PAD];
+  constexpr int V = T * BK / THREADS, MI = T / 32, NI = T / 16;
+  __shared__ double As[2][T][BK + PAD];
+  __shared__ double Bs[2][T][BK + PAD];
 
   int tm, tn;
   if (p.uplo != UPLO_FULL) {
@@ -134,10 +141,10 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
     tm = blockIdx.x / p.tiles_n;
     tn = blockIdx.x - tm * p.tiles_n;
   }
-  const int m0 = tm * BM, n0 = tn * BN;
-  // a skipped leading K range is a multiple of BM = BN, so kbeg stays on a K step
+  const int m0 = tm * T, n0 = tn * T;
+  // a skipped leading K range is a multiple of T, so kbeg stays on a K step
   const int kfirst = p.kskip == KSKIP_ROWS ? m0 : (p.kskip == KSKIP_COLS ? n0 : 0);
-  const int klast = p.kskip == KSKIP_ROWS_END ? m0 + BM : (p.kskip == KSKIP_COLS_END ? n0 + BN : p.K);
+  const int klast = p.kskip == KSKIP_ROWS_END ? m0 + T : (p.kskip == KSKIP_COLS_END ? n0 + T : p.K);
   const int kbeg = max((int)blockIdx.z * p.kchunk, kfirst);
   const int kend = min(min(p.K, klast), (int)blockIdx.z * p.kchunk + p.kchunk);
 
@@ -145,43 +152,43 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
   const int wm = warp >> 1, wn = warp & 1;
   const int g = lane >> 2, tg = lane & 3;
 
-  double acc[2][4][4];
+  double acc[MI][NI][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < MI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < NI; ++j)
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0;
 
-  double ra[8], rb[8];
+  double ra[V], rb[V];
   int buf = 0;
   if (kbeg < kend) {
-    load_tiles<TA, TB>(p, m0, n0, kbeg, kend, ra, rb);
-    store_tiles<TA, TB>(As[0], Bs[0], ra, rb);
+    load_tiles<T, TA, TB>(p, m0, n0, kbeg, kend, ra, rb);
+    store_tiles<T, TA, TB>(As[0], Bs[0], ra, rb);
   }
   __syncthreads();
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
     const bool more = k0 + BK < kend;
-    if (more) load_tiles<TA, TB>(p, m0, n0, k0 + BK, kend, ra, rb);
-    double a[2][8], b[4][4];
+    if (more) load_tiles<T, TA, TB>(p, m0, n0, k0 + BK, kend, ra, rb);
+    double a[MI][8], b[NI][4];
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
-      const int r = wm * 32 + mi * 16 + g;
+    for (int mi = 0; mi < MI; ++mi) {
+      const int r = wm * (T / 2) + mi * 16 + g;
 #pragma unroll
       for (int i = 0; i < 8; ++i) a[mi][i] = As[buf][r + 8 * (i & 1)][tg + 4 * (i >> 1)];
     }
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni) {
-      const int c = wn * 32 + ni * 8 + g;
+    for (int ni = 0; ni < NI; ++ni) {
+      const int c = wn * (T / 2) + ni * 8 + g;
 #pragma unroll
       for (int i = 0; i < 4; ++i) b[ni][i] = Bs[buf][c][tg + 4 * i];
     }
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+    for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
-      for (int ni = 0; ni < 4; ++ni) dmma16816(acc[mi][ni], a[mi], b[ni]);
+      for (int ni = 0; ni < NI; ++ni) dmma16816(acc[mi][ni], a[mi], b[ni]);
     if (more) {
-      store_tiles<TA, TB>(As[buf ^ 1], Bs[buf ^ 1], ra, rb);
+      store_tiles<T, TA, TB>(As[buf ^ 1], Bs[buf ^ 1], ra, rb);
       __syncthreads();
       buf ^= 1;
     }
@@ -192,13 +199,13 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
   const bool split = p.partial != nullptr;
   double *part = split ? p.partial + (size_t)blockIdx.z * p.M * p.N : nullptr;
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
+    for (int ni = 0; ni < NI; ++ni)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int row = m0 + wm * 32 + mi * 16 + g + ((r >> 1) << 3);
-        const int col = n0 + wn * 32 + ni * 8 + 2 * tg + (r & 1);
+        const int row = m0 + wm * (T / 2) + mi * 16 + g + ((r >> 1) << 3);
+        const int col = n0 + wn * (T / 2) + ni * 8 + 2 * tg + (r & 1);
         if (row >= p.M || col >= p.N) continue;
         const double v = p.alpha * acc[mi][ni][r];
         if (split) {
@@ -253,14 +260,19 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   p.sA = g.sA;
   p.sB = g.sB;
   p.sC = g.sC;
-  const int tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
+  // 64-wide tiles, or 32-wide ones for a single small product that 64-wide
+  // tiles and split K could not spread over the part (the symbolic steps of
+  // the adjoint, 128 x 128 x 128: 16 CTAs with 64-wide tiles, 128 with 32-wide)
+  const bool small = g.batch == 1 && g.M <= 256 && g.N <= 256 && scratch != nullptr;
+  const int T = small ? 32 : 64;
+  const int tm = (g.M + T - 1) / T, tn = (g.N + T - 1) / T;
   p.tiles_n = tn;
   const long long tiles = (g.uplo != UPLO_FULL) ? (long long)tm * (tm + 1) / 2 : (long long)tm * tn;
 
   // Split K when the output alone cannot fill the machine.
   int splits = 1;
   const long long target = 3LL * sm_count();  // three CTAs fit per SM
-  const int kmin = std::max(tuning().splitk_min, BK);
+  const int kmin = small ? BK : std::max(tuning().splitk_min, BK);
   if (scratch && g.batch == 1 && tiles < target && p.K >= 2 * kmin) {
     long long want = (target + tiles - 1) / tiles;
     want = std::min<long long>(want, p.K / kmin);
@@ -281,12 +293,21 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   const double flops = g.algo_flops > 0.0 ? g.algo_flops : 2.0 * mn * (double)p.K * g.batch;
   const double bytes =
       8.0 * g.batch * ((double)g.M * p.K + (double)p.K * g.N + (g.beta != 0.0 ? 2.0 : 1.0) * mn);
-  GPC_LAUNCH(GPC_TRACE_GEMM_F64, flops, bytes, s, {
-    if (!g.transA && !g.transB) gemm_f64_kernel<false, false><<<grid, THREADS, 0, s>>>(p);
-    else if (!g.transA && g.transB) gemm_f64_kernel<false, true><<<grid, THREADS, 0, s>>>(p);
-    else if (g.transA && !g.transB) gemm_f64_kernel<true, false><<<grid, THREADS, 0, s>>>(p);
-    else gemm_f64_kernel<true, true><<<grid, THREADS, 0, s>>>(p);
-  });
+  if (small) {
+    GPC_LAUNCH(GPC_TRACE_GEMM_F64, flops, bytes, s, {
+      if (!g.transA && !g.transB) gemm_f64_kernel<32, false, false><<<grid, THREADS, 0, s>>>(p);
+      else if (!g.transA && g.transB) gemm_f64_kernel<32, false, true><<<grid, THREADS, 0, s>>>(p);
+      else if (g.transA && !g.transB) gemm_f64_kernel<32, true, false><<<grid, THREADS, 0, s>>>(p);
+      else gemm_f64_kernel<32, true, true><<<grid, THREADS, 0, s>>>(p);
+    });
+  } else {
+    GPC_LAUNCH(GPC_TRACE_GEMM_F64, flops, bytes, s, {
+      if (!g.transA && !g.transB) gemm_f64_kernel<64, false, false><<<grid, THREADS, 0, s>>>(p);
+      else if (!g.transA && g.transB) gemm_f64_kernel<64, false, true><<<grid, THREADS, 0, s>>>(p);
+      else if (g.transA && !g.transB) gemm_f64_kernel<64, true, false><<<grid, THREADS, 0, s>>>(p);
+      else gemm_f64_kernel<64, true, true><<<grid, THREADS, 0, s>>>(p);
+    });
+  }
   if (splits > 1) {
     const long long total = (long long)g.M * g.N;
     GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (splits + 2) * mn, s,
