@@ -554,8 +554,13 @@ def main():
     tuned = {}
     if not args.no_autotune:
         from paper_1907_01063_gb300 import autotune
-        # timed at the workload's own order: the best FP64 block moves with n
-        tuned["fp64_block"] = autotune.tune_fp64_block(autotune.n_bucket(n))["best"]
+        # FP64 schedule (block size, split-K minimum, small-product tile limit),
+        # timed on chol + adjoint at the workload's order capped at 8192 (one
+        # FP64 pass at 16384 takes seconds); the choice is applied
+        rec64 = autotune.tune_fp64(min(n, 8192))
+        tuned["fp64_block"] = rec64["best"]["fp64_block"]
+        tuned["fp64_schedule"] = dict(rec64["best"], timed_at_n=rec64["n"])
+        tuned["fp64_schedule_ms"] = rec64["ms"]
         if "mixed" in precisions:
             rec = autotune.tune_mixed(n)
             tuned["mixed_schedule"] = dict(rec["best"], timed_at_n=rec["n"],

@@ -123,6 +123,11 @@ int gpc_workspace_size(int n, int precision, size_t *bytes);
 #define GPC_TUNE_MIXED_PRIORITY 7
 /* Mixed adjoint: SMs its background products leave to the chain (0..64, default 16). */
 #define GPC_TUNE_MIXED_ADJ_FREE_SMS 8
+/* FP64 products (GEMM, factorisation and adjoint pieces): a single product
+ * whose M and N are both at most this value takes 32 x 32 output tiles
+ * instead of 64 x 64, so that it spreads over the part (0 = always 64 x 64;
+ * 0..4096, default 256). */
+#define GPC_TUNE_F64_SMALL_TILE 9
 int gpc_set_tuning(int key, int value);
 int gpc_get_tuning(int key, int *value);
 

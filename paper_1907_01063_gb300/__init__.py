@@ -39,6 +39,7 @@ GPC_TUNE_MIXED_FREE_SMS = 5
 GPC_TUNE_MIXED_CTA_ITEMS = 6
 GPC_TUNE_MIXED_PRIORITY = 7
 GPC_TUNE_MIXED_ADJ_FREE_SMS = 8
+GPC_TUNE_F64_SMALL_TILE = 9
 
 PRECISIONS = {"fp64": GPC_FP64, "mixed": GPC_MIXED, GPC_FP64: GPC_FP64, GPC_MIXED: GPC_MIXED}
 

@@ -21,7 +21,9 @@ Knobs:
     exponent group) stays 128.
   * the FP64 schedule (tune_fp64): the block size above together with the
     minimum K per split of the split-K products (the K tile of a partial
-    product: 32, 64, 128).
+    product: 32, 64, 128) and the output tile of the FP64 products (single
+    products up to a size limit take 32 x 32 tiles, the rest 64 x 64; the
+    limit is searched over 256, 0 (always 64 x 64), 128 and 512).
 Schedules with several knobs are searched coordinate by coordinate
 (coordinate_search): each knob in turn over its candidates with the others
 held at their best so far.  Cache keys carry the device, the precision and the
@@ -170,10 +172,11 @@ def coordinate_search(knobs, measure, start=None) -> dict:
 
 _MIXED_KNOBS = [("mixed_defer", (6, 1, 2, 4, 8)), ("mixed_free_sms", (2, 4, 8)),
                 ("mixed_adj_free_sms", (16, 8, 24))]
-_FP64_KNOBS = [("fp64_block", (128, 64, 96)), ("splitk_min", (32, 64, 128))]
+_FP64_KNOBS = [("fp64_block", (128, 64, 96)), ("splitk_min", (32, 64, 128)),
+               ("f64_small_tile", (256, 0, 128, 512))]
 _KNOB_IDS = {"mixed_defer": gp.GPC_TUNE_MIXED_DEFER, "mixed_free_sms": gp.GPC_TUNE_MIXED_FREE_SMS,
              "mixed_adj_free_sms": gp.GPC_TUNE_MIXED_ADJ_FREE_SMS, "fp64_block": gp.GPC_TUNE_BLOCK,
-             "splitk_min": gp.GPC_TUNE_SPLITK_MIN}
+             "splitk_min": gp.GPC_TUNE_SPLITK_MIN, "f64_small_tile": gp.GPC_TUNE_F64_SMALL_TILE}
 
 
 def _apply(cfg: dict):

@@ -153,6 +153,10 @@ int gpc_set_tuning(int key, int value) {
       if (value < 0 || value > 64) return GPC_ERR_INVALID_ARG;
       tuning().mixed_adj_free_sms = value;
       return GPC_OK;
+    case GPC_TUNE_F64_SMALL_TILE:
+      if (value < 0 || value > 4096) return GPC_ERR_INVALID_ARG;
+      tuning().f64_small_tile = value;
+      return GPC_OK;
     default:
       return GPC_ERR_INVALID_ARG;
   }
@@ -170,6 +174,7 @@ int gpc_get_tuning(int key, int *value) {
     case GPC_TUNE_MIXED_CTA_ITEMS: *value = tuning().mixed_cta_items; return GPC_OK;
     case GPC_TUNE_MIXED_PRIORITY: *value = tuning().mixed_priority; return GPC_OK;
     case GPC_TUNE_MIXED_ADJ_FREE_SMS: *value = tuning().mixed_adj_free_sms; return GPC_OK;
+    case GPC_TUNE_F64_SMALL_TILE: *value = tuning().f64_small_tile; return GPC_OK;
     default: return GPC_ERR_INVALID_ARG;
   }
 }

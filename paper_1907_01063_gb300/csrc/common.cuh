@@ -21,6 +21,7 @@ struct Tuning {
   int mixed_defer = 6;    // mixed path: block columns whose trailing updates are merged (K = 128 x this)
   int mixed_free_sms = 2; // mixed factorisation: SMs the background products leave to the FP64 chain
   int mixed_adj_free_sms = 16;  // mixed adjoint: the same
+  int f64_small_tile = 256;  // FP64 products with M, N <= this take 32 x 32 tiles (0: never)
   int mixed_cta_items = 0;  // mixed path: work items per CTA of a background product (0: persistent)
   int mixed_priority = 1;   // mixed path: launch the critical chain at the device's greatest priority
 };

@@ -260,25 +260,35 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   p.sA = g.sA;
   p.sB = g.sB;
   p.sC = g.sC;
-  // 64-wide tiles, or 32-wide ones for a single small product that 64-wide
-  // tiles and split K could not spread over the part (the symbolic steps of
-  // the adjoint, 128 x 128 x 128: 16 CTAs with 64-wide tiles, 128 with 32-wide)
-  const bool small = g.batch == 1 && g.M <= 256 && g.N <= 256 && scratch != nullptr;
+  // 64-wide tiles; a single product that 64-wide tiles and split K cannot
+  // spread over every SM takes 32-wide tiles and K steps down to 16 (the
+  // symbolic steps of the adjoint, 128 x 128 x 128: 16 CTAs with 64-wide
+  // tiles, 128 with 32-wide).  A long-K product of the same output (split
+  // K reaches every SM) keeps 64-wide tiles, which read fewer operands per
+  // DMMA.  The size limit is a tuning knob (0: never 32-wide).
+  const long long target = 3LL * sm_count();  // three CTAs fit per SM
+  const long long cap_splits = (long long)(kScratchCap / (sizeof(double) * (size_t)g.M * g.N));
+  auto tile_count = [&](int T) {
+    const long long tm_ = (g.M + T - 1) / T, tn_ = (g.N + T - 1) / T;
+    return (g.uplo != UPLO_FULL) ? tm_ * (tm_ + 1) / 2 : tm_ * tn_;
+  };
+  auto max_splits = [&](int kmin) {
+    return std::max<long long>(1, std::min<long long>(std::min<long long>(64, p.K / kmin), cap_splits));
+  };
+  const int kmin64 = std::max(tuning().splitk_min, BK);
+  const int small_max = tuning().f64_small_tile;
+  const bool small = g.batch == 1 && scratch != nullptr && g.M <= small_max && g.N <= small_max &&
+                     tile_count(64) * max_splits(kmin64) < sm_count();
   const int T = small ? 32 : 64;
-  const int tm = (g.M + T - 1) / T, tn = (g.N + T - 1) / T;
-  p.tiles_n = tn;
-  const long long tiles = (g.uplo != UPLO_FULL) ? (long long)tm * (tm + 1) / 2 : (long long)tm * tn;
+  p.tiles_n = (g.N + T - 1) / T;
+  const long long tiles = tile_count(T);
 
   // Split K when the output alone cannot fill the machine.
   int splits = 1;
-  const long long target = 3LL * sm_count();  // three CTAs fit per SM
-  const int kmin = small ? BK : std::max(tuning().splitk_min, BK);
+  const int kmin = small ? BK : kmin64;
   if (scratch && g.batch == 1 && tiles < target && p.K >= 2 * kmin) {
     long long want = (target + tiles - 1) / tiles;
-    want = std::min<long long>(want, p.K / kmin);
-    want = std::min<long long>(want, 64);
-    const long long cap = (long long)(kScratchCap / (sizeof(double) * (size_t)g.M * g.N));
-    want = std::min(want, cap);
+    want = std::min(want, max_splits(kmin));
     splits = (int)std::max<long long>(want, 1);
   }
   int kchunk = (p.K + splits - 1) / splits;

@@ -177,7 +177,8 @@ def test_error_word_and_fault_knobs_host_checks():
 
 def test_mixed_schedule_knobs_roundtrip_and_validation():
     knobs = {gp.GPC_TUNE_MIXED_DEFER: ((1, 8), (0, 9)), gp.GPC_TUNE_MIXED_FREE_SMS: ((0, 32), (-1, 33)),
-             gp.GPC_TUNE_MIXED_CTA_ITEMS: ((0, 1024), (-1, 1025)), gp.GPC_TUNE_MIXED_PRIORITY: ((0, 1), (-1, 2))}
+             gp.GPC_TUNE_MIXED_CTA_ITEMS: ((0, 1024), (-1, 1025)), gp.GPC_TUNE_MIXED_PRIORITY: ((0, 1), (-1, 2)),
+             gp.GPC_TUNE_F64_SMALL_TILE: ((0, 4096), (-1, 4097))}
     for key, (good, bad) in knobs.items():
         old = gp.get_tuning(key)
         try:

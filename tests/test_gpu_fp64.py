@@ -65,6 +65,27 @@ def test_chol_block_sizes(block):
         gp.set_tuning(gp.GPC_TUNE_BLOCK, old)
 
 
+@pytest.mark.parametrize("tile_limit", [0, 256, 4096])
+def test_small_product_tile_limit(tile_limit):
+    # The FP64 products take 32 x 32 output tiles up to a tuned size limit
+    # (0: never, 4096: every product of this size); the factor, the adjoint
+    # and a plain GEMM must match the oracle with either tile.
+    old = gp.get_tuning(gp.GPC_TUNE_F64_SMALL_TILE)
+    try:
+        gp.set_tuning(gp.GPC_TUNE_F64_SMALL_TILE, tile_limit)
+        _, K = se_problem(451, seed=6)
+        L = gp.chol(dev(K)).cpu().numpy()
+        assert rel(L, O.chol(K)) <= TOL
+        Lbar = W.random_lower(451, seed=7)
+        G = gp.chol_adjoint(dev(L), dev(Lbar)).cpu().numpy()
+        assert rel(G, O.chol_adjoint(L, Lbar)) <= TOL
+        A = W.gp_inputs(97, 203, seed=8)
+        B = W.gp_inputs(203, 45, seed=9)
+        assert rel(gp.gemm(dev(A), dev(B)).cpu().numpy(), O.gemm(A, B)) <= 1e-12
+    finally:
+        gp.set_tuning(gp.GPC_TUNE_F64_SMALL_TILE, old)
+
+
 def test_chol_in_place_padded_ld_and_upper_ignored():
     n = 250
     _, K = se_problem(n, seed=5)
