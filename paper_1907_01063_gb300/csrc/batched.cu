@@ -384,21 +384,6 @@ __device__ __forceinline__ void df_acc4(float &hi, float &lo, float g2, float g3
   lo = __fsub_rn(e, __fsub_rn(hi, s));
 }
 
-// FP32 -> FP64 by moving the fields (exact for every normal value and zero),
-// which keeps the conversion off the FP64 unit; subnormals, Inf and NaN take
-// the conversion instruction.
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) {
-    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);
-    return (double)f;
-  }
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)d);
-}
-
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                "l"(src), "r"(src_bytes)
@@ -543,7 +528,7 @@ __device__ __noinline__ void tile_gemm_sl(const SliceOp &A, const SliceOp &B, do
         const int row = m0 + frag_row(wm, mi) + g + ((r >> 1) << 3);
         const int col = n0 + frag_col(wn, ni) + 2 * tg + (r & 1);
         if (row >= M || col >= N || (lower && col > row)) continue;
-        const double v = f32_to_f64(hi[mi][ni][r]) + f32_to_f64(lo[mi][ni][r]);  // exact
+        const double v = exact_f64(hi[mi][ni][r]) + exact_f64(lo[mi][ni][r]);  // exact
         C[(long long)row * ldc + col] = cv[mi][ni][r] - v;
       }
 }

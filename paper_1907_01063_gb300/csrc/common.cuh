@@ -61,6 +61,52 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// ---------------------------------------------------------------- double-float conversions
+// On this part the FP64 pipe (which also runs the FP32 <-> FP64 conversion
+// instructions) is a small fraction of the integer and FP32 rates, so the
+// conversions between FP64 and double-float storage (an FP32 pair hi + lo)
+// move the fields with integer instructions where the result is exact.
+
+// FP32 -> FP64, exact for every normal value and zero; subnormals, Inf and
+// NaN take the conversion instruction.
+__device__ __forceinline__ double exact_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);
+    return (double)f;
+  }
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// FP64 x -> (hi, lo): hi = x rounded to nearest FP32 (ties to even), lo = the
+// exact remainder x - hi rounded to nearest FP32 -- the same pair as
+// hi = (float)x, lo = (float)(x - (double)hi).  For 2^-74 <= |x| < 2^127 both
+// are normal FP32 numbers and the pair is formed from the fields: the 52-bit
+// mantissa splits into its top 23 bits (rounded on the 29 below) and the
+// signed remainder r (|r| <= 2^28, exact in an int), so lo = r 2^(E - 1075)
+// converts r with the integer-to-FP32 instruction and scales by a power of
+// two.  Other values take the FP64 conversions.
+__device__ __forceinline__ float2 split_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned E = (unsigned)(b >> 52) & 0x7FFu;
+  if (E >= 949u && E <= 1149u) {
+    const unsigned s = (unsigned)(b >> 63);
+    const unsigned m23 = (unsigned)((b >> 29) & 0x7FFFFFull);
+    const int rem = (int)(b & 0x1FFFFFFFull);  // the 29 bits below m23
+    const bool up = rem > 0x10000000 || (rem == 0x10000000 && (m23 & 1u));
+    const unsigned hb = (s << 31) | (((E - 896u) << 23) + m23 + (up ? 1u : 0u));
+    const int r = up ? rem - 0x20000000 : rem;   // x - hi in units of 2^(E - 1075)
+    const float lo = __fmul_rn(__int2float_rn(s ? -r : r), __uint_as_float((E - 948u) << 23));  // 2^(E - 1075)
+    return make_float2(__uint_as_float(hb), lo);
+  }
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+
 // ---------------------------------------------------------------- error word, symbols, test faults
 // Device address of a file-scope __device__ variable on the current device,
 // cached per device together with the context it was looked up in (a new

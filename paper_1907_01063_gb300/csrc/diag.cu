@@ -133,7 +133,7 @@ trtri_batched_kernel(int n, const double *L, long long ldl, int first, int b, do
 __device__ __forceinline__ double load_entry(const double *p, int df) {
   if (df) {
     const float2 v = *reinterpret_cast<const float2 *>(p);
-    return (double)v.x + (double)v.y;
+    return exact_f64(v.x) + exact_f64(v.y);
   }
   return *p;
 }

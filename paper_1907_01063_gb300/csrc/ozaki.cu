@@ -708,11 +708,7 @@ __global__ void to_df_lower_kernel(int n, const double *src, long long lds, floa
   if (idx >= (long long)n * n) return;
   const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
   float2 v = make_float2(0.f, 0.f);
-  if (j <= i) {
-    const double x = src[(long long)i * lds + j];
-    const float hi = __double2float_rn(x);
-    v = make_float2(hi, __double2float_rn(x - (double)hi));
-  }
+  if (j <= i) v = split_f64(src[(long long)i * lds + j]);
   dst[(long long)i * ldd + j] = v;
 }
 
@@ -722,7 +718,7 @@ __global__ void from_df_rect_kernel(int m, int c, double *p, long long ld) {
   const int i = (int)(idx / c), j = (int)(idx - (long long)i * c);
   double *q = p + (long long)i * ld + j;
   const float2 v = *(const float2 *)q;
-  *q = (double)v.x + (double)v.y;
+  *q = exact_f64(v.x) + exact_f64(v.y);
 }
 
 __global__ void df_reduce_kernel(int M, int N, int splits, const float2 *partial, float2 *C, long long ldc,
