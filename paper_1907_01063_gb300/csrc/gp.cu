@@ -97,7 +97,13 @@ se_cov_df_kernel(int n, int d, const double *X, long long ldx, double a2, dfa::d
       if (t.hi <= 80.0f) {
         int k;
         const dfa::df m = dfa::exp_neg(t, k);
-        v = dfa::to_double(m) * (a2 * dfa::pow2(k));
+        // (hi + lo) a2 2^k: the conversions and the power of two by field
+        // moves (exact), one FP64 add and one multiply
+        const int ea = (int)((unsigned long long)__double_as_longlong(a2) >> 52) & 0x7FF;
+        const double a2k = (ea > 116 && ea < 2047)  // a2 and a2 2^k normal (k >= -116)
+                               ? __longlong_as_double(__double_as_longlong(a2) + ((long long)k << 52))
+                               : a2 * dfa::pow2(k);
+        v = (exact_f64(m.hi) + exact_f64(m.lo)) * a2k;
       } else {
         v = a2 * exp(-dfa::to_double(t));
       }
@@ -190,7 +196,8 @@ se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alp
     if (i >= n || j >= n || j > i) continue;
     const double kb = Kbar[(long long)i * ldkb + j];
     if (i == j) {
-      se = dfa::add(se, dfa::from_double(kb));  // e_ii = 1, r2_ii = 0
+      const float2 kd = split_f64(kb);
+      se = dfa::add(se, dfa::df{kd.x, kd.y});  // e_ii = 1, r2_ii = 0
       gs = fma(kb, 2.0 * sigma, gs);
       continue;
     }
@@ -201,7 +208,8 @@ se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alp
       const dfa::df m = dfa::exp_neg(t, k);
       const float sc = __int_as_float((k + 127) << 23);  // 2^k, k >= -116
       const dfa::df e = {m.hi * sc, m.lo * sc};
-      const dfa::df w = dfa::mul(dfa::from_double(kb), e);
+      const float2 kd = split_f64(kb);
+      const dfa::df w = dfa::mul(dfa::df{kd.x, kd.y}, e);
       se = dfa::add(se, w);
       ser = dfa::add(ser, dfa::mul(w, r2));
     } else {
