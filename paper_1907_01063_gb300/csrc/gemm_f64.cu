@@ -101,8 +101,13 @@ __device__ __forceinline__ void load_tiles(const Params &p, int m0, int n0, int 
   }
 }
 
+// Row padding of the operand stages: 4 doubles for 64-wide tiles, 2 for
+// 32-wide ones (9 KB per stage pair, room to spare beside a product CTA).
+template <int T>
+constexpr int tile_pad() { return T == 64 ? PAD : 2; }
+
 template <int T, bool TA, bool TB>
-__device__ __forceinline__ void store_tiles(double (*As)[BK + PAD], double (*Bs)[BK + PAD],
+__device__ __forceinline__ void store_tiles(double (*As)[BK + tile_pad<T>()], double (*Bs)[BK + tile_pad<T>()],
                                             const double (&ra)[T * BK / THREADS], const double (&rb)[T * BK / THREADS]) {
   constexpr int V = T * BK / THREADS, RK = BK / V, RM = T / V;
   const int t = threadIdx.x;
@@ -128,11 +133,15 @@ __device__ __forceinline__ void store_tiles(double (*As)[BK + PAD], double (*Bs)
 
 // T x T output tile per CTA (T = 64, or 32 for products too small to fill the
 // part with 64-wide tiles); 4 warps in a 2 x 2 grid, (T/2) x (T/2) per warp.
+// T = 64 double-buffers its operand stage; T = 32 keeps one stage (9 KB of
+// shared memory), so that a CTA fits beside a split-product CTA on the same
+// SM (which leaves about 11 KB free): the small products of the adjoint's
+// chain then use every SM while a product runs in the background.
 template <int T, bool TA, bool TB>
 __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
-  constexpr int V = T * BK / THREADS, MI = T / 32, NI = T / 16;
-  __shared__ double As[2][T][BK + PAD];
-  __shared__ double Bs[2][T][BK + PAD];
+  constexpr int V = T * BK / THREADS, MI = T / 32, NI = T / 16, NS = (T == 64) ? 2 : 1;
+  __shared__ double As[NS][T][BK + tile_pad<T>()];
+  __shared__ double Bs[NS][T][BK + tile_pad<T>()];
 
   int tm, tn;
   if (p.uplo != UPLO_FULL) {
@@ -161,15 +170,7 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
       for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0;
 
   double ra[V], rb[V];
-  int buf = 0;
-  if (kbeg < kend) {
-    load_tiles<T, TA, TB>(p, m0, n0, kbeg, kend, ra, rb);
-    store_tiles<T, TA, TB>(As[0], Bs[0], ra, rb);
-  }
-  __syncthreads();
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    const bool more = k0 + BK < kend;
-    if (more) load_tiles<T, TA, TB>(p, m0, n0, k0 + BK, kend, ra, rb);
+  auto compute = [&](int buf) {
     double a[MI][8], b[NI][4];
 #pragma unroll
     for (int mi = 0; mi < MI; ++mi) {
@@ -187,10 +188,32 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(Params p) {
     for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
       for (int ni = 0; ni < NI; ++ni) dmma16816(acc[mi][ni], a[mi], b[ni]);
-    if (more) {
-      store_tiles<T, TA, TB>(As[buf ^ 1], Bs[buf ^ 1], ra, rb);
+  };
+  if constexpr (NS == 2) {
+    int buf = 0;
+    if (kbeg < kend) {
+      load_tiles<T, TA, TB>(p, m0, n0, kbeg, kend, ra, rb);
+      store_tiles<T, TA, TB>(As[0], Bs[0], ra, rb);
+    }
+    __syncthreads();
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+      const bool more = k0 + BK < kend;
+      if (more) load_tiles<T, TA, TB>(p, m0, n0, k0 + BK, kend, ra, rb);
+      compute(buf);
+      if (more) {
+        store_tiles<T, TA, TB>(As[buf ^ 1], Bs[buf ^ 1], ra, rb);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  } else {  // one stage: the next K step waits in registers while this one is computed
+    if (kbeg < kend) load_tiles<T, TA, TB>(p, m0, n0, kbeg, kend, ra, rb);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+      __syncthreads();  // the previous step's reads of the stage are done
+      store_tiles<T, TA, TB>(As[0], Bs[0], ra, rb);
       __syncthreads();
-      buf ^= 1;
+      if (k0 + BK < kend) load_tiles<T, TA, TB>(p, m0, n0, k0 + BK, kend, ra, rb);
+      compute(0);
     }
   }
 
@@ -238,6 +261,26 @@ __global__ void splitk_reduce_kernel(Params p, int splits) {
 }  // namespace
 
 size_t gemm_f64_scratch_bytes() { return kScratchCap; }
+
+namespace {
+// The 32-wide instantiations share SMs with split-product CTAs only when they
+// run in the same (maximal) shared-memory configuration.
+bool g_small_carveout[64];
+cudaError_t small_tile_carveout() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaSuccess;
+  if (g_small_carveout[dev]) return cudaSuccess;
+  const void *fns[] = {(const void *)gemm_f64_kernel<32, false, false>, (const void *)gemm_f64_kernel<32, false, true>,
+                       (const void *)gemm_f64_kernel<32, true, false>, (const void *)gemm_f64_kernel<32, true, true>};
+  for (const void *f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  g_small_carveout[dev] = true;
+  return cudaSuccess;
+}
+}  // namespace
 
 cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
@@ -304,6 +347,7 @@ cudaError_t gemm_f64(const Gemm &g, double *scratch, cudaStream_t s) {
   const double bytes =
       8.0 * g.batch * ((double)g.M * p.K + (double)p.K * g.N + (g.beta != 0.0 ? 2.0 : 1.0) * mn);
   if (small) {
+    if (cudaError_t ce = small_tile_carveout(); ce != cudaSuccess) return ce;
     GPC_LAUNCH(GPC_TRACE_GEMM_F64, flops, bytes, s, {
       if (!g.transA && !g.transB) gemm_f64_kernel<32, false, false><<<grid, THREADS, 0, s>>>(p);
       else if (!g.transA && g.transB) gemm_f64_kernel<32, false, true><<<grid, THREADS, 0, s>>>(p);

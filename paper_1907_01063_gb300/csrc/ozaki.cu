@@ -650,30 +650,36 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 // covers k in [0, first), chunk c >= 1 covers [first + 128 (c - 1), + 128).
 // Output planes: dst[p * plane + r * kpad + c * 128 + kk] (BF16), zero where
 // the operand has no element; rows r >= row_end are not written.  Grid:
-// (chunks, ceil(row_end / 32)), 256 threads.
+// (chunks, ceil(row_end / SPLIT_ROWS)), 256 threads, one row per warp.  The
+// 8-row tile (8 KB of shared memory) lets a CTA run beside a product CTA on
+// the same SM (which leaves about 11 KB free), so the splits of the chain do
+// not wait for SMs while a product runs in the background.
+constexpr int SPLIT_ROWS = 8;
 __global__ void __launch_bounds__(256)
 split_kernel(const double *src, long long rs, long long ks, int M, int K, int first, __nv_bfloat16 *dst,
              long long plane, int kpad, int row_end) {
-  __shared__ double tile[32][129];
-  const int c = blockIdx.x, r0 = blockIdx.y * 32;
+  __shared__ double tile[SPLIT_ROWS][129];
+  const int c = blockIdx.x, r0 = blockIdx.y * SPLIT_ROWS;
   const int kbeg = (c == 0) ? 0 : first + (c - 1) * OZ_CHUNK;
   const int klen = (c == 0) ? min(first, K) : min(OZ_CHUNK, K - kbeg);
   if (ks == 1) {
-    for (int idx = threadIdx.x; idx < 32 * 128; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < SPLIT_ROWS * 128; idx += blockDim.x) {
       const int rr = idx >> 7, kk = idx & 127;
       const int r = r0 + rr;
       tile[rr][kk] = (r < M && kk < klen) ? src[(long long)r * rs + (kbeg + kk)] : 0.0;
     }
   } else {
-    for (int idx = threadIdx.x; idx < 32 * 128; idx += blockDim.x) {
-      const int kk = idx >> 5, rr = idx & 31;
+    for (int idx = threadIdx.x; idx < SPLIT_ROWS * 128; idx += blockDim.x) {
+      const int kk = idx / SPLIT_ROWS, rr = idx % SPLIT_ROWS;
       const int r = r0 + rr;
       tile[rr][kk] = (r < M && kk < klen) ? src[(long long)r * rs + (long long)(kbeg + kk) * ks] : 0.0;
     }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int rr = warp * 4; rr < warp * 4 + 4; ++rr) {
+  static_assert(SPLIT_ROWS == 8, "one row per warp of 256 threads");
+  {
+    const int rr = warp;
     unsigned long long bits[4];
     int ex = 0;
 #pragma unroll
@@ -691,7 +697,7 @@ split_kernel(const double *src, long long rs, long long ks, int M, int K, int fi
       for (int pp = 0; pp < OZ_S; ++pp) out[pp][i] = __bfloat16_as_ushort(__float2bfloat16_rn(v[pp]));
     }
     const int r = r0 + rr;
-    if (r >= row_end) continue;
+    if (r >= row_end) return;  // past the last barrier
 #pragma unroll
     for (int pp = 0; pp < OZ_S; ++pp) {
       uint2 pack;
@@ -786,7 +792,16 @@ cudaError_t split_operand(const double *src, long long rs, long long ks, int M, 
   if (chunks <= 0 || row_offset < 0 || row_offset + M > out.rows_pad) return cudaErrorInvalidValue;
   // rows written: the operand's M rows (at row_offset), or every row of the buffer when row_offset == 0
   const int row_end = row_offset > 0 ? M : out.rows_pad;
-  dim3 grid((unsigned)chunks, (unsigned)((row_end + 31) / 32));
+  static bool carveout_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !carveout_set[dev]) {  // the same shared-memory configuration as the products
+    cudaError_t e = cudaFuncSetAttribute(split_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    carveout_set[dev] = true;
+  }
+  dim3 grid((unsigned)chunks, (unsigned)((row_end + SPLIT_ROWS - 1) / SPLIT_ROWS));
   const long long plane = (long long)out.rows_pad * out.kpad;
   GPC_LAUNCH(GPC_TRACE_SPLIT, 0.0, 8.0 * M * K + 2.0 * OZ_S * (double)row_end * chunks * OZ_CHUNK, s,
              launch_k(split_kernel, grid, 256, 0, s, src, rs, ks, M, K, first,
