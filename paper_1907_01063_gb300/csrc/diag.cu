@@ -305,61 +305,65 @@ trsm_rows_kernel(int m, int nb, double *X, long long ldx, const double *T, long 
   }
 }
 
-// The same panel solve with four threads per row and no block barriers, for
-// the block sizes the factorisations use (NB = 64 or 128).  Thread t of a row
-// holds columns k = 4c + t (c < NB / 4) in registers; at step j the owner of
-// column j (final by then) passes it to the row's other three threads with a
-// warp shuffle, every thread updates its columns still to be solved, and the
-// owner of the next column scales it.  Columns are dealt round-robin so the
-// shrinking work stays balanced; the loops are unrolled at compile time so the
-// row stays in registers.  The FP64 pipe, not synchronisation, bounds it.
-constexpr int TQ_THREADS = 64;  // 16 rows per CTA: enough CTAs that every SM gets an even share
-template <int NB, int MODE>
+// The same panel solve with TPR threads per row (4, or 16 for short panels)
+// and no block barriers, for the block sizes the factorisations use (NB = 64
+// or 128).  Thread t of a row holds columns k = TPR c + t (c < NB / TPR) in
+// registers; at step j the owner of column j (final by then) passes it to the
+// row's other threads with a warp shuffle, every thread updates its columns
+// still to be solved, and the owner of the next column scales it.  Columns
+// are dealt round-robin so the shrinking work stays balanced; the loops are
+// unrolled at compile time so the row stays in registers.  The FP64 pipe, not
+// synchronisation, bounds it: one FP64 warp instruction holds a sub-partition's
+// FP64 unit for about 64 cycles, so a short panel (the 64 x 64 solve of a
+// diagonal block's halves) is spread over 16 threads per row and more warps.
+// Every element sees the same operations in the same order for any TPR.
+constexpr int TQ_THREADS = 64;  // 16 rows per CTA at TPR = 4: enough CTAs that every SM gets an even share
+template <int NB, int MODE, int TPR>
 __global__ void __launch_bounds__(TQ_THREADS)
 trsm_quad_kernel(int m, double *X, long long ldx, const double *T, long long ldt, int df) {
-  constexpr int C = NB / 4;
+  constexpr int C = NB / TPR;
   __shared__ double rdiag[NB];
   for (int k = threadIdx.x; k < NB; k += blockDim.x) rdiag[k] = 1.0 / __ldg(&T[(long long)k * ldt + k]);
   __syncthreads();
-  const int lane = threadIdx.x & 31, t = lane & 3, src0 = lane & ~3;
-  const int row = blockIdx.x * (TQ_THREADS / 4) + (threadIdx.x >> 2);
+  const int lane = threadIdx.x & 31, t = lane & (TPR - 1), src0 = lane & ~(TPR - 1);
+  const int row = blockIdx.x * (TQ_THREADS / TPR) + (threadIdx.x / TPR);
   const bool live = row < m;
   double *xr = X + (long long)(live ? row : 0) * ldx;
   double x[C];
 #pragma unroll
-  for (int c = 0; c < C; ++c) x[c] = live ? load_entry(xr + 4 * c + t, df) : 0.0;
+  for (int c = 0; c < C; ++c) x[c] = live ? load_entry(xr + TPR * c + t, df) : 0.0;
   if (MODE == 0) {  // X <- X T^{-T}: columns ascending, x_k -= x_j T[k][j] for k > j
     if (t == 0) x[0] *= rdiag[0];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      const double xj = __shfl_sync(0xffffffffu, x[j >> 2], src0 | (j & 3));
+      const double xj = __shfl_sync(0xffffffffu, x[j / TPR], src0 | (j % TPR));
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        if (4 * c + 3 <= j) continue;  // every column of this group is already final
-        const int k = 4 * c + t;
+        if (TPR * c + TPR - 1 <= j) continue;  // every column of this group is already final
+        const int k = TPR * c + t;
         const double tv = __ldg(&T[(long long)k * ldt + j]);
-        if (4 * c > j || k > j) x[c] = fma(-xj, tv, x[c]);
+        if (TPR * c > j || k > j) x[c] = fma(-xj, tv, x[c]);
       }
-      if (j + 1 < NB && t == ((j + 1) & 3)) x[(j + 1) >> 2] *= rdiag[j + 1];
+      if (j + 1 < NB && t == ((j + 1) % TPR)) x[(j + 1) / TPR] *= rdiag[j + 1];
     }
   } else {  // X <- X T^{-1}: columns descending, x_k -= x_j T[j][k] for k < j
-    if (t == ((NB - 1) & 3)) x[C - 1] *= rdiag[NB - 1];
+    if (t == ((NB - 1) % TPR)) x[C - 1] *= rdiag[NB - 1];
 #pragma unroll
     for (int j = NB - 1; j >= 0; --j) {
-      const double xj = __shfl_sync(0xffffffffu, x[j >> 2], src0 | (j & 3));
+      const double xj = __shfl_sync(0xffffffffu, x[j / TPR], src0 | (j % TPR));
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        if (4 * c >= j) continue;  // every column of this group is at or past j
-        const int k = 4 * c + t;
+        if (TPR * c >= j) continue;  // every column of this group is at or past j
+        const int k = TPR * c + t;
         const double tv = __ldg(&T[(long long)j * ldt + k]);
-        if (4 * c + 3 < j || k < j) x[c] = fma(-xj, tv, x[c]);
+        if (TPR * c + TPR - 1 < j || k < j) x[c] = fma(-xj, tv, x[c]);
       }
-      if (j > 0 && t == ((j - 1) & 3)) x[(j - 1) >> 2] *= rdiag[j - 1];
+      if (j > 0 && t == ((j - 1) % TPR)) x[(j - 1) / TPR] *= rdiag[j - 1];
     }
   }
   if (live) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) xr[4 * c + t] = x[c];
+    for (int c = 0; c < C; ++c) xr[TPR * c + t] = x[c];
   }
 }
 
@@ -657,8 +661,10 @@ cudaError_t trsm_carveout() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaSuccess;
   if (g_trsm_carveout[dev]) return cudaSuccess;
-  const void *fns[] = {(const void *)trsm_quad_kernel<64, 0>, (const void *)trsm_quad_kernel<64, 1>,
-                       (const void *)trsm_quad_kernel<128, 0>, (const void *)trsm_quad_kernel<128, 1>,
+  const void *fns[] = {(const void *)trsm_quad_kernel<64, 0, 4>, (const void *)trsm_quad_kernel<64, 1, 4>,
+                       (const void *)trsm_quad_kernel<128, 0, 4>, (const void *)trsm_quad_kernel<128, 1, 4>,
+                       (const void *)trsm_quad_kernel<64, 0, 16>, (const void *)trsm_quad_kernel<64, 1, 16>,
+                       (const void *)trsm_quad_kernel<128, 0, 16>, (const void *)trsm_quad_kernel<128, 1, 16>,
                        (const void *)trsm_rows_kernel<8>, (const void *)trsm_rows_kernel<16>,
                        (const void *)trsm_rows_kernel<32>};
   for (const void *f : fns) {
@@ -676,16 +682,27 @@ cudaError_t trsm_rows(int m, int nb, double *X, long long ldx, const double *T, 
   if (nb > kMaxBlock) return cudaErrorInvalidValue;
   if (cudaError_t ce = trsm_carveout(); ce != cudaSuccess) return ce;
   const double fl = (double)m * nb * nb, by = 16.0 * (double)m * nb + 4.0 * nb * nb;
-  const unsigned qgrid = (unsigned)((m + TQ_THREADS / 4 - 1) / (TQ_THREADS / 4));
   if (nb == 64 || nb == 128) {
-    if (nb == 64 && mode == 0)
-      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, launch_k(trsm_quad_kernel<64, 0>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df));
-    else if (nb == 64)
-      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, launch_k(trsm_quad_kernel<64, 1>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df));
-    else if (mode == 0)
-      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, launch_k(trsm_quad_kernel<128, 0>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df));
-    else
-      GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s, launch_k(trsm_quad_kernel<128, 1>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df));
+    // short panels (at most 256 rows): 16 threads per row, so the row's FP64
+    // work is spread over four times as many warps
+    const bool short_panel = m <= 256;
+    const int tpr = short_panel ? 16 : 4;
+    const unsigned qgrid = (unsigned)((m + TQ_THREADS / tpr - 1) / (TQ_THREADS / tpr));
+#define GPC_TRSM_QUAD(NB_, MODE_, TPR_)                                                                      \
+  GPC_LAUNCH(GPC_TRACE_TRSM, fl, by, s,                                                                     \
+             launch_k(trsm_quad_kernel<NB_, MODE_, TPR_>, qgrid, TQ_THREADS, 0, s, m, X, ldx, T, ldt, df))
+    if (short_panel) {
+      if (nb == 64 && mode == 0) GPC_TRSM_QUAD(64, 0, 16);
+      else if (nb == 64) GPC_TRSM_QUAD(64, 1, 16);
+      else if (mode == 0) GPC_TRSM_QUAD(128, 0, 16);
+      else GPC_TRSM_QUAD(128, 1, 16);
+    } else {
+      if (nb == 64 && mode == 0) GPC_TRSM_QUAD(64, 0, 4);
+      else if (nb == 64) GPC_TRSM_QUAD(64, 1, 4);
+      else if (mode == 0) GPC_TRSM_QUAD(128, 0, 4);
+      else GPC_TRSM_QUAD(128, 1, 4);
+    }
+#undef GPC_TRSM_QUAD
     return cudaGetLastError();
   }
   // other block sizes: 32 rows per CTA when that still gives two CTAs per SM, else 16 or 8
