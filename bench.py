@@ -19,6 +19,8 @@ The same JSON line also carries:
   * the batched workload: 512 GPs per GPU, one persistent launch, dealt to the ranks by n^3;
   * `tri`: the triangular inverse and the triangular solve's reverse mode at the same n;
   * `gemm_glm`: the FP64 GEMM and its reverse mode, and the fused Bernoulli-logit GLM likelihood;
+  * `mixed_product_alone`: the split-BF16 tcgen05 product by itself at K = 128, 768 and 1024
+    (the kernel's own fraction of the sustained BF16 peak, beside the step-averaged `roofline`);
   * the oracle (`cpu_baseline`) and the multi-core CPU baseline (`cpu_parallel_baseline`) on a
     leading block of the workload;
   * `fp64_vs_oracle` and `mixed_vs_oracle`: each path's L, Kbar, alpha, log det, LML and
@@ -79,6 +81,8 @@ def parse_args():
     p.add_argument("--tri-m", type=int, default=1024, help="right-hand-side columns of the solve-adjoint leg")
     p.add_argument("--tri-reps", type=int, default=2)
     p.add_argument("--no-gemm-glm", action="store_true", help="skip the GEMM and GLM legs")
+    p.add_argument("--no-product-alone", action="store_true",
+                   help="skip timing the split-BF16 product by itself")
     p.add_argument("--glm-n", type=int, default=1 << 20)
     p.add_argument("--glm-k", type=int, default=512)
     return p.parse_args()
@@ -696,6 +700,41 @@ def main():
 
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+
+    def run_product_isolated():
+        """The split-BF16 tcgen05 product alone (no other kernel running), on an
+        8192 x 8192 double-float output at three K depths: K = 128 reads and
+        writes the output once per 128-wide chunk (the depth of the adjoint's
+        B-bar updates), K = 768 is the factorisation's deferred depth.  Kernel
+        time from the library's per-launch events; flops 30 M N K (15 slice
+        products per FP64 multiply-add)."""
+        g = torch.Generator(device=dev)
+        g.manual_seed(11)
+        out = {}
+        sust = peaks.get("bf16_tflops_sustained")
+        burst = peaks.get("bf16_tflops")
+        for kk in (128, 768, 1024):
+            A = torch.randn(8192, kk, generator=g, dtype=torch.float64, device=dev)
+            B = torch.randn(8192, kk, generator=g, dtype=torch.float64, device=dev)
+            gp.test_ozaki_gemm(A, B)
+            torch.cuda.synchronize()
+            gp.trace_enable(True)
+            for _ in range(3):
+                gp.test_ozaki_gemm(A, B)
+            torch.cuda.synchronize()
+            tr = gp.trace_summary()["gemm_mixed"]
+            gp.trace_enable(False)
+            tf = tr["flops"] / (tr["ms"] * 1e-3) / 1e12
+            out[f"8192x8192xK{kk}"] = {"kernel_ms": tr["ms"] / tr["launches"], "tflops": tf,
+                                         "frac_of_burst_bf16": tf / burst if burst else None,
+                                         "frac_of_sustained_bf16": tf / sust if sust else None}
+            del A, B
+        out["peak_source"] = "of measured: bf16_tflops (burst) and bf16_tflops_sustained"
+        return out
+
+    product_alone = None
+    if "mixed" in precisions and not args.no_product_alone and rank == 0:
+        product_alone = run_product_isolated()
     extra = None
     if not args.no_gemm_glm:
         torch.cuda.nvtx.range_push("gemm_glm")
@@ -809,6 +848,8 @@ def main():
             gl["frac_of_fp64_peak"] = gl["fp64_gflops"] / fp64_peak
             gl["bound"] = "alu (FP64)"
         line["gemm_glm"] = extra
+    if product_alone is not None:
+        line["mixed_product_alone"] = product_alone
     if tri is not None:
         for leg in ("inverse", "solve_adjoint"):
             tri[leg]["frac_of_fp64_peak"] = tri[leg]["gflops"] / fp64_peak
