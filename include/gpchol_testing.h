@@ -40,6 +40,18 @@ int gpc_test_ozaki_gemm(int M, int N, int K, const double *A, const double *B, d
 int gpc_test_recip_rsqrt(int n, const double *x, double *out, gpc_stream_t stream);
 
 /*
+ * The FP64 -> double-float conversion of the mixed path (the split of every
+ * FP64 matrix entry into an FP32 pair, formed from the bit fields without
+ * the conversion instructions) and its inverse, on the n device doubles x:
+ *   hilo[2 i] = hi_i, hilo[2 i + 1] = lo_i, meant to equal hi = (float)x_i
+ *   and lo = (float)(x_i - (double)hi) with round-to-nearest-even;
+ *   back[i] = (double)hi_i + (double)lo_i formed by the exact FP32 -> FP64
+ *   field move.
+ * hilo: 2 n device floats; back: n device doubles.
+ */
+int gpc_test_split_f64(int n, const double *x, float *hilo, double *back, gpc_stream_t stream);
+
+/*
  * Fault injection for the tests of the bounded device waits.  These knobs
  * change what later launches do (process-wide, host-side; not thread-safe):
  *   GPC_TEST_WAIT_NS         budget of every bounded wait of the solve and

@@ -51,6 +51,7 @@ _SIGNATURES = {
     "gpc_get_error": ([ctypes.POINTER(_c_int), _c_int, _c_vp], _c_int),
     "gpc_test_set_fault": ([_c_int, ctypes.c_longlong], _c_int),
     "gpc_test_recip_rsqrt": ([_c_int, _c_vp, _c_vp, _c_vp], _c_int),
+    "gpc_test_split_f64": ([_c_int, _c_vp, _c_vp, _c_vp, _c_vp], _c_int),
     "gpc_version": ([], _c_int),
     "gpc_workspace_size": ([_c_int, _c_int, ctypes.POINTER(_c_size)], _c_int),
     "gpc_set_tuning": ([_c_int, _c_int], _c_int),

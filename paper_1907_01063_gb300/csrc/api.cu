@@ -436,11 +436,31 @@ int gpc_gp_lml(int n, const double *K, int ldk, const double *y, double *L, int 
   const double *inv = (const double *)w.core;
   const int b = chol_block_size(precision);
   if (e == cudaSuccess) e = cudaMemcpyAsync(alpha, y, n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
-  if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, alpha, 0, w.flags, info, stream);
-  if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, alpha, 1, w.flags, info, stream);
-  if (precision == GPC_MIXED && e == cudaSuccess)
-    e = refine(n, K, ldk, L, ldl, inv, b, y, alpha, w.refine, w.flags, info, kRefineMaxIters, kRefineTol,
-               stream);
+  if (precision == GPC_MIXED) {
+    // The mixed path solves in double-float: its factor's own error is far
+    // larger, and the FP64 refinement against K removes both.  L's lower
+    // triangle is converted once into the workspace core behind the block
+    // inverses (free after the factorisation); the solved sub-blocks pass
+    // through w.vec.
+    const size_t inv_bytes = align_up((size_t)((n + b - 1) / b) * b * b * sizeof(double), 256);
+    const bool room = core_bytes(n, precision) >= inv_bytes + (size_t)n * n * sizeof(float2);
+    float2 *Ld = room ? (float2 *)((char *)w.core + inv_bytes) : nullptr;
+    float2 *xdf = (float2 *)w.vec;
+    if (Ld) {
+      if (e == cudaSuccess) e = to_df_tri(n, L, ldl, Ld, n, stream);
+      if (e == cudaSuccess) e = trsv_inv_df(n, Ld, n, inv, b, alpha, xdf, 0, w.flags, info, stream);
+      if (e == cudaSuccess) e = trsv_inv_df(n, Ld, n, inv, b, alpha, xdf, 1, w.flags, info, stream);
+    } else {
+      if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, alpha, 0, w.flags, info, stream);
+      if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, alpha, 1, w.flags, info, stream);
+    }
+    if (e == cudaSuccess)
+      e = refine(n, K, ldk, L, ldl, inv, b, y, alpha, w.refine, w.flags, info, kRefineMaxIters, kRefineTol,
+                 stream, Ld, n, xdf);
+  } else {
+    if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, alpha, 0, w.flags, info, stream);
+    if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, alpha, 1, w.flags, info, stream);
+  }
   if (e == cudaSuccess) e = lml_finalize(n, L, ldl, y, alpha, logdet, value, stream);
   return status_of(e);
 }

@@ -81,14 +81,25 @@ __device__ __forceinline__ double exact_f64(float f) {
   return __longlong_as_double((long long)d);
 }
 
+// Signed integer |v| <= 2^28 -> nearest FP32 without the integer-to-float
+// instruction (which issues on the FP64 pipe on this part): v = a 2^14 + b with
+// a = v >> 14 and b = v & (2^14 - 1) each exact in FP32 by the exponent-field
+// trick (2^23 + b and 1.5 * 2^23 + a are FP32 numbers whose low mantissa bits
+// hold b and a), then one FMA rounds a 2^14 + b once.
+__device__ __forceinline__ float int29_to_float_rn(int v) {
+  const float a = __fsub_rn(__int_as_float(0x4B400000 + (v >> 14)), 12582912.0f);
+  const float b = __fsub_rn(__int_as_float(0x4B000000 | (v & 0x3FFF)), 8388608.0f);
+  return __fmaf_rn(a, 16384.0f, b);
+}
+
 // FP64 x -> (hi, lo): hi = x rounded to nearest FP32 (ties to even), lo = the
 // exact remainder x - hi rounded to nearest FP32 -- the same pair as
 // hi = (float)x, lo = (float)(x - (double)hi).  For 2^-74 <= |x| < 2^127 both
 // are normal FP32 numbers and the pair is formed from the fields: the 52-bit
 // mantissa splits into its top 23 bits (rounded on the 29 below) and the
 // signed remainder r (|r| <= 2^28, exact in an int), so lo = r 2^(E - 1075)
-// converts r with the integer-to-FP32 instruction and scales by a power of
-// two.  Other values take the FP64 conversions.
+// rounds r to FP32 (int29_to_float_rn) and scales by a power of two.  Other
+// values take the FP64 conversions.
 __device__ __forceinline__ float2 split_f64(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned E = (unsigned)(b >> 52) & 0x7FFu;
@@ -99,7 +110,7 @@ __device__ __forceinline__ float2 split_f64(double x) {
     const bool up = rem > 0x10000000 || (rem == 0x10000000 && (m23 & 1u));
     const unsigned hb = (s << 31) | (((E - 896u) << 23) + m23 + (up ? 1u : 0u));
     const int r = up ? rem - 0x20000000 : rem;   // x - hi in units of 2^(E - 1075)
-    const float lo = __fmul_rn(__int2float_rn(s ? -r : r), __uint_as_float((E - 948u) << 23));  // 2^(E - 1075)
+    const float lo = __fmul_rn(int29_to_float_rn(s ? -r : r), __uint_as_float((E - 948u) << 23));  // 2^(E - 1075)
     return make_float2(__uint_as_float(hb), lo);
   }
   const float hi = __double2float_rn(x);
@@ -280,13 +291,25 @@ cudaError_t trsv(int n, const double *L, long long ldl, double *x, int trans, vo
 // r = y - K x, x += L^{-T} L^{-1} r, until |r| <= tol |y|, the residual stops
 // halving, or max_iters corrections; info[1] = GPC_ERR_NO_CONVERGENCE otherwise.
 size_t refine_workspace_bytes(int n);
+// With Ld (the lower triangle of L as FP32 pairs, leading dimension ldd) the
+// correction solves run in double-float (trsv_inv_df) through xdf.
 cudaError_t refine(int n, const double *K, long long ldk, const double *L, long long ldl, const double *inv,
                    int b, const double *y, double *x, void *ws, void *trsv_ws, int *info, int max_iters,
-                   double tol, cudaStream_t s);
+                   double tol, cudaStream_t s, const float2 *Ld = nullptr, long long ldd = 0,
+                   float2 *xdf = nullptr);
 // Blocked solve with stored diagonal-block inverses (blocks of b rows from the
 // top, inverse I at inv + I b^2); ws as for trsv.
 cudaError_t trsv_inv(int n, const double *L, long long ldl, const double *inv, int b, double *x, int trans,
                      void *ws, int *info, cudaStream_t s, const int *skip = nullptr);
+// The same solve in double-float arithmetic on Ld, the lower triangle of L as
+// FP32 pairs (hi, lo) with leading dimension ldd (to_df_tri); x is FP64 in and
+// out, xdf (n pairs, 8-byte aligned) is scratch through which the solved
+// sub-blocks pass.
+cudaError_t trsv_inv_df(int n, const float2 *Ld, long long ldd, const double *inv, int b, double *x,
+                        float2 *xdf, int trans, void *ws, int *info, cudaStream_t s, const int *skip = nullptr);
+// Lower triangle of the FP64 matrix src as FP32 pairs (hi, lo) into dst; the
+// strict upper triangle of dst is not written.
+cudaError_t to_df_tri(int n, const double *src, long long lds, float2 *dst, long long ldd, cudaStream_t s);
 // Block size the factorisation uses at a precision, and where it leaves its
 // diagonal-block inverses (start of the workspace core).
 int chol_block_size(int precision);

@@ -277,6 +277,28 @@ __device__ __forceinline__ bool wait_flag(const int *flag, int &value, unsigned 
   }
 }
 
+// The same wait with an acquire load: the block's other threads, released by
+// the barrier that follows, see everything the flag's writer published.
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool wait_flag_acquire(const int *flag, int &value, unsigned long long wait_ns) {
+  const unsigned long long t0 = clock_ns();
+  for (unsigned it = 0;; ++it) {
+    value = ld_acquire(flag);
+    if (value != 0) return true;
+    if ((it & 255) == 255 && clock_ns() - t0 > wait_ns) return false;
+    if (it > 1024) __nanosleep(32);
+  }
+}
+// Publish a flag after a barrier: the acquire-release fence makes the writes
+// of every thread of the block that reached the barrier visible before it.
+__device__ __forceinline__ void publish_flag(int *p, int v) {
+  asm volatile("fence.acq_rel.gpu;\n\tst.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // withhold >= 0 (test hook): the block with that index in solve order computes
 // its rows but never publishes its ready flag.
 __global__ void __launch_bounds__(256)
@@ -573,6 +595,234 @@ trsv_inv_kernel(int n, const double *L, long long ldl, const double *inv, int b,
   }
 }
 
+// The same blocked solve in double-float arithmetic, for the mixed path: its
+// initial solve and its refinement corrections.  There the factor's own error
+// (split-BF16 trailing updates) is far above the 2^-44 or so that a
+// double-float solve adds, and the FP64 residual of the refinement removes
+// both, so the correction solves need not run on the FP64 pipe, which on this
+// part issues about one warp instruction per 64 cycles per sub-partition.  L
+// is read from a copy already split into FP32 pairs (Ld: hi = nearest FP32,
+// lo = nearest FP32 to the remainder; one conversion pass per factor, reused
+// by every solve), the sub-block inverses are split as they are loaded.
+// Every product l x = (lh + ll)(xh + xl) keeps lh xh exactly (FMA
+// two-product) plus the cross terms lh xl + ll xh, and the sums are kept as a
+// running FP32 sum with its two-sum errors collected beside it (renormalised
+// every few sub-blocks).  Solved sub-blocks are published to the later ones
+// as FP32 pairs in xdf (n pairs, 8-byte aligned) behind an acquire/release
+// flag; x receives hi + lo in FP64.  Measured at n = 16384 (mixed factor):
+// forward 0.82 ms and transposed 0.74 ms against about 1.4-1.8 ms each for
+// the FP64 kernel; reading L as FP64 and splitting it in the loop left each
+// CTA's walk over the earlier sub-blocks instruction-bound (about 1000
+// instructions per warp and sub-block, 10-13 us per step).
+__device__ __forceinline__ void df_dot_term(float2 l, float2 v, float &S, float &E) {
+  const float ph = __fmul_rn(l.x, v.x);
+  float pl = __fmaf_rn(l.x, v.x, -ph);
+  pl = __fmaf_rn(l.x, v.y, pl);
+  pl = __fmaf_rn(l.y, v.x, pl);
+  const dfa::df t = dfa::two_sum(S, ph);
+  S = t.hi;
+  E = __fadd_rn(E, __fadd_rn(t.lo, pl));
+}
+
+__global__ void __launch_bounds__(256)
+trsv_inv_df_kernel(int n, const float2 *Ld, long long ldd, const double *inv, int b, int sb, double *x,
+                   float2 *xdf, int trans, int *sync, int *info, const int *skip, int *gerr,
+                   unsigned long long wait_ns) {
+  if (skip && *skip) return;
+  __shared__ float2 dinv_s[TS][TS + 1];
+  __shared__ int s_order, s_ab[2];
+  __shared__ float2 vbuf[TS], xs[TS];
+  __shared__ float2 red[TQ][TS];
+  const int nsb = (n + sb - 1) / sb;
+  if (threadIdx.x == 0) {
+    s_order = atomicAdd(&sync[0], 1);
+    s_ab[0] = s_ab[1] = 0;
+  }
+  __syncthreads();
+  const int order = s_order;
+  const int sbk = trans ? (nsb - 1 - order) : order;
+  const int i0 = sbk * sb, nb = min(sb, n - i0);
+  {
+    const int B = i0 / b, off = i0 - B * b, nbB = min(b, n - B * b);
+    const double *Dinv = inv + (size_t)B * b * b + (size_t)off * nbB + off;  // leading dimension nbB
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+      const int rr = idx / nb, kk = idx - rr * nb;
+      dinv_s[rr][kk] = split_f64(__ldg(Dinv + (size_t)rr * nbB + kk));
+    }
+  }
+  const int r = threadIdx.x % TS, q = threadIdx.x / TS;
+  bool aborted = false;
+  float S = 0.f, E = 0.f;
+  float2 lv[TW];
+  const float2 rhs = (q == 0 && r < nb) ? split_f64(x[i0 + r]) : make_float2(0.f, 0.f);
+  const float2 zero2 = make_float2(0.f, 0.f);
+
+  if (!trans) {
+    // Thread (column kk of the sub-block, row quarter rq) keeps one partial
+    // sum per row rq TW + rr over its column, so that a warp reads 32
+    // consecutive entries of a row of L; the 64 column partials of every row
+    // meet in shared memory after the last flag.
+    extern __shared__ float2 part[];  // [TS][TS + 1]
+    const int kk = threadIdx.x % TS, rq = threadIdx.x / TS;
+    float aS[TW], aE[TW];
+#pragma unroll
+    for (int rr = 0; rr < TW; ++rr) {
+      aS[rr] = aE[rr] = 0.f;
+      const int row = rq * TW + rr;
+      lv[rr] = (sbk > 0 && row < nb && kk < sb) ? __ldg(Ld + (long long)(i0 + row) * ldd + kk) : zero2;
+    }
+    for (int c = 0; c < sbk; ++c) {
+      if (threadIdx.x == 0) {
+        int f;
+        if (!wait_flag_acquire(&sync[1 + c], f, wait_ns) || f != 1) s_ab[c & 1] = 1;
+      }
+      __syncthreads();
+      if (s_ab[c & 1]) {
+        aborted = true;
+        break;
+      }
+      const int c0 = c * sb;  // c < sbk: a full sub-block
+      const float2 xk = kk < sb ? __ldcg(&xdf[c0 + kk]) : zero2;
+#pragma unroll
+      for (int rr = 0; rr < TW; ++rr) df_dot_term(lv[rr], xk, aS[rr], aE[rr]);
+      if ((c & 15) == 15) {
+#pragma unroll
+        for (int rr = 0; rr < TW; ++rr) {
+          const dfa::df t = dfa::two_sum(aS[rr], aE[rr]);
+          aS[rr] = t.hi;
+          aE[rr] = t.lo;
+        }
+      }
+      if (c + 1 < sbk) {
+        const int c1 = c0 + sb;
+#pragma unroll
+        for (int rr = 0; rr < TW; ++rr) {
+          const int row = rq * TW + rr;
+          lv[rr] = (row < nb && kk < sb) ? __ldg(Ld + (long long)(i0 + row) * ldd + c1 + kk) : zero2;
+        }
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < TW; ++rr) {
+      const dfa::df t = dfa::two_sum(aS[rr], aE[rr]);
+      part[(rq * TW + rr) * (TS + 1) + kk] = make_float2(t.hi, t.lo);
+    }
+    __syncthreads();
+    // thread (r, q): row r's partials of columns q TW .. q TW + TW - 1
+    float S1 = 0.f, E1 = 0.f;
+#pragma unroll
+    for (int u = 0; u < TW; u += 2) {
+      const float2 p0 = part[r * (TS + 1) + q * TW + u], p1 = part[r * (TS + 1) + q * TW + u + 1];
+      dfa::df t = dfa::two_sum(S, p0.x);
+      S = t.hi;
+      E = __fadd_rn(E, __fadd_rn(t.lo, p0.y));
+      t = dfa::two_sum(S1, p1.x);
+      S1 = t.hi;
+      E1 = __fadd_rn(E1, __fadd_rn(t.lo, p1.y));
+    }
+    const dfa::df t = dfa::two_sum(S, S1);
+    const dfa::df u2 = dfa::two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(E, E1)));
+    S = u2.hi;
+    E = u2.lo;
+  } else {
+    // thread (i = r, row quarter q): lv[u] = Ld[c0 + q TW + u][i0 + i] for the next sub-block c below
+    {
+      const int c0 = (nsb - 1) * sb, cn = n - c0;
+#pragma unroll
+      for (int u = 0; u < TW; ++u) {
+        const int k = q * TW + u;
+        lv[u] = (order > 0 && r < nb && k < cn) ? __ldg(Ld + (long long)(c0 + k) * ldd + i0 + r) : zero2;
+      }
+    }
+    for (int step = 0; step < order; ++step) {
+      const int c = nsb - 1 - step;
+      if (threadIdx.x == 0) {
+        int f;
+        if (!wait_flag_acquire(&sync[1 + c], f, wait_ns) || f != 1) s_ab[step & 1] = 1;
+      }
+      __syncthreads();
+      if (s_ab[step & 1]) {
+        aborted = true;
+        break;
+      }
+      const int c0 = c * sb, cn = min(sb, n - c0);
+      if (threadIdx.x < TS) xs[threadIdx.x] = threadIdx.x < cn ? __ldcg(&xdf[c0 + threadIdx.x]) : zero2;
+      __syncthreads();
+      float S1 = 0.f, E1 = 0.f;
+#pragma unroll
+      for (int u = 0; u < TW; u += 2) {
+        df_dot_term(lv[u], xs[q * TW + u], S, E);
+        df_dot_term(lv[u + 1], xs[q * TW + u + 1], S1, E1);
+      }
+      {
+        const dfa::df t = dfa::two_sum(S, S1);
+        const dfa::df u2 = dfa::two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(E, E1)));
+        S = u2.hi;
+        E = u2.lo;
+      }
+      if (step + 1 < order) {
+        const int p0 = c0 - sb;  // the next sub-block up is a full one
+#pragma unroll
+        for (int u = 0; u < TW; ++u) {
+          const int k = q * TW + u;
+          lv[u] = (r < nb && k < sb) ? __ldg(Ld + (long long)(p0 + k) * ldd + i0 + r) : zero2;
+        }
+      }
+    }
+  }
+  red[q][r] = make_float2(S, E);
+  __syncthreads();  // red and dinv_s complete
+  if (!aborted && q == 0 && r < nb) {
+    const dfa::df a = dfa::add(dfa::df{red[0][r].x, red[0][r].y}, dfa::df{red[1][r].x, red[1][r].y});
+    const dfa::df c = dfa::add(dfa::df{red[2][r].x, red[2][r].y}, dfa::df{red[3][r].x, red[3][r].y});
+    const dfa::df v = dfa::add(dfa::df{rhs.x, rhs.y}, dfa::neg(dfa::add(a, c)));
+    vbuf[r] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  S = 0.f;
+  E = 0.f;
+  if (!aborted && r < nb) {
+    float S1 = 0.f, E1 = 0.f;
+    if (!trans) {
+#pragma unroll
+      for (int u = 0; u < TW; u += 2) {
+        const int k = q * TW + u;
+        if (k <= r) df_dot_term(dinv_s[r][k], vbuf[k], S, E);
+        if (k + 1 <= r) df_dot_term(dinv_s[r][k + 1], vbuf[k + 1], S1, E1);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < TW; u += 2) {
+        const int k = q * TW + u;
+        if (k >= r && k < nb) df_dot_term(dinv_s[k][r], vbuf[k], S, E);
+        if (k + 1 >= r && k + 1 < nb) df_dot_term(dinv_s[k + 1][r], vbuf[k + 1], S1, E1);
+      }
+    }
+    const dfa::df t = dfa::two_sum(S, S1);
+    S = t.hi;
+    E = __fadd_rn(t.lo, __fadd_rn(E, E1));
+  }
+  red[q][r] = make_float2(S, E);
+  __syncthreads();
+  if (!aborted && q == 0 && r < nb) {
+    const dfa::df a = dfa::add(dfa::df{red[0][r].x, red[0][r].y}, dfa::df{red[1][r].x, red[1][r].y});
+    const dfa::df c = dfa::add(dfa::df{red[2][r].x, red[2][r].y}, dfa::df{red[3][r].x, red[3][r].y});
+    const dfa::df v = dfa::add(a, c);
+    xdf[i0 + r] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (aborted && info && info[1] == 0) info[1] = GPC_ERR_TIMEOUT;
+    if (aborted) record_error(gerr, GPC_ERR_TIMEOUT);
+    publish_flag(&sync[1 + sbk], aborted ? 2 : 1);
+  }
+  // the FP64 result after the flag: nothing in this launch reads x of another sub-block
+  if (!aborted && q == 0 && r < nb) {
+    const float2 v = xdf[i0 + r];
+    x[i0 + r] = exact_f64(v.x) + exact_f64(v.y);
+  }
+}
+
 // ---------------------------------------------------------------- likelihood pieces
 __global__ void __launch_bounds__(256)
 lml_finalize_kernel(int n, const double *L, long long ldl, const double *y, const double *alpha,
@@ -696,7 +946,7 @@ lml_lbar_kernel(int n, const double *L, long long ldl, const double *alpha, cons
   }
 }
 
-bool g_attr[64][4];
+bool g_attr[64][5];
 
 cudaError_t set_dyn_smem(const void *fn, int which) {
   int dev = 0;
@@ -800,6 +1050,25 @@ cudaError_t trsv_inv(int n, const double *L, long long ldl, const double *inv, i
   GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n + 2.0 * n * b, 4.0 * (double)n * (n + 1) + 8.0 * n * b, s,
              trsv_inv_kernel<<<nsb, 256, 0, s>>>(n, L, ldl, inv, b, sb, x, trans ? 1 : 0, sync, info, skip,
                                                  error_word(), faults().wait_ns));
+  return cudaGetLastError();
+}
+
+cudaError_t trsv_inv_df(int n, const float2 *Ld, long long ldd, const double *inv, int b, double *x,
+                        float2 *xdf, int trans, void *ws, int *info, cudaStream_t s, const int *skip) {
+  if (n <= 0) return cudaSuccess;
+  if (b < 1 || b > 2 * TS || !Ld || !xdf || ((uintptr_t)xdf & 7u) || ((uintptr_t)Ld & 7u))
+    return cudaErrorInvalidValue;
+  const int sb = b > TS ? (b + 1) / 2 : b;
+  if (sb > TS || (b > TS && 2 * sb != b)) return cudaErrorInvalidValue;
+  const int nsb = (n + sb - 1) / sb;
+  int *sync = (int *)ws;
+  cudaError_t e = set_dyn_smem((const void *)trsv_inv_df_kernel, 4);  // the forward solve's row partials
+  if (e == cudaSuccess) e = cudaMemsetAsync(sync, 0, (size_t)(nsb + 1) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const size_t dyn = trans ? 0 : (size_t)TS * (TS + 1) * sizeof(float2);
+  GPC_LAUNCH(GPC_TRACE_TRSV, (double)n * n + 2.0 * n * b, 4.0 * (double)n * (n + 1) + 8.0 * n * b, s,
+             trsv_inv_df_kernel<<<nsb, 256, dyn, s>>>(n, Ld, ldd, inv, b, sb, x, xdf, trans ? 1 : 0, sync, info,
+                                                      skip, error_word(), faults().wait_ns));
   return cudaGetLastError();
 }
 
@@ -923,7 +1192,7 @@ size_t refine_workspace_bytes(int n) {
 
 cudaError_t refine(int n, const double *K, long long ldk, const double *L, long long ldl, const double *inv,
                    int b, const double *y, double *x, void *ws, void *trsv_ws, int *info, int max_iters,
-                   double tol, cudaStream_t s) {
+                   double tol, cudaStream_t s, const float2 *Ld, long long ldd, float2 *xdf) {
   if (n <= 0) return cudaSuccess;
   const int nblk = (n + RB - 1) / RB;
   char *p = (char *)ws;
@@ -940,8 +1209,11 @@ cudaError_t refine(int n, const double *K, long long ldk, const double *L, long 
     GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * nblk, s,
                refine_check_kernel<<<1, 256, 0, s>>>(nblk, partial, norms, tol * tol, state));
     if (it == max_iters) break;
-    cudaError_t e = trsv_inv(n, L, ldl, inv, b, r, 0, trsv_ws, info, s, state);
-    if (e == cudaSuccess) e = trsv_inv(n, L, ldl, inv, b, r, 1, trsv_ws, info, s, state);
+    cudaError_t e = Ld ? trsv_inv_df(n, Ld, ldd, inv, b, r, xdf, 0, trsv_ws, info, s, state)
+                       : trsv_inv(n, L, ldl, inv, b, r, 0, trsv_ws, info, s, state);
+    if (e == cudaSuccess)
+      e = Ld ? trsv_inv_df(n, Ld, ldd, inv, b, r, xdf, 1, trsv_ws, info, s, state)
+             : trsv_inv(n, L, ldl, inv, b, r, 1, trsv_ws, info, s, state);
     if (e != cudaSuccess) return e;
     GPC_LAUNCH(GPC_TRACE_ELEM, (double)n, 24.0 * n, s,
                refine_axpy_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, r, state));

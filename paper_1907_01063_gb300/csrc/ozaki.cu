@@ -718,6 +718,15 @@ __global__ void to_df_lower_kernel(int n, const double *src, long long lds, floa
   dst[(long long)i * ldd + j] = v;
 }
 
+// lower triangle only: grid.y = row blocks of 4, 256 threads over the columns
+__global__ void to_df_tri_kernel(int n, const double *src, long long lds, float2 *dst, long long ldd) {
+  const int i = blockIdx.y * 4 + (threadIdx.x >> 6);
+  if (i >= n) return;
+  const double *row = src + (long long)i * lds;
+  float2 *out = dst + (long long)i * ldd;
+  for (int j = blockIdx.x * 64 + (threadIdx.x & 63); j <= i; j += gridDim.x * 64) out[j] = split_f64(row[j]);
+}
+
 __global__ void from_df_rect_kernel(int m, int c, double *p, long long ld) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)m * c) return;
@@ -882,6 +891,14 @@ cudaError_t ozaki_gemm(const SliceBuf &A, int a_row0, int a_k0, const SliceBuf &
   GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (splits + 2) * mn, s,
              df_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, N, splits, partial, C, ldc,
                                                                            lower ? 1 : 0));
+  return cudaGetLastError();
+}
+
+cudaError_t to_df_tri(int n, const double *src, long long lds, float2 *dst, long long ldd, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min((n + 63) / 64, 32), (unsigned)((n + 3) / 4));
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 8.0 * (double)n * (n + 1), s,
+             to_df_tri_kernel<<<grid, 256, 0, s>>>(n, src, lds, dst, ldd));
   return cudaGetLastError();
 }
 

@@ -11,6 +11,14 @@ constexpr size_t kTestPartialCap = size_t(64) << 20;
 
 int chunks_of(int K) { return std::max(1, (K + 127) / 128); }
 
+__global__ void split_probe_kernel(int n, const double *x, float2 *hilo, double *back) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float2 v = split_f64(x[i]);
+  hilo[i] = v;
+  back[i] = exact_f64(v.x) + exact_f64(v.y);
+}
+
 size_t test_bytes(int M, int N, int K) {
   const int c = chunks_of(K);
   return slice_bytes(M, c) + slice_bytes(N, c) + kTestPartialCap;
@@ -60,4 +68,14 @@ extern "C" int gpc_test_recip_rsqrt(int n, const double *x, double *out, gpc_str
   if (n == 0) return GPC_OK;
   if (!x || !out) return GPC_ERR_INVALID_ARG;
   return recip_rsqrt_probe(n, x, out, stream) == cudaSuccess ? GPC_OK : GPC_ERR_CUDA;
+}
+
+extern "C" int gpc_test_split_f64(int n, const double *x, float *hilo, double *back, gpc_stream_t stream) {
+  if (n < 0) return GPC_ERR_INVALID_ARG;
+  if (n == 0) return GPC_OK;
+  if (!x || !hilo || !back || ((uintptr_t)hilo & 7u)) return GPC_ERR_INVALID_ARG;
+  cudaStream_t s = stream;
+  GPC_LAUNCH(GPC_TRACE_ELEM, 0.0, 24.0 * n, s,
+             split_probe_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, (float2 *)hilo, back));
+  return cudaGetLastError() == cudaSuccess ? GPC_OK : GPC_ERR_CUDA;
 }
