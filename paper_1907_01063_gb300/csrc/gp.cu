@@ -70,6 +70,12 @@ __device__ __forceinline__ dfa::df se_r2_df(const dfa::df *xi, const dfa::df *xj
   return r2;
 }
 
+// FP64 -> double-float pair by field moves (the same pair as dfa::from_double)
+__device__ __forceinline__ dfa::df df_of(double x) {
+  const float2 v = split_f64(x);
+  return dfa::df{v.x, v.y};
+}
+
 __global__ void __launch_bounds__(256)
 se_cov_df_kernel(int n, int d, const double *X, long long ldx, double a2, dfa::df inv2r2, double diagv,
                  double *K, long long ldk, int full) {
@@ -80,8 +86,8 @@ se_cov_df_kernel(int n, int d, const double *X, long long ldx, double a2, dfa::d
   const int i0 = ti * CT, j0 = tj * CT;
   for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
     const int r = idx / d, t = idx - r * d;
-    xi[idx] = dfa::from_double((i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0);
-    xj[t * CT + r] = dfa::from_double((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
+    xi[idx] = df_of((i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0);
+    xj[t * CT + r] = df_of((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
   }
   __syncthreads();
   const int c = threadIdx.x & (CT - 1);
@@ -170,7 +176,9 @@ se_hyper_grad_kernel(int n, int d, const double *X, long long ldx, double alpha,
 
 // Mixed-precision hyperparameter gradient: the sums sum Kbar_ij e_ij and
 // sum Kbar_ij e_ij r2_ij (e_ij = exp(-r2_ij / (2 rho^2))) are accumulated per
-// thread in double-float, then reduced in FP64; partial = (2 alpha S_e,
+// thread in double-float (a running FP32 sum of the terms' high parts with
+// the two-sum errors and the low parts collected beside it), then reduced in
+// FP64; partial = (2 alpha S_e,
 // alpha^2 / rho^3 S_er, 2 sigma sum Kbar_ii) per tile as in the FP64 kernel.
 __global__ void __launch_bounds__(256)
 se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alpha, double rho,
@@ -183,13 +191,19 @@ se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alp
   const int i0 = ti * CT, j0 = tj * CT;
   for (int idx = threadIdx.x; idx < CT * d; idx += blockDim.x) {
     const int r = idx / d, t = idx - r * d;
-    xi[idx] = dfa::from_double((i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0);
-    xj[t * CT + r] = dfa::from_double((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
+    xi[idx] = df_of((i0 + r < n) ? X[(long long)(i0 + r) * ldx + t] : 0.0);
+    xj[t * CT + r] = df_of((j0 + r < n) ? X[(long long)(j0 + r) * ldx + t] : 0.0);
   }
   __syncthreads();
   const int c = threadIdx.x & (CT - 1);
   const int j = j0 + c;
-  dfa::df se = {0.0f, 0.0f}, ser = {0.0f, 0.0f};
+  // the two sums as running FP32 sums with their two-sum errors beside them
+  float seS = 0.0f, seE = 0.0f, serS = 0.0f, serE = 0.0f;
+  auto acc = [](float &S, float &E, dfa::df w) {
+    const dfa::df u = dfa::two_sum(S, w.hi);
+    S = u.hi;
+    E = __fadd_rn(E, __fadd_rn(u.lo, w.lo));
+  };
   double big_e = 0.0, big_er = 0.0, gs = 0.0;  // entries past the double-float range, in FP64
   for (int r = threadIdx.x >> 5; r < CT; r += blockDim.x >> 5) {
     const int i = i0 + r;
@@ -197,7 +211,7 @@ se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alp
     const double kb = Kbar[(long long)i * ldkb + j];
     if (i == j) {
       const float2 kd = split_f64(kb);
-      se = dfa::add(se, dfa::df{kd.x, kd.y});  // e_ii = 1, r2_ii = 0
+      acc(seS, seE, dfa::df{kd.x, kd.y});  // e_ii = 1, r2_ii = 0
       gs = fma(kb, 2.0 * sigma, gs);
       continue;
     }
@@ -210,8 +224,8 @@ se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alp
       const dfa::df e = {m.hi * sc, m.lo * sc};
       const float2 kd = split_f64(kb);
       const dfa::df w = dfa::mul(dfa::df{kd.x, kd.y}, e);
-      se = dfa::add(se, w);
-      ser = dfa::add(ser, dfa::mul(w, r2));
+      acc(seS, seE, w);
+      acc(serS, serE, dfa::mul(w, r2));
     } else {
       const double r2d = dfa::to_double(r2);
       const double w = kb * exp(-dfa::to_double(t));
@@ -220,8 +234,8 @@ se_hyper_grad_df_kernel(int n, int d, const double *X, long long ldx, double alp
     }
   }
   const double a2 = alpha * alpha, inv_r3 = 1.0 / (rho * rho * rho);
-  const double ga = 2.0 * alpha * (dfa::to_double(se) + big_e);
-  const double gr = a2 * inv_r3 * (dfa::to_double(ser) + big_er);
+  const double ga = 2.0 * alpha * (((double)seS + (double)seE) + big_e);
+  const double gr = a2 * inv_r3 * (((double)serS + (double)serE) + big_er);
   const double sa = block_sum_256(ga, red);
   const double sr = block_sum_256(gr, red);
   const double ss = block_sum_256(gs, red);
