@@ -238,3 +238,19 @@ def test_gp_step_captures_in_a_cuda_graph():
     torch.cuda.synchronize()
     assert info.tolist()[1] == gp.GPC_OK
     assert torch.equal(val, v0) and torch.equal(g3, g0) and torch.equal(L, L0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 127, 128, 129, 191, 300])
+def test_gp_lml_mixed_edge_sizes(n):
+    # the double-float solves at their edges: one sub-block (n <= 64), a
+    # one-row last sub-block (65, 129), block boundaries of the factorisation
+    # (128) and ragged tails; alpha after refinement, the value and log det
+    # against the oracle's pass
+    X, y, (a, r, s) = cond_problem(n, cond=1e4)
+    ref = O.gp_lml_and_grad(X, y, a, r, s, 0.0)
+    K = gp.se_cov(dev(X), a, r, s, 0.0)
+    res = gp.gp_lml(K, dev(y), precision="mixed", check=False)
+    assert res["info"].tolist()[1] == gp.GPC_OK
+    assert abs(res["value"].item() - ref["value"]) <= 1e-10 * max(abs(ref["value"]), 1.0)
+    assert abs(res["logdet"].item() - ref["logdet"]) <= 1e-10 * max(abs(ref["logdet"]), 1.0)
+    assert rel(res["alpha"].cpu().numpy(), ref["alpha"]) <= 1e-10
